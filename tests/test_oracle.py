@@ -1,0 +1,298 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by the mathematics.
+
+Each check is chosen so that a plausible mistake fails it: a dropped
+stabilisation term, a wrong sign, a transposed block, a bad boundary normal, or
+a wrong quadrature.
+  * DoF counts against the paper's tables (golden file).
+  * Quadrature against closed-form simplex integrals.
+  * Linear and constant patch tests: CG-VMS is consistent, and P1 reproduces
+    a linear pressure with a constant Darcy velocity exactly.
+  * Sparse LU against dense LU.
+  * Block-structure identities of K (Eq. "S4_cg_stiffness_matrix").
+  * MMS convergence rate 2 in every field (Sections 5.1 and 5.2, slope
+    alpha/d = 1 in 2D and 2/3 in 3D).
+  * The mass-balance invariant (Eqs. "DG_GE_Darcy_mass_balance_1/2" with q = 1).
+  * Network swap symmetry, and decoupling at beta = 0.
+  * Wathen's element bound for the Jacobi-scaled P1 mass matrix.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import inputs
+import oracle
+from oracle.assembly import assemble_problem, geometry
+from oracle.quadrature import cell_rule, facet_rule
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append([int(v) for v in line.split()])
+    return rows
+
+
+def _solve(P, coords=True):
+    K, f = assemble_problem(P)
+    x = oracle.solve_direct(K, f, coords=P.mesh.coords if coords else None)
+    return K, f, oracle.to_nodal(x, P.mesh.n_nodes)
+
+
+# --------------------------------------------------------------------------- meshes
+
+def test_dof_counts_match_paper_tables():
+    for dim, n, dof in _load("dof_tables.txt"):
+        assert inputs.dof_count(dim, n) == dof
+        if (n + 1) ** dim <= 40000:
+            assert inputs.unit_mesh(dim, n).n_dofs == dof
+
+
+@pytest.mark.parametrize("dim,n", [(2, 3), (3, 2)])
+def test_mesh_is_a_conforming_partition(dim, n):
+    m = inputs.unit_mesh(dim, n)
+    g = geometry(m.coords, m.cells)
+    assert np.all(g.vol > 0)
+    assert np.isclose(g.vol.sum(), 1.0)                      # tiles the unit square / cube
+    # boundary measure = perimeter / surface area
+    X = m.coords[m.bfacets]
+    if dim == 2:
+        meas = np.linalg.norm(X[:, 1] - X[:, 0], axis=1)
+        assert np.isclose(meas.sum(), 4.0)
+    else:
+        meas = 0.5 * np.linalg.norm(np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), axis=1)
+        assert np.isclose(meas.sum(), 6.0)
+    assert m.n_cells == (2 if dim == 2 else 6) * n ** dim
+
+
+# --------------------------------------------------------------------------- quadrature
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cell_rule_integrates_p1_products_exactly(dim):
+    # int_K lambda_a lambda_b = |K| (1 + delta_ab) / ((d+1)(d+2)); int_K lambda_a = |K|/(d+1)
+    lam, w = cell_rule(dim)
+    nv = dim + 1
+    M = np.einsum("q,qa,qb->ab", w, lam, lam)
+    ref = (np.ones((nv, nv)) + np.eye(nv)) / ((dim + 1) * (dim + 2))
+    assert np.allclose(M, ref, rtol=0, atol=1e-15)
+    assert np.allclose(w @ lam, 1.0 / nv)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_facet_rule_integrates_p1_products_exactly(dim):
+    lam, w = facet_rule(dim)
+    nf = dim
+    M = np.einsum("q,qa,qb->ab", w, lam, lam)
+    ref = (np.ones((nf, nf)) + np.eye(nf)) / (dim * (dim + 1))
+    assert np.allclose(M, ref, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- patch tests
+
+def _linear_problem(dim, n, a, c1, c2, k1, k2, beta, perturb=True):
+    m = inputs.unit_mesh(dim, n)
+    if perturb:  # move interior nodes so the patch test is not a structured-mesh accident
+        rng = inputs.rng(7)
+        X = m.coords.copy()
+        inner = np.all((X > 1e-12) & (X < 1 - 1e-12), axis=1)
+        X[inner] += rng.uniform(-0.2, 0.2, size=(inner.sum(), dim)) / n
+        m.coords = X
+    p01 = m.coords @ a + c1
+    p02 = m.coords @ a + c2
+    return inputs.Problem(m, np.full(m.n_cells, np.log(k1)), np.full(m.n_cells, np.log(k2)),
+                          1.3, beta, np.zeros(dim), p01, p02)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4), (3, 3)])
+def test_linear_patch_is_reproduced_exactly(dim, n):
+    a = np.array([0.7, -1.1, 0.4][:dim])
+    P = _linear_problem(dim, n, a, 0.3, 0.3, k1=2.0, k2=0.05, beta=3.0)
+    _, _, xn = _solve(P, coords=False)
+    mu = P.mu
+    d = dim
+    assert np.allclose(xn[:, d], P.mesh.coords @ a + 0.3, atol=1e-11)
+    assert np.allclose(xn[:, 2 * d + 1], P.mesh.coords @ a + 0.3, atol=1e-11)
+    assert np.allclose(xn[:, :d], -(2.0 / mu) * a[None, :], atol=1e-10)
+    assert np.allclose(xn[:, d + 1:2 * d + 1], -(0.05 / mu) * a[None, :], atol=1e-11)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4), (3, 2)])
+def test_constant_pressure_gives_zero_velocity(dim, n):
+    P = _linear_problem(dim, n, np.zeros(dim), 1.5, 1.5, k1=1.0, k2=0.1, beta=1.0)
+    _, _, xn = _solve(P, coords=False)
+    d = dim
+    assert np.allclose(xn[:, d], 1.5, atol=1e-12)
+    assert np.allclose(xn[:, 2 * d + 1], 1.5, atol=1e-12)
+    assert np.allclose(xn[:, :d], 0.0, atol=1e-11)
+    assert np.allclose(xn[:, d + 1:2 * d + 1], 0.0, atol=1e-11)
+
+
+# --------------------------------------------------------------------------- linear algebra
+
+@pytest.mark.parametrize("dim,n", [(2, 3), (2, 4), (3, 2)])
+def test_sparse_lu_matches_dense_lu(dim, n):
+    P = inputs.heterogeneous_problem(dim, n, seed=3, beta=2.5)
+    K, f = assemble_problem(P)
+    x1 = oracle.solve_direct(K, f)
+    x2 = oracle.solve_dense(K, f)
+    x3 = oracle.solve_direct(K, f, coords=P.mesh.coords)
+    assert np.allclose(x1, x2, rtol=1e-12, atol=1e-12 * np.abs(x2).max())
+    assert np.allclose(x3, x2, rtol=1e-12, atol=1e-12 * np.abs(x2).max())
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4), (3, 2)])
+def test_block_structure_identities(dim, n):
+    P = inputs.heterogeneous_problem(dim, n, seed=1, beta=0.7)
+    K, _ = assemble_problem(P)
+    b = oracle.field_split_blocks(K, P.mesh.n_nodes, dim)
+    # K_pu = -K_up^T exactly, for both networks
+    for i in ("1", "2"):
+        assert abs(b[f"K{i}pu"] + b[f"K{i}up"].T).max() < 1e-14
+    # the symmetric part of K is blockdiag(A, D): A SPD, D symmetric semi-definite
+    Kd = K.toarray()
+    S = 0.5 * (Kd + Kd.T)
+    A, D = b["A"].toarray(), b["D"].toarray()
+    nu = A.shape[0]
+    perm = np.concatenate([
+        np.concatenate([np.arange(s * P.mesh.n_nodes, (s + 1) * P.mesh.n_nodes)
+                        for s in list(range(dim)) + list(range(dim + 1, 2 * dim + 1))]),
+        np.arange(dim * P.mesh.n_nodes, (dim + 1) * P.mesh.n_nodes),
+        np.arange((2 * dim + 1) * P.mesh.n_nodes, (2 * dim + 2) * P.mesh.n_nodes)])
+    Sp = S[np.ix_(perm, perm)]
+    assert abs(Sp[:nu, nu:]).max() < 1e-14
+    assert np.linalg.eigvalsh(A).min() > 0
+    # D is only semi-definite: p1 = p2 = const is its one null vector (no gradient,
+    # no transfer). K stays nonsingular because B maps that vector to the boundary
+    # flux term, which is non-zero.
+    evd = np.linalg.eigvalsh(D)
+    assert evd[0] > -1e-13 * evd[-1] and evd[1] > 1e-6 * evd[-1]
+    ones = np.ones(D.shape[0])
+    assert np.linalg.norm(D @ ones) < 1e-13 * np.linalg.norm(D)
+    assert np.linalg.norm(b["B"] @ ones) > 1e-3
+    assert np.allclose(A, A.T, atol=1e-15) and np.allclose(D, D.T, atol=1e-15)
+    # K^T is K with the B and C blocks negated
+    Kt = Kd.T[np.ix_(perm, perm)]
+    Kp = Kd[np.ix_(perm, perm)].copy()
+    Kp[:nu, nu:] *= -1.0
+    Kp[nu:, :nu] *= -1.0
+    assert np.allclose(Kt, Kp, atol=1e-14)
+
+
+def test_selfp_schur_is_spd_and_has_two_ring_pattern():
+    P = inputs.heterogeneous_problem(2, 6, seed=2)
+    K, _ = assemble_problem(P)
+    S1, S2 = oracle.selfp_schur(K, P.mesh.n_nodes, 2)
+    for S in (S1, S2):
+        Sd = S.toarray()
+        assert np.allclose(Sd, Sd.T, atol=1e-13 * abs(Sd).max())
+        assert np.linalg.eigvalsh(Sd).min() > 0
+    # 2-ring: the pattern of G^2 for the node graph G
+    m = P.mesh
+    nv = 3
+    r = np.repeat(m.cells, nv, axis=1).ravel()
+    c = np.tile(m.cells, (1, nv)).ravel()
+    G = sp.csr_matrix((np.ones(r.size), (r, c)), shape=(m.n_nodes,) * 2)
+    G2 = (G @ G).astype(bool)
+    assert ((abs(S1) > 0).astype(bool) > G2).nnz == 0
+
+
+# --------------------------------------------------------------------------- MMS
+
+def _rates(dim, ns):
+    errs = []
+    for n in ns:
+        P = inputs.mms_problem(dim, n)
+        _, _, xn = _solve(P)
+        M = oracle.p1_mass_matrix(P.mesh.coords, P.mesh.cells)
+        errs.append(oracle.interp_l2_errors(xn, inputs.nodal_exact(P.mesh.coords), M))
+    out = {}
+    for fld in oracle.FIELDS:
+        out[fld] = [np.log(errs[i][fld] / errs[i + 1][fld]) / np.log(ns[i + 1] / ns[i])
+                    for i in range(len(ns) - 1)]
+    return out
+
+
+def test_mms_rate_2d():
+    rates = _rates(2, [8, 16, 32])
+    for fld, r in rates.items():
+        assert abs(r[-1] - 2.0) < 0.2, (fld, r)
+
+
+def test_mms_rate_3d():
+    rates = _rates(3, [4, 8])
+    for fld, r in rates.items():
+        assert abs(r[-1] - 2.0) < 0.3, (fld, r)
+
+
+def test_mms_solution_satisfies_strong_form():
+    # u_i = -(k_i/mu) grad p_i and div u1 = -beta/mu (p1 - p2), by centred differences
+    prm = inputs.PAPER
+    rng = inputs.rng(5)
+    for dim in (2, 3):
+        x = rng.uniform(0.2, 0.8, size=(20, dim))
+        h = 1e-5
+        u1, p1, u2, p2 = inputs.exact(x, prm)
+        div1 = np.zeros(20)
+        for k in range(dim):
+            e = np.zeros(dim)
+            e[k] = h
+            _, p1p, _, _ = inputs.exact(x + e, prm)
+            _, p1m, _, _ = inputs.exact(x - e, prm)
+            assert np.allclose(-(prm.k1 / prm.mu) * (p1p - p1m) / (2 * h), u1[:, k], rtol=1e-7)
+            u1p = inputs.exact(x + e, prm)[0][:, k]
+            u1m = inputs.exact(x - e, prm)[0][:, k]
+            div1 += (u1p - u1m) / (2 * h)
+        assert np.allclose(div1, -prm.beta / prm.mu * (p1 - p2), rtol=1e-6)
+
+
+# --------------------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("dim,n", [(2, 8), (3, 3)])
+def test_mass_balance_invariant(dim, n):
+    P = inputs.heterogeneous_problem(dim, n, seed=4, beta=1.7)
+    _, _, xn = _solve(P)
+    b1, b2 = oracle.mass_balance(xn, P.mesh.coords, P.mesh.cells, P.mu, P.beta)
+    scale = np.abs(xn).max()
+    assert abs(b1) < 1e-11 * scale and abs(b2) < 1e-11 * scale
+
+
+def test_swap_symmetry_and_beta_zero_decoupling():
+    m = inputs.unit_mesh(2, 6)
+    lk, _ = inputs.lognormal_logk(m.n_cells, 9)
+    p0, _ = inputs.boundary_pressures(m.coords)
+    P = inputs.Problem(m, lk, lk.copy(), 1.0, 2.0, np.zeros(2), p0, p0.copy())
+    _, _, xn = _solve(P)
+    assert np.allclose(xn[:, :3], xn[:, 3:], atol=1e-12 * abs(xn).max())
+    # beta = 0: network 1 does not see network 2's data
+    lk1, lk2 = inputs.lognormal_logk(m.n_cells, 10)
+    q1, q2 = inputs.boundary_pressures(m.coords)
+    Pa = inputs.Problem(m, lk1, lk2, 1.0, 0.0, np.zeros(2), q1, q2)
+    Pb = inputs.Problem(m, lk1, lk2 + 1.0, 1.0, 0.0, np.zeros(2), q1, -q2)
+    _, _, xa = _solve(Pa)
+    _, _, xb = _solve(Pb)
+    assert np.allclose(xa[:, :3], xb[:, :3], atol=1e-12 * abs(xa).max())
+    assert not np.allclose(xa[:, 3:], xb[:, 3:])
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 2)])
+def test_wathen_bound_for_jacobi_scaled_mass(dim, n):
+    # eig(diag(M)^-1 M) lies in [1/2, (d+2)/2] for any positive per-cell weights
+    m = inputs.unit_mesh(dim, n)
+    geom = geometry(m.coords, m.cells)
+    lam, wq = cell_rule(dim)
+    wts = np.exp(inputs.rng(11).normal(0, 2, m.n_cells))
+    Me = np.einsum("c,c,q,qa,qb->cab", wts, geom.vol, wq, lam, lam)
+    nv = dim + 1
+    r = np.repeat(m.cells, nv, axis=1).ravel()
+    c = np.tile(m.cells, (1, nv)).ravel()
+    M = sp.csr_matrix((Me.ravel(), (r, c)), shape=(m.n_nodes,) * 2).toarray()
+    Dm = np.diag(1.0 / np.sqrt(np.diag(M)))
+    ev = np.linalg.eigvalsh(Dm @ M @ Dm)
+    assert ev.min() >= 0.5 - 1e-12
+    assert ev.max() <= (dim + 2) / 2 + 1e-12
