@@ -1,0 +1,225 @@
+/*
+ * dpp.h -- C ABI of the GB300 solver for the four-field double
+ * porosity/permeability (DPP) model.
+ *
+ * Model and method: Joshaghani, Chang, Nakshatrala & Knepley, "Composable
+ * block solvers for the four-field double porosity/permeability model"
+ * (2018).
+ *   - Governing equations: Eqs. "DG_GE_Darcy_BLM" (Darcy in each network plus
+ *     mass balance) and "Composable_mass_transfer" (chi = -beta/mu (p1 - p2)),
+ *     Section 2.
+ *   - Pressure boundary data p0i on Gamma^p: Eq. "DG_GE_Darcy_pBC". It is
+ *     imposed weakly through -(w.n; p0i) in the linear functional (Section 3,
+ *     L_Gal; appendix CG-VMS listing, which uses no strong BCs).
+ *   - Discretisation: the CG-VMS stabilised mixed form (Eq.
+ *     "CG_VMS_Weak_form", Section 3.3), P1 on triangles and tetrahedra.
+ *     Blocks: Eq. "S4_cg_stiffness_matrix"; load: Eq. "S4_cg_rhs"; system
+ *     K u = f: Eq. "S4_linear_problem" (Section 4).
+ *   - Solver: Method 2 of Section 4.2 ("splitting by fields"). A full
+ *     Schur factorisation of [[A, B], [C, D]] with A = blockdiag(K1_uu,
+ *     K2_uu); the selfp Schur matrix S_p = D - C diag(A)^-1 B, additively
+ *     split into its two diagonal blocks (Eqs. "S4_sp1", "S4_sp2"); one
+ *     multigrid V-cycle per block; single-sweep inner solves inside an outer
+ *     Krylov method.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA global-memory addresses on the current device.
+ *     The caller owns them and keeps them valid until the call's stream work
+ *     has completed. The library owns its handles and frees them only in
+ *     dpp_destroy_*.
+ *   - Work is ordered on `stream` (NULL = the legacy default stream). Calls that
+ *     must report a host-visible result (dpp_solve*, dpp_setup_pc and
+ *     dpp_assemble's size discovery) synchronise that stream before they return.
+ *   - No call aborts, exits or traps. Errors come back as dpp_status, and
+ *     dpp_last_error() gives a thread-local message. Input arrays are checked
+ *     on the device for index range and finiteness before any kernel uses
+ *     them as an index.
+ *   - Unknown layout: node-interleaved. Node a holds 2d+2 doubles
+ *     [u1_0 .. u1_{d-1}, p1, u2_0 .. u2_{d-1}, p2] at offset a*(2d+2).
+ *   - There is no CPU fallback. Without a CUDA device every call that needs
+ *     one returns DPP_ERR_CUDA.
+ */
+#ifndef DPP_H
+#define DPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so callers need no CUDA headers. */
+typedef struct CUstream_st* dpp_stream_t;
+
+typedef enum {
+    DPP_OK = 0,
+    DPP_ERR_INVALID_ARGUMENT = 1, /* bad size, null pointer, index out of range, degenerate cell */
+    DPP_ERR_OUT_OF_MEMORY = 2,
+    DPP_ERR_CUDA = 3,             /* a CUDA runtime error (including "no device") */
+    DPP_ERR_NOT_CONVERGED = 4,    /* max_iters reached; x holds the last iterate */
+    DPP_ERR_BREAKDOWN = 5,        /* Krylov breakdown before convergence */
+    DPP_ERR_NONFINITE = 6,        /* NaN or Inf in an input or in the iteration */
+    DPP_ERR_TIMEOUT = 7,          /* a bounded device wait ran out */
+    DPP_ERR_BAD_STATE = 8         /* handle mismatch or misuse */
+} dpp_status;
+
+typedef enum { DPP_FP64 = 0, DPP_MIXED_FP32_FP64 = 1 } dpp_precision;
+typedef enum { DPP_MEM_DEVICE = 0, DPP_MEM_HOST = 1 } dpp_memory;
+
+typedef struct dpp_problem_s* dpp_problem; /* opaque: graph, K pair values, f */
+typedef struct dpp_pc_s* dpp_pc;           /* opaque: S_p blocks and AMG hierarchy */
+
+/*
+ * Problem description (Section 2 and the CG-VMS forms of Section 3.3).
+ * `memory` says where every array below lives. For DPP_MEM_HOST the library
+ * copies the arrays to the device inside dpp_assemble.
+ */
+typedef struct {
+    int32_t dim;              /* 2 (triangles) or 3 (tetrahedra) */
+    int32_t memory;           /* dpp_memory of the arrays below */
+    int64_t n_nodes, n_cells, n_bfacets;
+    const double* coords;     /* [n_nodes][dim] */
+    const int32_t* cells;     /* [n_cells][dim+1] node ids; either orientation */
+    const int32_t* bfacets;   /* [n_bfacets][dim] boundary facets on Gamma^p (pressure data) */
+    const double* log_k1;     /* [n_cells] natural-log macro permeability k1 */
+    const double* log_k2;     /* [n_cells] natural-log micro permeability k2 */
+    double mu;                /* viscosity, > 0 */
+    double beta;              /* mass-transfer coefficient, >= 0 (Eq. "Composable_mass_transfer") */
+    double gamma_b[3];        /* constant gamma*b body force (first dim entries used) */
+    const double* p01;        /* [n_nodes] macro pressure data, read at bfacet nodes */
+    const double* p02;        /* [n_nodes] micro pressure data, read at bfacet nodes */
+} dpp_problem_desc;
+
+/* Preconditioner options (Section 4.2, Method 2; defaults from dpp_pc_opts_default). */
+typedef struct {
+    int32_t cheb_degree_mass;  /* Chebyshev-Jacobi degree for A^-1 (default 3) */
+    int32_t cheb_degree_amg;   /* Chebyshev-Jacobi pre/post smoothing degree (default 2) */
+    int32_t coarse_max_rows;   /* stop coarsening at or below this many rows (default 384) */
+    int32_t max_levels;        /* hierarchy depth cap (default 12) */
+    double strength_theta;     /* SA symmetric strength threshold (default 0.02) */
+    double cheb_ratio;         /* AMG smoothing interval [lmax/ratio, 1.1 lmax] (default 20) */
+    int32_t use_lumped_diag;   /* 0: diag(K_uu) as written (default); 1: row-sum lumping */
+    int32_t precision;         /* dpp_precision of the hierarchy values */
+} dpp_pc_opts;
+
+/* Krylov options. */
+typedef struct {
+    double rtol;               /* stop at FP64 ||f - K x||_2 / ||f||_2 <= rtol (default 1e-10) */
+    int32_t restart;           /* FGMRES restart length m (default 30, at most 64) */
+    int32_t max_iters;         /* total inner iterations cap (default 1000) */
+    int32_t x0_zero;           /* 1: ignore x on entry and start from 0 (default 1) */
+    int32_t x_memory;          /* dpp_memory of x / lambda arrays passed to dpp_solve* (default device) */
+    int32_t check_every;       /* host convergence check period in iterations (default 1) */
+    double inner_rtol;         /* mixed precision: inner cycle reduction target (default 1e-4) */
+    int64_t wait_budget_cycles;/* bound for device-side waits, 0 = library default */
+} dpp_solve_opts;
+
+typedef struct {
+    int32_t status;            /* dpp_status of the call */
+    int32_t iterations;        /* inner Krylov iterations */
+    int32_t restarts;          /* restarts / refinement steps */
+    int32_t levels;            /* AMG levels (from the pc) */
+    double rel_residual;       /* FP64 true ||f - K x|| / ||f|| at exit */
+    double ms_assemble, ms_setup, ms_solve;
+} dpp_solve_info;
+
+void dpp_pc_opts_default(dpp_pc_opts* o);
+void dpp_solve_opts_default(dpp_solve_opts* o);
+
+/*
+ * Assemble K and f of Eq. "S4_linear_problem" for the CG-VMS P1 form.
+ * Per node pair (a, b) the library keeps the distinct block values of
+ * Eq. "S4_cg_stiffness_matrix": the two weighted masses 1/2 (w; mu/ki u),
+ * the d entries of K_up, the d entries of K_pu, the two K_pp diagonals and
+ * the coupling K12_pp = K21_pp. precision = DPP_MIXED_FP32_FP64 also keeps
+ * an FP32 copy of the values. On success *out is a new handle.
+ * Errors: INVALID_ARGUMENT (null pointers, dim not 2 or 3, an index out of
+ * range, a zero-volume cell, mu <= 0 or beta < 0, a bfacet that is not a
+ * cell face), NONFINITE (NaN or Inf in coords, log k or p0), OUT_OF_MEMORY,
+ * CUDA.
+ */
+dpp_status dpp_assemble(const dpp_problem_desc* desc, int32_t precision, dpp_stream_t stream,
+                        dpp_problem* out);
+
+/*
+ * Build the field-split preconditioner of Section 4.2 (Method 2). It forms
+ * S_pi = Ki_pp - Ki_pu diag(Ki_uu)^-1 Ki_up (Eqs. "S4_sp1", "S4_sp2") on the
+ * device, then one smoothed-aggregation AMG hierarchy on blockdiag(S_p1,
+ * S_p2). Synchronises `stream`. Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA.
+ */
+dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t stream,
+                        dpp_pc* out);
+
+/*
+ * Solve K x = f with right-preconditioned FGMRES(m), the preconditioner of
+ * dpp_setup_pc, in FP64 (or FP64-outer / FP32-inner refinement if the problem
+ * and pc were built with DPP_MIXED_FP32_FP64). x: [n_nodes][2d+2], where
+ * opts->x_memory says; on entry the initial guess unless opts->x0_zero,
+ * on exit the solution. info may be NULL. Returns NOT_CONVERGED (x = last
+ * iterate), BREAKDOWN, NONFINITE, INVALID_ARGUMENT or CUDA on failure.
+ */
+dpp_status dpp_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts, double* x,
+                     dpp_solve_info* info, dpp_stream_t stream);
+
+/*
+ * Adjoint of the solve for J(x) with a given gradient dJdx (device,
+ * [n_nodes][2d+2]). It solves K^T lambda = dJdx with the same preconditioner
+ * (S_p is unchanged when B and C change sign). It then forms, for every cell
+ * c, dJ/dlog k1_c = -lambda^T (dK/dlog k1_c x - df/dlog k1_c), the same for
+ * log k2, and dJ/dbeta = -lambda^T (dK/dbeta) x. Outputs (device): lambda
+ * [n_nodes][2d+2], dJ_dlogk1 [n_cells], dJ_dlogk2 [n_cells], dJ_dbeta [1].
+ * x must be the forward solution of the same problem.
+ */
+dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts,
+                             const double* x, const double* dJdx, double* lambda,
+                             double* dJ_dlogk1, double* dJ_dlogk2, double* dJ_dbeta,
+                             dpp_solve_info* info, dpp_stream_t stream);
+
+void dpp_destroy_problem(dpp_problem prob);
+void dpp_destroy_pc(dpp_pc pc);
+const char* dpp_status_string(int32_t status);
+const char* dpp_last_error(void); /* thread-local detail of the last failing call */
+
+/* ---------------- inspection entry points (used by the parity tests) ---------------- */
+
+/* Sizes: out[0] = n_nodes, out[1] = n_cells, out[2] = n_pairs (CSR entries
+ * of the node-pair graph, self pairs included), out[3] = values per pair,
+ * out[4] = dim, out[5] = SELL slot groups. */
+dpp_status dpp_problem_sizes(dpp_problem prob, int64_t out[6]);
+
+/* y = K x, or y = K^T x if transpose != 0. x, y: device [n_nodes][2d+2], FP64. */
+dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, double* y,
+                       dpp_stream_t stream);
+
+/* Copy f (device, [n_nodes][2d+2]) into `f`. */
+dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream);
+
+/* Export the node-pair graph and values in CSR order: row_ptr [n_nodes+1],
+ * col [n_pairs], vals [n_pairs][values per pair] (all device). Value order
+ * per pair (a, b): m1, m2, Kup[0..d-1], Kpu[0..d-1], d1, d2, e where
+ * (u1_i, u1_i) = m1, (u1_i, p1) = Kup[i], (p1, u1_i) = Kpu[i], (p1, p1) = d1,
+ * (p2, p2) = d2, (p1, p2) = (p2, p1) = e, with the same pattern for network 2. */
+dpp_status dpp_export_pairs(dpp_problem prob, int32_t* row_ptr, int32_t* col, double* vals,
+                            dpp_stream_t stream);
+
+/* z = P^-1 r for the preconditioner (device [n_nodes][2d+2]); transpose != 0
+ * applies the preconditioner of K^T. */
+dpp_status dpp_pc_apply(dpp_problem prob, dpp_pc pc, int32_t transpose, const double* r,
+                        double* z, dpp_stream_t stream);
+
+/* Sizes of AMG level `level`: out[0] = rows, out[1] = nnz, out[2] = levels,
+ * out[3] = columns of the prolongator P (0 on the coarsest level), out[4] = nnz(P). */
+dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]);
+
+/* Export the CSR matrix of AMG level `level` (level 0 = blockdiag(S_p1, S_p2))
+ * and, for level < levels-1, its prolongator P (device arrays sized from
+ * dpp_pc_level_sizes). Null P pointers skip P. */
+dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32_t* col,
+                               double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
+                               dpp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPP_H */

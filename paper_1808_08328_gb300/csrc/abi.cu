@@ -1,0 +1,391 @@
+// extern "C" entry points of libdpp (declared in include/dpp.h). Every call
+// validates its arguments on the host, runs its work on the caller's stream,
+// and converts internal exceptions into a dpp_status plus a thread-local
+// message. Nothing here aborts, exits or traps.
+#include <cstring>
+#include <new>
+
+#include "amg.cuh"
+
+namespace dpp {
+void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s);
+void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
+              cudaStream_t s);
+dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, const double* rhs,
+                  double* x, bool transpose, dpp_solve_info& info, cudaStream_t s,
+                  HostScratch& hs);
+void adjoint_gradients(const ProblemImpl& P, const double* x, const double* lambda, double* g1,
+                       double* g2, double* gbeta, cudaStream_t s);
+}  // namespace dpp
+
+using namespace dpp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dpp_status set_error(dpp_status s, const std::string& m) {
+    g_last_error = m;
+    return s;
+}
+
+template <class F>
+dpp_status guarded(const char* name, F&& f) {
+    try {
+        g_last_error.clear();
+        return f();
+    } catch (const Error& e) {
+        return set_error(e.status, std::string(name) + ": " + e.what());
+    } catch (const std::bad_alloc&) {
+        return set_error(DPP_ERR_OUT_OF_MEMORY, std::string(name) + ": host allocation failed");
+    } catch (const std::exception& e) {
+        return set_error(DPP_ERR_CUDA, std::string(name) + ": " + e.what());
+    } catch (...) {
+        return set_error(DPP_ERR_CUDA, std::string(name) + ": unknown failure");
+    }
+}
+
+void require(bool ok, const std::string& what) {
+    if (!ok) fail(DPP_ERR_INVALID_ARGUMENT, what);
+}
+
+void require_aligned(const void* p, const char* what) {
+    require(((uintptr_t)p & 15u) == 0, std::string(what) + " must be 16-byte aligned");
+}
+
+void ensure_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        fail(DPP_ERR_CUDA, "no CUDA device is available (libdpp has no CPU fallback)");
+    }
+}
+
+struct EventTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit EventTimer(cudaStream_t st) : s(st) {
+        DPP_CK(cudaEventCreate(&a));
+        DPP_CK(cudaEventCreate(&b));
+        DPP_CK(cudaEventRecord(a, s));
+    }
+    double stop() {
+        DPP_CK(cudaEventRecord(b, s));
+        DPP_CK(cudaEventSynchronize(b));
+        float ms = 0;
+        DPP_CK(cudaEventElapsedTime(&ms, a, b));
+        return ms;
+    }
+    ~EventTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+void dpp_pc_opts_default(dpp_pc_opts* o) {
+    if (!o) return;
+    o->cheb_degree_mass = 3;
+    o->cheb_degree_amg = 2;
+    o->coarse_max_rows = 384;
+    o->max_levels = 12;
+    o->strength_theta = 0.02;
+    o->cheb_ratio = 20.0;
+    o->use_lumped_diag = 0;
+    o->precision = DPP_FP64;
+}
+
+void dpp_solve_opts_default(dpp_solve_opts* o) {
+    if (!o) return;
+    o->rtol = 1e-10;
+    o->restart = 30;
+    o->max_iters = 1000;
+    o->x0_zero = 1;
+    o->x_memory = DPP_MEM_DEVICE;
+    o->check_every = 1;
+    o->inner_rtol = 1e-4;
+    o->wait_budget_cycles = 0;
+}
+
+const char* dpp_status_string(int32_t s) {
+    switch (s) {
+        case DPP_OK: return "DPP_OK";
+        case DPP_ERR_INVALID_ARGUMENT: return "DPP_ERR_INVALID_ARGUMENT";
+        case DPP_ERR_OUT_OF_MEMORY: return "DPP_ERR_OUT_OF_MEMORY";
+        case DPP_ERR_CUDA: return "DPP_ERR_CUDA";
+        case DPP_ERR_NOT_CONVERGED: return "DPP_ERR_NOT_CONVERGED";
+        case DPP_ERR_BREAKDOWN: return "DPP_ERR_BREAKDOWN";
+        case DPP_ERR_NONFINITE: return "DPP_ERR_NONFINITE";
+        case DPP_ERR_TIMEOUT: return "DPP_ERR_TIMEOUT";
+        case DPP_ERR_BAD_STATE: return "DPP_ERR_BAD_STATE";
+        default: return "DPP_ERR_UNKNOWN";
+    }
+}
+
+const char* dpp_last_error(void) { return g_last_error.c_str(); }
+
+dpp_status dpp_assemble(const dpp_problem_desc* d, int32_t precision, dpp_stream_t stream,
+                        dpp_problem* out) {
+    return guarded("dpp_assemble", [&]() -> dpp_status {
+        require(d != nullptr && out != nullptr, "null descriptor or output handle");
+        *out = nullptr;
+        require(d->dim == 2 || d->dim == 3, "dim must be 2 or 3");
+        require(d->memory == DPP_MEM_DEVICE || d->memory == DPP_MEM_HOST, "bad memory kind");
+        require(precision == DPP_FP64 || precision == DPP_MIXED_FP32_FP64, "bad precision");
+        require(d->n_nodes > 0 && d->n_cells > 0 && d->n_bfacets >= 0, "sizes must be positive");
+        require(d->n_nodes < (1LL << 30) && d->n_cells < (1LL << 30), "mesh too large for int32 ids");
+        require(d->coords && d->cells && d->log_k1 && d->log_k2 && d->p01 && d->p02,
+                "null input array");
+        require(d->n_bfacets == 0 || d->bfacets, "null bfacets with n_bfacets > 0");
+        require(d->mu > 0 && std::isfinite(d->mu), "mu must be positive and finite");
+        require(d->beta >= 0 && std::isfinite(d->beta), "beta must be >= 0 and finite");
+        for (int k = 0; k < d->dim; ++k) require(std::isfinite(d->gamma_b[k]), "gamma_b not finite");
+        ensure_device();
+        cudaStream_t s = (cudaStream_t)stream;
+        auto* h = new dpp_problem_s();
+        try {
+            EventTimer t(s);
+            h->impl.precision = precision;
+            assemble_problem(h->impl, *d, s);
+            h->impl.ms_assemble = t.stop();
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t stream,
+                        dpp_pc* out) {
+    return guarded("dpp_setup_pc", [&]() -> dpp_status {
+        require(prob != nullptr && out != nullptr, "null problem or output handle");
+        *out = nullptr;
+        dpp_pc_opts o;
+        dpp_pc_opts_default(&o);
+        if (opts) o = *opts;
+        require(o.cheb_degree_mass >= 1 && o.cheb_degree_mass <= 16, "cheb_degree_mass in [1,16]");
+        require(o.cheb_degree_amg >= 1 && o.cheb_degree_amg <= 16, "cheb_degree_amg in [1,16]");
+        require(o.coarse_max_rows >= 1 && o.coarse_max_rows <= 4096, "coarse_max_rows in [1,4096]");
+        require(o.max_levels >= 1 && o.max_levels <= 32, "max_levels in [1,32]");
+        require(o.strength_theta >= 0 && o.strength_theta < 1, "strength_theta in [0,1)");
+        require(o.cheb_ratio > 1, "cheb_ratio > 1");
+        require(o.precision == DPP_FP64 || o.precision == DPP_MIXED_FP32_FP64, "bad precision");
+        cudaStream_t s = (cudaStream_t)stream;
+        auto* h = new dpp_pc_s();
+        try {
+            EventTimer t(s);
+            h->impl.opts = o;
+            h->impl.precision = o.precision;
+            h->owner = prob;
+            pc_setup(h->impl, prob->impl, s);
+            h->impl.ms_setup = t.stop();
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+        return DPP_OK;
+    });
+}
+
+static dpp_status solve_common(const char* name, dpp_problem prob, dpp_pc pc,
+                               const dpp_solve_opts* opts, const double* rhs_dev, double* x,
+                               bool transpose, dpp_solve_info* info, dpp_stream_t stream) {
+    dpp_solve_info local{};
+    dpp_solve_info& inf = info ? *info : local;
+    std::memset(&inf, 0, sizeof(inf));
+    dpp_status st = guarded(name, [&]() -> dpp_status {
+        require(prob && pc && x, "null problem, pc or x");
+        require(pc->owner == prob, "pc was built for a different problem");
+        dpp_solve_opts o;
+        dpp_solve_opts_default(&o);
+        if (opts) o = *opts;
+        require(o.rtol > 0 && o.rtol < 1, "rtol in (0,1)");
+        require(o.restart >= 1 && o.restart <= 64, "restart in [1,64]");
+        require(o.max_iters >= 1, "max_iters >= 1");
+        require(o.x_memory == DPP_MEM_DEVICE || o.x_memory == DPP_MEM_HOST, "bad x_memory");
+        const ProblemImpl& P = prob->impl;
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t n = P.n_nodes * P.ns;
+        inf.levels = (int)pc->impl.levels.size();
+        inf.ms_assemble = P.ms_assemble;
+        inf.ms_setup = pc->impl.ms_setup;
+        EventTimer t(s);
+        DBuf<double> xd;
+        double* xw = x;
+        if (o.x_memory == DPP_MEM_HOST) {
+            xd.alloc(n);
+            xw = xd.get();
+            if (!o.x0_zero)
+                DPP_CK(cudaMemcpyAsync(xw, x, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        } else {
+            require_aligned(x, "x");
+        }
+        dpp_status r = fgmres(P, pc->impl, o, rhs_dev ? rhs_dev : P.f.get(), xw, transpose, inf, s,
+                              const_cast<HostScratch&>(P.hs));
+        if (o.x_memory == DPP_MEM_HOST)
+            DPP_CK(cudaMemcpyAsync(x, xw, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        inf.ms_solve = t.stop();
+        if (r != DPP_OK) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "%s after %d iterations, relative residual %.3e",
+                     dpp_status_string(r), inf.iterations, inf.rel_residual);
+            g_last_error = std::string(name) + ": " + buf;
+        }
+        return r;
+    });
+    inf.status = st;
+    return st;
+}
+
+dpp_status dpp_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts, double* x,
+                     dpp_solve_info* info, dpp_stream_t stream) {
+    return solve_common("dpp_solve", prob, pc, opts, nullptr, x, false, info, stream);
+}
+
+dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts,
+                             const double* x, const double* dJdx, double* lambda,
+                             double* dJ_dlogk1, double* dJ_dlogk2, double* dJ_dbeta,
+                             dpp_solve_info* info, dpp_stream_t stream) {
+    dpp_status st;
+    {
+        dpp_status pre = guarded("dpp_adjoint_solve", [&]() -> dpp_status {
+            require(prob && x && dJdx && lambda && dJ_dlogk1 && dJ_dlogk2 && dJ_dbeta,
+                    "null argument");
+            if (opts) require(opts->x_memory == DPP_MEM_DEVICE, "adjoint arrays must be device memory");
+            require_aligned(x, "x");
+            require_aligned(dJdx, "dJdx");
+            return DPP_OK;
+        });
+        if (pre != DPP_OK) {
+            if (info) { std::memset(info, 0, sizeof(*info)); info->status = pre; }
+            return pre;
+        }
+    }
+    dpp_solve_opts o;
+    dpp_solve_opts_default(&o);
+    if (opts) o = *opts;
+    st = solve_common("dpp_adjoint_solve", prob, pc, &o, dJdx, lambda, true, info, stream);
+    if (st != DPP_OK) return st;
+    return guarded("dpp_adjoint_solve", [&]() -> dpp_status {
+        cudaStream_t s = (cudaStream_t)stream;
+        adjoint_gradients(prob->impl, x, lambda, dJ_dlogk1, dJ_dlogk2, dJ_dbeta, s);
+        DPP_CK(cudaStreamSynchronize(s));
+        return DPP_OK;
+    });
+}
+
+void dpp_destroy_problem(dpp_problem p) { delete p; }
+void dpp_destroy_pc(dpp_pc p) { delete p; }
+
+dpp_status dpp_problem_sizes(dpp_problem prob, int64_t out[6]) {
+    return guarded("dpp_problem_sizes", [&]() -> dpp_status {
+        require(prob && out, "null argument");
+        const ProblemImpl& P = prob->impl;
+        out[0] = P.n_nodes;
+        out[1] = P.n_cells;
+        out[2] = P.n_pairs;
+        out[3] = P.nv;
+        out[4] = P.dim;
+        out[5] = P.n_groups;
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, double* y,
+                       dpp_stream_t stream) {
+    return guarded("dpp_apply_K", [&]() -> dpp_status {
+        require(prob && x && y && x != y, "null or aliased argument");
+        require_aligned(x, "x");
+        require_aligned(y, "y");
+        apply_K(prob->impl, x, y, nullptr, transpose != 0, false, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream) {
+    return guarded("dpp_get_rhs", [&]() -> dpp_status {
+        require(prob && f, "null argument");
+        const ProblemImpl& P = prob->impl;
+        DPP_CK(cudaMemcpyAsync(f, P.f.get(), P.n_nodes * P.ns * sizeof(double),
+                               cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+        return DPP_OK;
+    });
+}
+
+}  // extern "C"
+
+namespace dpp {
+void export_pairs(const ProblemImpl& P, int* rp, int* col, double* vals, cudaStream_t s);
+}
+
+extern "C" {
+
+dpp_status dpp_export_pairs(dpp_problem prob, int32_t* row_ptr, int32_t* col, double* vals,
+                            dpp_stream_t stream) {
+    return guarded("dpp_export_pairs", [&]() -> dpp_status {
+        require(prob && row_ptr && col && vals, "null argument");
+        export_pairs(prob->impl, row_ptr, col, vals, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_pc_apply(dpp_problem prob, dpp_pc pc, int32_t transpose, const double* r, double* z,
+                        dpp_stream_t stream) {
+    return guarded("dpp_pc_apply", [&]() -> dpp_status {
+        require(prob && pc && r && z && r != z, "null or aliased argument");
+        require(pc->owner == prob, "pc was built for a different problem");
+        require_aligned(r, "r");
+        require_aligned(z, "z");
+        pc_apply(prob->impl, pc->impl, r, z, transpose != 0, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]) {
+    return guarded("dpp_pc_level_sizes", [&]() -> dpp_status {
+        require(pc && out, "null argument");
+        const auto& L = pc->impl.levels;
+        require(level >= 0 && level < (int)L.size(), "level out of range");
+        out[0] = L[level].A.n_rows;
+        out[1] = L[level].A.nnz;
+        out[2] = (int64_t)L.size();
+        out[3] = (level + 1 < (int)L.size()) ? L[level].P.n_cols : 0;
+        out[4] = (level + 1 < (int)L.size()) ? L[level].P.nnz : 0;
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32_t* col,
+                               double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
+                               dpp_stream_t stream) {
+    return guarded("dpp_pc_export_level", [&]() -> dpp_status {
+        require(pc && row_ptr && col && val, "null argument");
+        const auto& L = pc->impl.levels;
+        require(level >= 0 && level < (int)L.size(), "level out of range");
+        cudaStream_t s = (cudaStream_t)stream;
+        const Csr& A = L[level].A;
+        DPP_CK(cudaMemcpyAsync(row_ptr, A.row_ptr.get(), (A.n_rows + 1) * sizeof(int),
+                               cudaMemcpyDeviceToDevice, s));
+        DPP_CK(cudaMemcpyAsync(col, A.col.get(), A.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+        DPP_CK(cudaMemcpyAsync(val, A.val.get(), A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (p_row_ptr && p_col && p_val && level + 1 < (int)L.size()) {
+            const Csr& P = L[level].P;
+            DPP_CK(cudaMemcpyAsync(p_row_ptr, P.row_ptr.get(), (P.n_rows + 1) * sizeof(int),
+                                   cudaMemcpyDeviceToDevice, s));
+            DPP_CK(cudaMemcpyAsync(p_col, P.col.get(), P.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
+            DPP_CK(cudaMemcpyAsync(p_val, P.val.get(), P.nnz * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s));
+        }
+        DPP_CK(cudaStreamSynchronize(s));
+        return DPP_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,516 @@
+// Smoothed-aggregation AMG on blockdiag(S_p1, S_p2) with Chebyshev-Jacobi
+// smoothing. It plays the role the paper gives to one BoomerAMG V-cycle per
+// Schur block (Section 4.2, Method 2, "fieldsplit_1" of its appendix
+// options).
+//
+// Setup per level (Vanek, Mandel & Brezina, Computing 56, 1996, for the
+// aggregation and prolongator smoothing; Bell, Dalton & Olson, SIAM J. Sci.
+// Comput. 34(4), 2012, for the parallel distance-2 independent-set
+// aggregation):
+//   1. symmetric strength: j is a strong neighbour of i if
+//      |a_ij| >= theta sqrt(|a_ii a_jj|);
+//   2. a distance-2 maximal independent set of the strength graph. Ties are
+//      broken by a fixed integer hash of the row id, so the result is
+//      deterministic. Each root plus its strong neighbours forms an
+//      aggregate; the remaining rows join the aggregate of a strong
+//      neighbour;
+//   3. tentative prolongator P0 = aggregate indicator; smoothed prolongator
+//      P = (I - omega D^-1 A) P0 with omega = 4 / (3 lambda_max(D^-1 A));
+//   4. Galerkin coarse matrix A_c = P^T (A P).
+// lambda_max comes from 15 power iterations on D^-1 A. The coarsest matrix is
+// inverted densely (Gauss-Jordan without pivoting, valid for SPD) and applied
+// as a dense matrix-vector product.
+//
+// Smoother: Chebyshev polynomial in D^-1 A on [lambda_max / ratio,
+// 1.1 lambda_max] (Adams, Brezina, Hu & Tuminaro, J. Comput. Phys. 188,
+// 2003).
+#include "amg.cuh"
+
+#include <cmath>
+
+namespace dpp {
+
+namespace {
+
+// ------------------------------------------------------------------ CSR SpMV
+// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x
+template <int L, int MODE>
+__global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __restrict__ rp,
+                                                  const int* __restrict__ col,
+                                                  const double* __restrict__ val,
+                                                  const double* __restrict__ x,
+                                                  const double* __restrict__ b,
+                                                  double* __restrict__ y) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = t / L;
+    const int lane = (int)(t % L);
+    const bool active = row < n_rows;  // inactive lanes still join the shuffles
+    double acc = 0.0;
+    if (active)
+        for (int p = rp[row] + lane; p < rp[row + 1]; p += L) acc += val[p] * __ldg(x + col[p]);
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
+    if (active && lane == 0) {
+        if (MODE == 0) y[row] = acc;
+        else if (MODE == 1) y[row] = b[row] - acc;
+        else y[row] += acc;
+    }
+}
+
+template <int MODE>
+void spmv_lanes(int lanes, const Csr& A, const double* x, const double* b, double* y,
+                cudaStream_t s) {
+    const int B = 256;
+    const int64_t thr = A.n_rows * lanes;
+    const int g = grid_for(thr, B);
+    const int* rp = A.row_ptr.get();
+    const int* cl = A.col.get();
+    const double* v = A.val.get();
+    switch (lanes) {
+        case 1: k_csr_spmv<1, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 2: k_csr_spmv<2, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 4: k_csr_spmv<4, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 8: k_csr_spmv<8, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 16: k_csr_spmv<16, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        default: k_csr_spmv<32, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+    }
+    DPP_LAUNCH_CK();
+}
+
+int pick_lanes(const Csr& A) {
+    double avg = A.n_rows ? (double)A.nnz / (double)A.n_rows : 1.0;
+    if (avg <= 3) return 2;
+    if (avg <= 10) return 4;
+    if (avg <= 24) return 8;
+    if (avg <= 56) return 16;
+    return 32;
+}
+
+// ------------------------------------------------------------------ vectors
+__global__ void k_diag_inv(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, double* __restrict__ dinv,
+                           double* __restrict__ dabs, int* status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (col[p] == i) d = val[p];
+    if (!(d > 0.0) || !isfinite(d)) atomicOr(status, kDevDegenerate);
+    dinv[i] = 1.0 / d;
+    if (dabs) dabs[i] = fabs(d);
+}
+
+// Chebyshev vector step: zero_init: d = c2 Dinv b, x = d.  else: d = c1 d + c2 Dinv r, x += d
+__global__ void k_cheb_update(int64_t n, const double* __restrict__ dinv,
+                              const double* __restrict__ r, double* __restrict__ d,
+                              double* __restrict__ x, double c1, double c2, int zero_init) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (zero_init) {
+            double v = c2 * dinv[i] * r[i];
+            d[i] = v;
+            x[i] = v;
+        } else {
+            double v = c1 * d[i] + c2 * dinv[i] * r[i];
+            d[i] = v;
+            x[i] += v;
+        }
+    }
+}
+
+__global__ void k_fill_int(int64_t n, int v, int* __restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+__global__ void k_dinv_scale(int64_t n, const double* __restrict__ dinv, double* __restrict__ v) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        v[i] *= dinv[i];
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {  // murmur3 finaliser
+    x ^= x >> 16;
+    x *= 0x85ebca6bu;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35u;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = 0.5 + (double)(mix32((uint32_t)i * 2654435761u + 12345u) >> 8) / 16777216.0;
+}
+
+// ------------------------------------------------------------------ aggregation
+__global__ void k_strength_count(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                                 const double* __restrict__ val, const double* __restrict__ dabs,
+                                 double theta, int* __restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    const double di = dabs[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        int j = col[p];
+        if (j != i && fabs(val[p]) >= theta * sqrt(di * dabs[j])) ++c;
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_strength_fill(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ dabs,
+                                double theta, const int* __restrict__ srp, int* __restrict__ scol) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int q = srp[i];
+    const double di = dabs[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        int j = col[p];
+        if (j != i && fabs(val[p]) >= theta * sqrt(di * dabs[j])) scol[q++] = j;
+    }
+}
+
+enum : int { kOut = 0, kUnd = 1, kIn = 2 };
+
+__device__ __forceinline__ uint64_t mis_key(int state, int64_t i) {
+    return ((uint64_t)state << 62) | ((uint64_t)mix32((uint32_t)i) << 30) | (uint64_t)(i & 0x3fffffff);
+}
+
+__global__ void k_mis_t0(int64_t n, const int* __restrict__ state, uint64_t* __restrict__ t0) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t0[i] = mis_key(state[i], i);
+}
+
+__global__ void k_mis_max(int64_t n, const int* __restrict__ srp, const int* __restrict__ scol,
+                          const uint64_t* __restrict__ tin, uint64_t* __restrict__ tout) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t m = tin[i];
+    for (int p = srp[i]; p < srp[i + 1]; ++p) m = max(m, tin[scol[p]]);
+    tout[i] = m;
+}
+
+__global__ void k_mis_update(int64_t n, int* __restrict__ state, const uint64_t* __restrict__ t0,
+                             const uint64_t* __restrict__ t2, int* __restrict__ undecided) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != kUnd) return;
+    if (t2[i] == t0[i]) state[i] = kIn;
+    else if ((int)(t2[i] >> 62) == kIn) state[i] = kOut;
+    else atomicAdd(undecided, 1);
+}
+
+__global__ void k_root_flags(int64_t n, const int* __restrict__ state, int* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (state[i] == kIn) ? 1 : 0;
+}
+
+__global__ void k_agg_pass1(int64_t n, const int* __restrict__ srp, const int* __restrict__ scol,
+                            const int* __restrict__ state, const int* __restrict__ root_id,
+                            int* __restrict__ agg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (state[i] == kIn) { agg[i] = root_id[i]; return; }
+    uint64_t best = 0;
+    int a = -1;
+    for (int p = srp[i]; p < srp[i + 1]; ++p) {
+        int j = scol[p];
+        if (state[j] != kIn) continue;
+        uint64_t k = mis_key(kIn, j);
+        if (a < 0 || k > best) { best = k; a = root_id[j]; }
+    }
+    agg[i] = a;
+}
+
+__global__ void k_agg_pass2(int64_t n, const int* __restrict__ srp, const int* __restrict__ scol,
+                            const int* __restrict__ agg1, int* __restrict__ agg2, int* status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (agg1[i] >= 0) { agg2[i] = agg1[i]; return; }
+    uint64_t best = 0;
+    int a = -1;
+    for (int p = srp[i]; p < srp[i + 1]; ++p) {
+        int j = scol[p];
+        if (agg1[j] < 0) continue;
+        uint64_t k = mis_key(kUnd, j);
+        if (a < 0 || k > best) { best = k; a = agg1[j]; }
+    }
+    agg2[i] = a;
+    if (a < 0) atomicOr(status, kDevOverflow);
+}
+
+__global__ void k_p0(int64_t n, const int* __restrict__ agg, int* __restrict__ rp,
+                     int* __restrict__ col, double* __restrict__ val) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        rp[i] = (int)i;
+        col[i] = agg[i];
+        val[i] = 1.0;
+    }
+    if (i == n) rp[n] = (int)n;
+}
+
+// P = P0 - omega D^-1 (A P0), in place on the values of A P0.
+__global__ void k_smooth_p(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                           double* __restrict__ val, const int* __restrict__ agg,
+                           const double* __restrict__ dinv, double omega) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double w = omega * dinv[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) val[p] = (col[p] == agg[i] ? 1.0 : 0.0) - w * val[p];
+}
+
+// ------------------------------------------------------------------ coarse dense inverse
+__global__ void k_csr_to_dense(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ M) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) M[i * n + col[p]] = val[p];
+}
+
+// Gauss-Jordan step k, part 1 (one block): scale pivot row, save and clear column k.
+__global__ void k_gj_pivot(int n, int k, double* __restrict__ M, double* __restrict__ f) {
+    __shared__ double piv;
+    if (threadIdx.x == 0) piv = M[(int64_t)k * n + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(int64_t)i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double v = (j == k) ? 1.0 : M[(int64_t)k * n + j];
+        M[(int64_t)k * n + j] = v / piv;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (i != k) M[(int64_t)i * n + k] = 0.0;
+}
+
+// part 2: row_i -= f_i * row_k for every i != k
+__global__ void k_gj_elim(int n, int k, double* __restrict__ M, const double* __restrict__ f) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    int i = (int)(t / n), j = (int)(t % n);
+    if (i == k) return;
+    M[t] -= f[i] * M[(int64_t)k * n + j];
+}
+
+// x = Minv b, one warp per row
+__global__ void k_dense_mv(int n, const double* __restrict__ M, const double* __restrict__ b,
+                           double* __restrict__ x) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += M[row * n + j] * b[j];
+    acc = warp_sum(acc);
+    if (lane == 0) x[row] = acc;
+}
+
+inline int sgrid(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 8 * kSMs); }
+
+void check_dev(DBuf<int>& st, cudaStream_t s, HostScratch& hs, const char* what) {
+    int v = read_scalar(st.get(), s, hs);
+    if (v) fail(DPP_ERR_INVALID_ARGUMENT, std::string("AMG setup: ") + what);
+}
+
+double power_lmax(const Csr& A, const double* dinv, int lanes, cudaStream_t s, HostScratch& hs) {
+    const int64_t n = A.n_rows;
+    DBuf<double> v(n), w(n), nrm(2);
+    const int B = 256;
+    k_hash_vector<<<grid_for(n, B), B, 0, s>>>(n, v.get());
+    DPP_LAUNCH_CK();
+    Reducer R;
+    double lam = 0.0;
+    for (int it = 0; it < 15; ++it) {
+        dot(R, v.get(), v.get(), n, nrm.get() + 1, s);
+        spmv_lanes<0>(lanes, A, v.get(), nullptr, w.get(), s);
+        k_dinv_scale<<<sgrid(n), 256, 0, s>>>(n, dinv, w.get());
+        DPP_LAUNCH_CK();
+        dot(R, w.get(), w.get(), n, nrm.get(), s);
+        double* h = (double*)hs.get(2 * sizeof(double));
+        DPP_CK(cudaMemcpyAsync(h, nrm.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DPP_CK(cudaStreamSynchronize(s));
+        if (!(h[0] > 0.0) || !(h[1] > 0.0)) fail(DPP_ERR_NONFINITE, "AMG setup: power iteration");
+        lam = std::sqrt(h[0] / h[1]);
+        axpby(1.0 / std::sqrt(h[0]), w.get(), 0.0, v.get(), n, s);  // v = w / ||w||
+    }
+    return lam;
+}
+
+void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s) {
+    const int64_t n = A.n_rows;
+    inv.alloc(n * n);
+    DPP_CK(cudaMemsetAsync(inv.get(), 0, n * n * sizeof(double), s));
+    k_csr_to_dense<<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
+                                                    inv.get());
+    DPP_LAUNCH_CK();
+    DBuf<double> f(n);
+    for (int k = 0; k < n; ++k) {
+        k_gj_pivot<<<1, 256, 0, s>>>((int)n, k, inv.get(), f.get());
+        k_gj_elim<<<grid_for(n * n, 256), 256, 0, s>>>((int)n, k, inv.get(), f.get());
+    }
+    DPP_LAUNCH_CK();
+    DPP_CK(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
+    auto& hs = pc.hs;
+    const dpp_pc_opts& o = pc.opts;
+    pc.levels.clear();
+    pc.levels.emplace_back();
+    pc.levels[0].A = std::move(A0);
+    DBuf<int> st(1);
+    const int B = 256;
+    for (int l = 0;; ++l) {
+        Level& L = pc.levels[l];
+        const int64_t n = L.A.n_rows;
+        L.lanes = pick_lanes(L.A);
+        L.dinv.alloc(n);
+        DBuf<double> dabs(n);
+        DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
+        k_diag_inv<<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(), L.A.val.get(),
+                                                L.dinv.get(), dabs.get(), st.get());
+        DPP_LAUNCH_CK();
+        check_dev(st, s, hs, "a level matrix has a non-positive diagonal entry");
+        L.lmax = power_lmax(L.A, L.dinv.get(), L.lanes, s, hs);
+        L.x.alloc(n);
+        L.b.alloc(n);
+        L.r.alloc(n);
+        L.d.alloc(n);
+        const bool last = (n <= o.coarse_max_rows) || (l + 1 >= o.max_levels);
+        if (last) break;
+
+        // strength graph
+        Csr S;
+        S.n_rows = S.n_cols = n;
+        S.row_ptr.alloc(n + 1);
+        DPP_CK(cudaMemsetAsync(S.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
+        k_strength_count<<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                      L.A.val.get(), dabs.get(), o.strength_theta,
+                                                      S.row_ptr.get());
+        DPP_LAUNCH_CK();
+        S.nnz = exclusive_scan(S.row_ptr.get(), S.row_ptr.get(), n + 1, s, hs);
+        S.col.alloc(std::max<int64_t>(S.nnz, 1));
+        k_strength_fill<<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                     L.A.val.get(), dabs.get(), o.strength_theta,
+                                                     S.row_ptr.get(), S.col.get());
+        DPP_LAUNCH_CK();
+
+        // distance-2 maximal independent set
+        DBuf<int> state(n), undecided(1);
+        DBuf<uint64_t> t0(n), t1(n), t2(n);
+        k_fill_int<<<grid_for(n, B), B, 0, s>>>(n, kUnd, state.get());
+        DPP_LAUNCH_CK();
+        for (int round = 0; round < 64; ++round) {
+            DPP_CK(cudaMemsetAsync(undecided.get(), 0, sizeof(int), s));
+            k_mis_t0<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get());
+            k_mis_max<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t0.get(), t1.get());
+            k_mis_max<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t1.get(), t2.get());
+            k_mis_update<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get(), t2.get(),
+                                                      undecided.get());
+            DPP_LAUNCH_CK();
+            if (read_scalar(undecided.get(), s, hs) == 0) break;
+            if (round == 63) fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: MIS-2 did not finish");
+        }
+        DBuf<int> root_id(n + 1), agg1(n), agg(n);
+        k_root_flags<<<grid_for(n, B), B, 0, s>>>(n, state.get(), root_id.get());
+        DPP_LAUNCH_CK();
+        const int64_t n_agg = exclusive_scan(root_id.get(), root_id.get(), n + 1, s, hs);
+        k_agg_pass1<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), state.get(),
+                                                 root_id.get(), agg1.get());
+        DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
+        k_agg_pass2<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), agg1.get(),
+                                                 agg.get(), st.get());
+        DPP_LAUNCH_CK();
+        check_dev(st, s, hs, "a row was left without an aggregate");
+        if (n_agg <= 0 || n_agg >= n) break;  // no coarsening possible: this level is the last
+
+        // prolongator
+        Csr P0;
+        P0.n_rows = n;
+        P0.n_cols = n_agg;
+        P0.nnz = n;
+        P0.row_ptr.alloc(n + 1);
+        P0.col.alloc(n);
+        P0.val.alloc(n);
+        k_p0<<<grid_for(n + 1, B), B, 0, s>>>(n, agg.get(), P0.row_ptr.get(), P0.col.get(),
+                                              P0.val.get());
+        DPP_LAUNCH_CK();
+        Csr Pm;
+        spgemm(view(L.A), view(P0), Pm, true, s, hs);
+        const double omega = 4.0 / (3.0 * L.lmax);
+        k_smooth_p<<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), Pm.val.get(),
+                                                agg.get(), L.dinv.get(), omega);
+        DPP_LAUNCH_CK();
+        L.P = std::move(Pm);
+        transpose(L.P, L.R, s, hs);
+        Csr AP;
+        spgemm(view(L.A), view(L.P), AP, true, s, hs);
+        Csr Ac;
+        spgemm(view(L.R), view(AP), Ac, true, s, hs);
+        pc.levels.emplace_back();
+        pc.levels.back().A = std::move(Ac);
+    }
+    // coarse solve
+    Level& C = pc.levels.back();
+    if (C.A.n_rows > 4096)
+        fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: coarsest level has more than 4096 rows; "
+                                       "raise max_levels or lower strength_theta");
+    pc.coarse_n = C.A.n_rows;
+    dense_inverse(C.A, pc.coarse_inv, s);
+}
+
+namespace {
+
+void cheb_smooth(const PcImpl& pc, Level& L, const double* b, double* x, bool zero_init,
+                 cudaStream_t s) {
+    const int deg = std::max(1, pc.opts.cheb_degree_amg);
+    const double hi = 1.1 * L.lmax, lo = L.lmax / pc.opts.cheb_ratio;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    const int64_t n = L.A.n_rows;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < deg; ++k) {
+        if (k == 0) {
+            if (zero_init) {
+                k_cheb_update<<<sgrid(n), 256, 0, s>>>(n, L.dinv.get(), b, L.d.get(), x, 0.0,
+                                                       1.0 / theta, 1);
+            } else {
+                spmv_lanes<1>(L.lanes, L.A, x, b, L.r.get(), s);
+                k_cheb_update<<<sgrid(n), 256, 0, s>>>(n, L.dinv.get(), L.r.get(), L.d.get(), x,
+                                                       0.0, 1.0 / theta, 0);
+            }
+        } else {
+            const double rho_new = 1.0 / (2.0 * sigma - rho);
+            spmv_lanes<1>(L.lanes, L.A, x, b, L.r.get(), s);
+            k_cheb_update<<<sgrid(n), 256, 0, s>>>(n, L.dinv.get(), L.r.get(), L.d.get(), x,
+                                                   rho_new * rho, 2.0 * rho_new / delta, 0);
+            rho = rho_new;
+        }
+        DPP_LAUNCH_CK();
+    }
+}
+
+void vcycle_level(PcImpl& pc, size_t l, const double* b, double* x, cudaStream_t s) {
+    Level& L = pc.levels[l];
+    if (l + 1 == pc.levels.size()) {
+        const int n = (int)pc.coarse_n;
+        k_dense_mv<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, pc.coarse_inv.get(), b, x);
+        DPP_LAUNCH_CK();
+        return;
+    }
+    Level& C = pc.levels[l + 1];
+    cheb_smooth(pc, L, b, x, true, s);
+    spmv_lanes<1>(L.lanes, L.A, x, b, L.r.get(), s);
+    spmv_lanes<0>(pick_lanes(L.R), L.R, L.r.get(), nullptr, C.b.get(), s);
+    vcycle_level(pc, l + 1, C.b.get(), C.x.get(), s);
+    spmv_lanes<2>(pick_lanes(L.P), L.P, C.x.get(), nullptr, x, s);
+    cheb_smooth(pc, L, b, x, false, s);
+}
+
+}  // namespace
+
+void amg_vcycle(PcImpl& pc, const double* b, double* x, cudaStream_t s) {
+    vcycle_level(pc, 0, b, x, s);
+}
+
+}  // namespace dpp

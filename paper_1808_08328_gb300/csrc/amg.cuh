@@ -1,0 +1,38 @@
+// Preconditioner-setup and AMG interfaces shared between translation units.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace dpp {
+
+// Non-owning view of a CSR matrix.
+struct CsrView {
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    const int* rp = nullptr;
+    const int* col = nullptr;
+    const double* val = nullptr;
+};
+inline CsrView view(const Csr& A) {
+    CsrView v;
+    v.n_rows = A.n_rows;
+    v.n_cols = A.n_cols;
+    v.nnz = A.nnz;
+    v.rp = A.row_ptr.get();
+    v.col = A.col.get();
+    v.val = A.val.get();
+    return v;
+}
+
+// C = A B (sorted columns in every row of B are required and produced in C).
+void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
+            HostScratch& hs);
+void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs);
+// blockdiag(S_p1, S_p2) from the pair values and mdiag = 1/diag(K_uu) per network.
+void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
+                 HostScratch& hs);
+
+void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s);
+// x = (one V-cycle) b on level 0; b is not modified.
+void amg_vcycle(PcImpl& pc, const double* b, double* x, cudaStream_t s);
+
+}  // namespace dpp

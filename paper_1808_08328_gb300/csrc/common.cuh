@@ -1,0 +1,145 @@
+// Internal helpers shared by the libdpp translation units: error handling,
+// device buffers, launch geometry and warp/block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/dpp.h"
+
+namespace dpp {
+
+// Exceptions are the internal error path; every extern "C" entry point catches
+// them and turns them into a dpp_status plus a thread-local message.
+struct Error : std::runtime_error {
+    dpp_status status;
+    Error(dpp_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define DPP_CK(call)                                                                    \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            throw ::dpp::Error(e_ == cudaErrorMemoryAllocation ? DPP_ERR_OUT_OF_MEMORY  \
+                                                               : DPP_ERR_CUDA,          \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));     \
+        }                                                                               \
+    } while (0)
+
+#define DPP_LAUNCH_CK() DPP_CK(cudaGetLastError())
+
+inline void fail(dpp_status s, const std::string& m) { throw Error(s, m); }
+
+// Owning device buffer. Freed with cudaFree (a device-wide sync point), which
+// only happens in dpp_destroy_* and on error paths.
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    explicit DBuf(size_t count) { alloc(count); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) DPP_CK(cudaMalloc(&p, count * sizeof(T)));
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    T* get() const { return p; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// Pinned host scratch for small device->host reads.
+struct HostScratch {
+    void* p = nullptr;
+    size_t cap = 0;
+    void* get(size_t bytes) {
+        if (bytes > cap) {
+            if (p) cudaFreeHost(p);
+            DPP_CK(cudaMallocHost(&p, bytes));
+            cap = bytes;
+        }
+        return p;
+    }
+    ~HostScratch() { if (p) cudaFreeHost(p); }
+};
+
+constexpr int kSMs = 152;        // GB300: 2 dies x 76 SMs
+constexpr int kSell = 32;        // SELL slice height = one warp
+
+inline int grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > (1LL << 30)) g = (1LL << 30);
+    return (int)g;
+}
+
+// Device status word codes (OR-ed by validation kernels).
+enum : int {
+    kDevOk = 0,
+    kDevBadIndex = 1,
+    kDevNonFinite = 2,
+    kDevDegenerate = 4,
+    kDevOverflow = 8,     // a per-node list exceeded its compile-time bound
+    kDevNoOwner = 16,     // a boundary facet is not a face of any cell
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum, result valid in thread 0. `sh` needs blockDim/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+// ------------------------------------------------------------------ host helpers
+
+// Exclusive prefix sum of n ints (in may alias out); returns the total.
+int64_t exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t s, HostScratch& hs);
+// Read one device value.
+template <class T>
+T read_scalar(const T* d, cudaStream_t s, HostScratch& hs) {
+    T* h = (T*)hs.get(sizeof(T));
+    DPP_CK(cudaMemcpyAsync(h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaStreamSynchronize(s));
+    return *h;
+}
+
+}  // namespace dpp

@@ -1,0 +1,88 @@
+// Library-internal data structures behind the opaque dpp_problem / dpp_pc handles.
+#pragma once
+
+#include "common.cuh"
+
+namespace dpp {
+
+// Per-cell geometry record: |K| then the d+1 constant gradients of the P1
+// barycentric basis, padded to a power of two.
+template <int DIM> struct GeoLayout;
+template <> struct GeoLayout<2> { static constexpr int stride = 8; };
+template <> struct GeoLayout<3> { static constexpr int stride = 16; };
+
+// Values stored per node pair (a, b): m1, m2, Kup[d], Kpu[d], d1, d2, e.
+__host__ __device__ constexpr int pair_values(int dim) { return 2 + 2 * dim + 3; }
+
+// Scalar CSR matrix (AMG levels, S_p, P, R).
+struct Csr {
+    int64_t n_rows = 0, n_cols = 0, nnz = 0;
+    DBuf<int> row_ptr, col;
+    DBuf<double> val;
+    DBuf<float> val32;
+};
+
+struct ProblemImpl {
+    int dim = 0, ns = 0, nv = 0;  // dimension, DoF per node (2d+2), values per pair
+    int64_t n_nodes = 0, n_cells = 0, n_bfacets = 0, n_pairs = 0;
+    double mu = 1, beta = 0, gb[3] = {0, 0, 0};
+    int precision = DPP_FP64;
+
+    DBuf<double> coords, logk1, logk2, p01, p02;
+    DBuf<int> cells, bfacets;
+    DBuf<int> nc_ptr, nc_list;   // node -> incident cells (sorted)
+    DBuf<int> nf_ptr, nf_list;   // node -> incident boundary facets (sorted)
+    DBuf<double> facet_nA;       // [n_bfacets][dim]: |F| times the outward unit normal
+    DBuf<int> row_ptr, col, pair_row;  // node-pair CSR (self pairs included, columns sorted)
+
+    // SELL-32 storage of the pair values: slice s holds rows 32s..32s+31,
+    // groups slice_ptr[s]..slice_ptr[s+1]-1, one group per column slot.
+    int64_t n_slices = 0, n_groups = 0;
+    DBuf<int> slice_ptr;    // [n_slices+1]
+    DBuf<int> sell_col;     // [n_groups][32], -1 = padding
+    DBuf<double> sell_val;  // [n_groups][nv][32]
+    DBuf<float> sell_val32; // FP32 copy (mixed precision)
+
+    DBuf<double> geo;       // [n_cells][GeoLayout<dim>::stride]
+    DBuf<double> kk;        // [n_cells][2]: k1, k2
+    DBuf<double> f;         // [n_nodes][ns]
+    DBuf<int> dstatus;      // device status word
+    HostScratch hs;
+    double ms_assemble = 0;
+};
+
+// One level of the AMG hierarchy on blockdiag(S_p1, S_p2).
+struct Level {
+    Csr A;            // level matrix
+    Csr P, R;         // prolongator to this level from the next coarser, and R = P^T
+    DBuf<double> dinv;        // 1 / diag(A)
+    DBuf<float> dinv32;
+    double lmax = 0;          // estimate of the largest eigenvalue of D^-1 A
+    int lanes = 4;            // CSR SpMV lanes per row
+    // V-cycle work vectors (length n_rows)
+    DBuf<double> x, b, r, d;
+    DBuf<float> x32, b32, r32, d32;
+};
+
+struct PcImpl {
+    int dim = 0;
+    int64_t n_nodes = 0;
+    int precision = DPP_FP64;
+    dpp_pc_opts opts{};
+    double mass_lmin = 0.5, mass_lmax = 2.0;  // Wathen bounds of D^-1 M (TRI: [1/2, 2], TET: [1/2, 5/2])
+    std::vector<Level> levels;
+    DBuf<double> coarse_inv;  // dense inverse of the coarsest matrix, row-major
+    DBuf<float> coarse_inv32;
+    int64_t coarse_n = 0;
+    // preconditioner work vectors (node-interleaved, n_nodes * ns)
+    DBuf<double> yu, su, tmp, dcheb;
+    DBuf<double> tp, yp;      // split pressures [2][n_nodes]
+    DBuf<double> mdiag;       // [n_nodes][2]: 1/m1_aa, 1/m2_aa (mass Jacobi)
+    HostScratch hs;
+    double ms_setup = 0;
+};
+
+}  // namespace dpp
+
+struct dpp_problem_s { dpp::ProblemImpl impl; };
+struct dpp_pc_s { dpp::PcImpl impl; const dpp_problem_s* owner = nullptr; };
