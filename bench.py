@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput of the DPP solver path on GB300: DoF/s to relative residual 1e-10.
+
+One step = dpp_assemble (CG-VMS P1 K and f) + dpp_setup_pc (selfp Schur blocks and
+SA-AMG hierarchy) + dpp_solve (field-split preconditioned FGMRES to a true FP64
+relative residual of 1e-10). It runs on the 3D workload: a 64^3-cube unit-cube
+mesh with 6 Kuhn tetrahedra per cube (274,625 nodes, 2,197,000 DoF), seeded
+i.i.d. per-cell log k1 ~ N(0,1) and log k2 ~ N(-3,1), mu = beta = 1, and
+pressure data from the paper's 3D manufactured solution. Inputs are resident in
+HBM when the timed region starts. The working set (pair values 354 MB,
+hierarchy, Krylov basis) is far larger than L2, so no flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(``scaling: weak``); the solve has no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF/s to rel. residual 1e-10"
+WORKLOADS = {
+    # name: (dim, n, seed, beta, description)
+    "3d64_lognormal_fp64": (3, 64, 0, 1.0, "3D unit cube 64^3 x 6 Kuhn tets, log k1~N(0,1), "
+                                           "log k2~N(-3,1), mu=beta=1, FP64 field-split+SA-AMG FGMRES"),
+    "2d32_mms_fp64": (2, 32, 0, 1.0, "2D unit square 32x32 x 2 tris, homogeneous k1=1 k2=0.1, MMS data"),
+    "3d32_lognormal_fp64": (3, 32, 0, 1.0, "3D unit cube 32^3 x 6 Kuhn tets, log-normal k"),
+    "3d48_lognormal_fp64": (3, 48, 0, 1.0, "3D unit cube 48^3 x 6 Kuhn tets, log-normal k "
+                                           "(profiling size: pair values 160 MB > L2)"),
+}
+CPU_SAMPLE = (3, 12, 0, 1.0)   # the oracle's bounded sample of the same recipe: 3D 12^3 cubes
+
+
+def make_problem(spec):
+    import inputs
+    dim, n, seed, beta = spec[:4]
+    if dim == 2:
+        return inputs.mms_problem(2, n)
+    return inputs.heterogeneous_problem(dim, n, seed=seed, beta=beta)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import inputs, oracle
+from oracle.assembly import assemble_problem
+dim, n, seed, beta = {spec!r}
+P = inputs.heterogeneous_problem(dim, n, seed=seed, beta=beta) if dim == 3 else inputs.mms_problem(2, n)
+reps, t_tot, steps = {reps}, 0.0, 0
+res = None
+while steps < reps:
+    t0 = time.perf_counter()
+    K, f = assemble_problem(P)
+    x = oracle.solve_direct(K, f, coords=P.mesh.coords)
+    t_tot += time.perf_counter() - t0
+    steps += 1
+    res = oracle.residual(K, x, f)
+    if t_tot > {budget}:
+        break
+print(json.dumps({{"dofs": P.n_dofs, "steps": steps, "seconds": t_tot, "residual": res}}))
+"""
+
+
+def run_oracle(spec, reps, budget):
+    """Time the oracle (assembly + direct solve) in a single-threaded child process."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = _ORACLE_SNIPPET.format(root=ROOT, spec=tuple(spec[:4]), reps=reps, budget=budget)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["dof_per_s"] = out["dofs"] * out["steps"] / out["seconds"]
+    return out
+
+
+def cpu_baseline_block(out, spec):
+    dim, n = spec[:2]
+    return {"value": out["dof_per_s"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{out['steps']} x (numpy CG-VMS assembly + SuperLU nested-dissection solve) "
+                      f"on the same recipe at {n}^{dim} cubes ({out['dofs']} DoF), "
+                      f"{out['seconds']:.1f} s, single-threaded BLAS"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if uuid:
+                cmd += ["-i", uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(family: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+        e = t.get(family)
+        if not e:
+            return None
+        src = os.path.join(ROOT, e["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != e["source_sha"]:
+            return None
+        return e["dram_bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- arms
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    out = run_oracle(CPU_SAMPLE, reps=args.steps + args.warmup, budget=240.0)
+    steps = out["steps"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": out["dof_per_s"], "unit": "DoF/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": 0,
+        "ms_per_step": 1000.0 * out["seconds"] / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_dofs": out["dofs"]},
+        "cpu_baseline": cpu_baseline_block(out, CPU_SAMPLE),
+        "e2e": {"value": out["dof_per_s"], "unit": "DoF/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def bench_gb300(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    spec = WORKLOADS[args.workload]
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = run_oracle(CPU_SAMPLE, reps=3, budget=20.0)   # before any GPU call
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_1808_08328_gb300 import binding as B
+    from paper_1808_08328_gb300.system import DPPSystem
+
+    P = make_problem(spec)
+    dofs = P.n_dofs
+    dev = torch.device("cuda", local)
+    # device-resident inputs (the descriptor of a DPPSystem without assembling it twice)
+    sysm = DPPSystem.from_problem(P, device=dev)
+    desc = sysm.desc
+    B.dpp_destroy_problem(sysm.prob)
+    sysm.prob = 0
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    pc_opts = B.dpp_pc_opts_default()
+    s_opts = B.dpp_solve_opts_default()
+    s_opts.rtol = 1e-10
+    x = torch.zeros((P.mesh.n_nodes, P.mesh.dofs_per_node), dtype=torch.float64, device=dev)
+
+    def step(d=desc, xv=x, so=s_opts):
+        prob = B.dpp_assemble(d, B.DPP_FP64, stream)
+        pc = B.dpp_setup_pc(prob, pc_opts, stream)
+        info = B.dpp_solve(prob, pc, so, xv, stream)
+        B.dpp_destroy_pc(pc)
+        B.dpp_destroy_problem(prob)
+        return info
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    B.dpp_profile_enable(True)
+    l0 = B.dpp_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream(dev))
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = B.dpp_launch_count() - l0
+    fam = {f: B.dpp_profile_read(f) for f in ("apply_K", "amg_csr_spmv", "mass_cheb")}
+    B.dpp_profile_enable(False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in {
+            "coords": P.mesh.coords, "cells": P.mesh.cells, "bfacets": P.mesh.bfacets,
+            "log_k1": P.logk1, "log_k2": P.logk2, "p01": P.p01, "p02": P.p02}.items()}
+        hd = B.dpp_problem_desc()
+        for f_, _t in hd._fields_:
+            if f_ != "gamma_b":
+                setattr(hd, f_, getattr(desc, f_))
+        for k in range(3):
+            hd.gamma_b[k] = desc.gamma_b[k]
+        hd.memory = B.DPP_MEM_HOST
+        for k, v in host.items():
+            setattr(hd, k, v.data_ptr())
+        xh = torch.zeros(x.shape, dtype=torch.float64).pin_memory()
+        so = B.dpp_solve_opts_default()
+        so.rtol = 1e-10
+        so.x_memory = B.DPP_MEM_HOST
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = xh.numel() * xh.element_size()
+        step(hd, xh.data_ptr(), so)  # warm
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(hd, xh.data_ptr(), so)
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * dofs * args.steps / te, "unit": "DoF/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    dom = max(fam, key=lambda f: fam[f]["ms"])
+    d = fam[dom]
+    achieved = d["alg_bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    traffic = ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_kind": peak_kind,
+                "traffic": traffic, "alg_bytes_per_launch": d["alg_bytes"] / max(d["launches"], 1),
+                "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1)}
+    kernels = {f: {"launches": v["launches"], "ms": v["ms"],
+                   "gbs": (v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else None)}
+               for f, v in fam.items()}
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": world * dofs * args.steps / (ms * 1e-3), "unit": "DoF/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "dofs": dofs, "description": spec[4],
+                   "rtol": 1e-10, "step": "assemble+setup_pc+solve",
+                   "l2": "working set larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": e2e, "roofline": roofline,
+        "cpu_baseline": cpu_baseline_block(cpu, CPU_SAMPLE) if cpu else None,
+        "clocks": clk, "gpu_launches": launches,
+        "solve": {"iterations": last.iterations, "rel_residual": last.rel_residual,
+                  "levels": last.levels, "ms_assemble": last.ms_assemble,
+                  "ms_setup": last.ms_setup, "ms_solve": last.ms_solve,
+                  "setup_solve_dof_per_s": dofs / ((last.ms_setup + last.ms_solve) * 1e-3)},
+        "kernels": kernels,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="3d64_lognormal_fp64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

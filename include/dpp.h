@@ -218,6 +218,26 @@ dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32
                                double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
                                dpp_stream_t stream);
 
+/* ---------------- instrumentation (no counterpart in the paper) ---------------- */
+
+/* Number of kernels this library has launched since it was loaded (every
+ * launch site is counted once). */
+int64_t dpp_launch_count(void);
+
+/* Enable (on != 0) or disable per-family CUDA-event timing and reset the
+ * records. When enabled, the library records a start and a stop event on the
+ * launching stream around every launch of the timed families: "apply_K",
+ * "apply_K_fp32", "mass_cheb" and "amg_csr_spmv". For each such launch it also
+ * accumulates the algorithmic bytes: every matrix value, index and vector
+ * entry, counted once. Timing adds a few microseconds of host work per launch. */
+dpp_status dpp_profile_enable(int32_t on);
+
+/* Totals for one family since the last dpp_profile_enable: launches, device
+ * milliseconds (summed event intervals, synchronising on them), algorithmic
+ * bytes. An unknown family gives zeros. */
+dpp_status dpp_profile_read(const char* family, int64_t* launches, double* total_ms,
+                            double* alg_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,10 @@ _SIGS = {
     "dpp_pc_apply": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "dpp_pc_level_sizes": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64)]),
     "dpp_pc_export_level": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    "dpp_launch_count": (C.c_int64, []),
+    "dpp_profile_enable": (C.c_int, [C.c_int32]),
+    "dpp_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -243,3 +247,19 @@ def dpp_pc_export_level(pc: int, level: int, row_ptr, col, val, p_row_ptr=None, 
                         p_val=None, stream: int = 0) -> None:
     _check(load().dpp_pc_export_level(pc, level, _ptr(row_ptr), _ptr(col), _ptr(val),
                                       _ptr(p_row_ptr), _ptr(p_col), _ptr(p_val), stream or None))
+
+
+def dpp_launch_count() -> int:
+    return int(load().dpp_launch_count())
+
+
+def dpp_profile_enable(on: bool) -> None:
+    _check(load().dpp_profile_enable(1 if on else 0))
+
+
+def dpp_profile_read(family: str) -> dict:
+    n = C.c_int64()
+    ms = C.c_double()
+    by = C.c_double()
+    _check(load().dpp_profile_read(family.encode(), C.byref(n), C.byref(ms), C.byref(by)))
+    return {"launches": n.value, "ms": ms.value, "alg_bytes": by.value}

@@ -2,7 +2,10 @@
 // validates its arguments on the host, runs its work on the caller's stream,
 // and converts internal exceptions into a dpp_status plus a thread-local
 // message. Nothing here aborts, exits or traps.
+#include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "amg.cuh"
@@ -16,6 +19,30 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
                   HostScratch& hs);
 void adjoint_gradients(const ProblemImpl& P, const double* x, const double* lambda, double* g1,
                        double* g2, double* gbeta, cudaStream_t s);
+}  // namespace dpp
+
+namespace dpp {
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_profiling{false};
+struct Family {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    double bytes = 0;
+};
+std::mutex g_prof_mu;
+std::map<std::string, Family> g_prof;
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool profiling_enabled() { return g_profiling.load(std::memory_order_relaxed); }
+void profile_record(const char* family, cudaEvent_t a, cudaEvent_t b, double bytes) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    auto& f = g_prof[family];
+    f.events.emplace_back(a, b);
+    f.bytes += bytes;
+}
+
 }  // namespace dpp
 
 using namespace dpp;
@@ -384,6 +411,50 @@ dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32
                                    cudaMemcpyDeviceToDevice, s));
         }
         DPP_CK(cudaStreamSynchronize(s));
+        return DPP_OK;
+    });
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int64_t dpp_launch_count(void) { return g_launches.load(); }
+
+dpp_status dpp_profile_enable(int32_t on) {
+    return guarded("dpp_profile_enable", [&]() -> dpp_status {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        for (auto& kv : g_prof)
+            for (auto& e : kv.second.events) {
+                cudaEventDestroy(e.first);
+                cudaEventDestroy(e.second);
+            }
+        g_prof.clear();
+        g_profiling.store(on != 0);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_profile_read(const char* family, int64_t* launches, double* total_ms,
+                            double* alg_bytes) {
+    return guarded("dpp_profile_read", [&]() -> dpp_status {
+        require(family && launches && total_ms && alg_bytes, "null argument");
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        *launches = 0;
+        *total_ms = 0;
+        *alg_bytes = 0;
+        auto it = g_prof.find(family);
+        if (it == g_prof.end()) return DPP_OK;
+        double ms = 0;
+        for (auto& e : it->second.events) {
+            DPP_CK(cudaEventSynchronize(e.second));
+            float t = 0;
+            DPP_CK(cudaEventElapsedTime(&t, e.first, e.second));
+            ms += t;
+        }
+        *launches = (int64_t)it->second.events.size();
+        *total_ms = ms;
+        *alg_bytes = it->second.bytes;
         return DPP_OK;
     });
 }

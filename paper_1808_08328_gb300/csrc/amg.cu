@@ -60,6 +60,9 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
 template <int MODE>
 void spmv_lanes(int lanes, const Csr& A, const double* x, const double* b, double* y,
                 cudaStream_t s) {
+    const double alg = (double)A.nnz * 12.0 + (double)(A.n_rows + 1) * 4.0 +
+                       (double)A.n_cols * 8.0 + (double)A.n_rows * 8.0 * (MODE == 0 ? 1 : 2);
+    ProfScope prof("amg_csr_spmv", s, alg);
     const int B = 256;
     const int64_t thr = A.n_rows * lanes;
     const int g = grid_for(thr, B);
@@ -345,9 +348,10 @@ void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s) {
     DBuf<double> f(n);
     for (int k = 0; k < n; ++k) {
         k_gj_pivot<<<1, 256, 0, s>>>((int)n, k, inv.get(), f.get());
+        DPP_LAUNCH_CK();
         k_gj_elim<<<grid_for(n * n, 256), 256, 0, s>>>((int)n, k, inv.get(), f.get());
+        DPP_LAUNCH_CK();
     }
-    DPP_LAUNCH_CK();
     DPP_CK(cudaStreamSynchronize(s));
 }
 
@@ -404,8 +408,11 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         for (int round = 0; round < 64; ++round) {
             DPP_CK(cudaMemsetAsync(undecided.get(), 0, sizeof(int), s));
             k_mis_t0<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get());
+            DPP_LAUNCH_CK();
             k_mis_max<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t0.get(), t1.get());
+            DPP_LAUNCH_CK();
             k_mis_max<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t1.get(), t2.get());
+            DPP_LAUNCH_CK();
             k_mis_update<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get(), t2.get(),
                                                       undecided.get());
             DPP_LAUNCH_CK();
@@ -418,6 +425,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         const int64_t n_agg = exclusive_scan(root_id.get(), root_id.get(), n + 1, s, hs);
         k_agg_pass1<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), state.get(),
                                                  root_id.get(), agg1.get());
+        DPP_LAUNCH_CK();
         DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
         k_agg_pass2<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), agg1.get(),
                                                  agg.get(), st.get());

@@ -31,9 +31,40 @@ struct Error : std::runtime_error {
         }                                                                               \
     } while (0)
 
-#define DPP_LAUNCH_CK() DPP_CK(cudaGetLastError())
+// Checks the launch just issued and counts it (see dpp_launch_count).
+#define DPP_LAUNCH_CK()                       \
+    do {                                      \
+        DPP_CK(cudaGetLastError());           \
+        ::dpp::count_launch();                \
+    } while (0)
 
 inline void fail(dpp_status s, const std::string& m) { throw Error(s, m); }
+
+// Launch accounting and optional per-family CUDA-event timing (abi.cu).
+void count_launch();
+bool profiling_enabled();
+void profile_record(const char* family, cudaEvent_t start, cudaEvent_t stop, double alg_bytes);
+
+// Times everything issued on `s` inside its scope when profiling is enabled.
+struct ProfScope {
+    const char* fam = nullptr;
+    cudaStream_t s = nullptr;
+    double bytes = 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(const char* family, cudaStream_t st, double alg_bytes) {
+        if (!profiling_enabled()) return;
+        fam = family;
+        s = st;
+        bytes = alg_bytes;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { fam = nullptr; return; }
+        cudaEventRecord(a, s);
+    }
+    ~ProfScope() {
+        if (!fam) return;
+        cudaEventRecord(b, s);
+        profile_record(fam, a, b, bytes);
+    }
+};
 
 // Owning device buffer. Freed with cudaFree (a device-wide sync point), which
 // only happens in dpp_destroy_* and on error paths.

@@ -266,6 +266,10 @@ __global__ void k_scatter_p(int64_t n_rows, const double* __restrict__ yp, doubl
 template <int DIM, class VT>
 void apply_K_t(const ProblemImpl& P, const VT* val, const double* x, double* y, const double* b,
                bool tr, cudaStream_t s) {
+    // algorithmic bytes: every pair's values and column once, x and y once (b once if given)
+    const double vecb = (double)P.n_nodes * P.ns * 8.0;
+    const double alg = (double)P.n_pairs * (P.nv * (double)sizeof(VT) + 4.0) + vecb * (b ? 3 : 2);
+    ProfScope prof(sizeof(VT) == 8 ? "apply_K" : "apply_K_fp32", s, alg);
     const int B = 128;
     const int grid = grid_for(P.n_slices * kSell, B);
     if (tr) {
@@ -312,6 +316,10 @@ template <> const float* vals_of<float>(const ProblemImpl& P) { return P.sell_va
 void mass_cheb_step(const ProblemImpl& P, const double* mdiag, const double* r, const double* xin,
                     double* xout, double* d, double c1, double c2, bool first, bool use32,
                     cudaStream_t s) {
+    const double vecb = (double)P.n_nodes * P.ns * 8.0;
+    const double alg = first ? 3 * vecb
+                             : (double)P.n_pairs * (2.0 * (use32 ? 4 : 8) + 4.0) + 5 * vecb;
+    ProfScope prof("mass_cheb", s, alg);
     const int B = 128;
     const int grid = grid_for(P.n_slices * kSell, B);
     DPP_DISPATCH_DV(P.dim, use32,
