@@ -218,6 +218,31 @@ dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32
                                double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
                                dpp_stream_t stream);
 
+/*
+ * Allocation-free variant of the adjoint's sensitivity step. The paper has no
+ * counterpart; this is an interface for callers that cannot allocate device
+ * memory. Examples: a custom call inside an XLA/JAX or TensorFlow graph, or a
+ * process whose device memory another framework's pool has already reserved.
+ * For them cudaMalloc/cudaFree would synchronise the device, bypass the owning
+ * pool, or fail.
+ * Given the forward solution x and the adjoint lambda (device, [n_nodes][2d+2])
+ * of an assembled problem, it writes the same dJ_dlogk1 [n_cells], dJ_dlogk2
+ * [n_cells] and dJ_dbeta [1] (all device) as dpp_adjoint_solve does after its
+ * transpose solve. It allocates nothing. Its scratch is one fixed array in the
+ * library (16384 doubles, 128 KiB on each GPU that loads the library, kept
+ * until the process exits), so n_cells must be at most 4,194,304. Larger
+ * meshes return DPP_ERR_INVALID_ARGUMENT. The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture. Every call
+ * overwrites the part of the array it uses before reading it, so no state
+ * carries over. Calls that overlap on the GPU share the array and race: order
+ * them on one stream. The work is queued on `stream`, and the call returns
+ * without waiting for it.
+ */
+dpp_status dpp_adjoint_gradients_noalloc(dpp_problem prob, const double* x, const double* lambda,
+                                         double* dJ_dlogk1, double* dJ_dlogk2, double* dJ_dbeta,
+                                         dpp_stream_t stream);
+
 /* ---------------- instrumentation (no counterpart in the paper) ---------------- */
 
 /* Number of kernels this library has launched since it was loaded (every

@@ -95,6 +95,7 @@ _SIGS = {
     "dpp_pc_apply": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "dpp_pc_level_sizes": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64)]),
     "dpp_pc_export_level": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    "dpp_adjoint_gradients_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "dpp_launch_count": (C.c_int64, []),
     "dpp_profile_enable": (C.c_int, [C.c_int32]),
     "dpp_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -247,6 +248,12 @@ def dpp_pc_export_level(pc: int, level: int, row_ptr, col, val, p_row_ptr=None, 
                         p_val=None, stream: int = 0) -> None:
     _check(load().dpp_pc_export_level(pc, level, _ptr(row_ptr), _ptr(col), _ptr(val),
                                       _ptr(p_row_ptr), _ptr(p_col), _ptr(p_val), stream or None))
+
+
+def dpp_adjoint_gradients_noalloc(prob: int, x, lam, g1, g2, gb, stream: int = 0) -> None:
+    """Adjoint sensitivities with no device allocation (fixed library scratch)."""
+    _check(load().dpp_adjoint_gradients_noalloc(prob, _ptr(x), _ptr(lam), _ptr(g1), _ptr(g2),
+                                                _ptr(gb), stream or None))
 
 
 def dpp_launch_count() -> int:

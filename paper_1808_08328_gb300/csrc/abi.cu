@@ -35,6 +35,7 @@ std::map<std::string, Family> g_prof;
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error_message(const char* m);
 bool profiling_enabled() { return g_profiling.load(std::memory_order_relaxed); }
 void profile_record(const char* family, cudaEvent_t a, cudaEvent_t b, double bytes) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -111,6 +112,10 @@ struct EventTimer {
 };
 
 }  // namespace
+
+namespace dpp {
+void set_last_error_message(const char* m) { g_last_error = m ? m : ""; }
+}  // namespace dpp
 
 extern "C" {
 
