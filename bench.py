@@ -263,6 +263,10 @@ def bench_gb300(args):
     ms = e0.elapsed_time(e1)
     launches = B.dpp_launch_count() - l0
     fam = {f: B.dpp_profile_read(f) for f in ("apply_K", "amg_csr_spmv", "mass_cheb")}
+    phases = {f: B.dpp_profile_read(f)["ms"] / args.steps
+              for f in ("assemble", "setup_selfp", "setup_amg", "setup_power", "setup_aggregate",
+                        "setup_prolong_rap", "setup_coarse_inverse", "spgemm_numeric",
+                        "spgemm_pattern", "spgemm_alloc", "spgemm_fill", "spgemm_fill_pattern")}
     B.dpp_profile_enable(False)
     clk = clocks.stop()
     if dist:
@@ -342,7 +346,7 @@ def bench_gb300(args):
                   "levels": last.levels, "ms_assemble": last.ms_assemble,
                   "ms_setup": last.ms_setup, "ms_solve": last.ms_solve,
                   "setup_solve_dof_per_s": dofs / ((last.ms_setup + last.ms_solve) * 1e-3)},
-        "kernels": kernels,
+        "kernels": kernels, "phases_ms_per_step": phases,
     }
     print(json.dumps(line))
     if dist:

@@ -181,6 +181,7 @@ dpp_status dpp_assemble(const dpp_problem_desc* d, int32_t precision, dpp_stream
         auto* h = new dpp_problem_s();
         try {
             EventTimer t(s);
+            ProfScope pr("assemble", s, 0);
             h->impl.precision = precision;
             assemble_problem(h->impl, *d, s);
             h->impl.ms_assemble = t.stop();

@@ -126,6 +126,15 @@ __global__ void k_fill_int(int64_t n, int v, int* __restrict__ x) {
     if (i < n) x[i] = v;
 }
 
+// y = x / sqrt(*nrm2)
+__global__ void k_scale_rsqrt(int64_t n, const double* __restrict__ x, double* __restrict__ y,
+                              const double* __restrict__ nrm2) {
+    const double a = 1.0 / sqrt(*nrm2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        y[i] = a * x[i];
+}
+
 __global__ void k_dinv_scale(int64_t n, const double* __restrict__ dinv, double* __restrict__ v) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -203,9 +212,11 @@ __global__ void k_mis_update(int64_t n, int* __restrict__ state, const uint64_t*
     else atomicAdd(undecided, 1);
 }
 
+// flag[0..n) = root indicator, flag[n] = 0 (the scan below runs over n + 1 entries)
 __global__ void k_root_flags(int64_t n, const int* __restrict__ state, int* __restrict__ flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) flag[i] = (state[i] == kIn) ? 1 : 0;
+    if (i == n) flag[n] = 0;
 }
 
 __global__ void k_agg_pass1(int64_t n, const int* __restrict__ srp, const int* __restrict__ scol,
@@ -314,28 +325,29 @@ void check_dev(DBuf<int>& st, cudaStream_t s, HostScratch& hs, const char* what)
     if (v) fail(DPP_ERR_INVALID_ARGUMENT, std::string("AMG setup: ") + what);
 }
 
+// lambda_max(D^-1 A) by 15 power steps; the vector is renormalised on the
+// device (no host round trip per step) and the estimate read once at the end.
 double power_lmax(const Csr& A, const double* dinv, int lanes, cudaStream_t s, HostScratch& hs) {
     const int64_t n = A.n_rows;
-    DBuf<double> v(n), w(n), nrm(2);
+    DBuf<double> v(n), w(n), nrm(1);
     const int B = 256;
     k_hash_vector<<<grid_for(n, B), B, 0, s>>>(n, v.get());
     DPP_LAUNCH_CK();
     Reducer R;
-    double lam = 0.0;
+    dot(R, v.get(), v.get(), n, nrm.get(), s);
+    k_scale_rsqrt<<<sgrid(n), 256, 0, s>>>(n, v.get(), v.get(), nrm.get());
+    DPP_LAUNCH_CK();
     for (int it = 0; it < 15; ++it) {
-        dot(R, v.get(), v.get(), n, nrm.get() + 1, s);
         spmv_lanes<0>(lanes, A, v.get(), nullptr, w.get(), s);
         k_dinv_scale<<<sgrid(n), 256, 0, s>>>(n, dinv, w.get());
         DPP_LAUNCH_CK();
-        dot(R, w.get(), w.get(), n, nrm.get(), s);
-        double* h = (double*)hs.get(2 * sizeof(double));
-        DPP_CK(cudaMemcpyAsync(h, nrm.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        DPP_CK(cudaStreamSynchronize(s));
-        if (!(h[0] > 0.0) || !(h[1] > 0.0)) fail(DPP_ERR_NONFINITE, "AMG setup: power iteration");
-        lam = std::sqrt(h[0] / h[1]);
-        axpby(1.0 / std::sqrt(h[0]), w.get(), 0.0, v.get(), n, s);  // v = w / ||w||
+        dot(R, w.get(), w.get(), n, nrm.get(), s);   // ||D^-1 A v||^2 with ||v|| = 1
+        k_scale_rsqrt<<<sgrid(n), 256, 0, s>>>(n, w.get(), v.get(), nrm.get());
+        DPP_LAUNCH_CK();
     }
-    return lam;
+    const double l2 = read_scalar(nrm.get(), s, hs);
+    if (!(l2 > 0.0) || !std::isfinite(l2)) fail(DPP_ERR_NONFINITE, "AMG setup: power iteration");
+    return std::sqrt(l2);
 }
 
 void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s) {
@@ -358,6 +370,7 @@ void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s) {
 }  // namespace
 
 void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
+    ProfScope prof_all("setup_amg", s, 0);
     auto& hs = pc.hs;
     const dpp_pc_opts& o = pc.opts;
     pc.levels.clear();
@@ -376,7 +389,10 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
                                                 L.dinv.get(), dabs.get(), st.get());
         DPP_LAUNCH_CK();
         check_dev(st, s, hs, "a level matrix has a non-positive diagonal entry");
-        L.lmax = power_lmax(L.A, L.dinv.get(), L.lanes, s, hs);
+        {
+            ProfScope pr("setup_power", s, 0);
+            L.lmax = power_lmax(L.A, L.dinv.get(), L.lanes, s, hs);
+        }
         L.x.alloc(n);
         L.b.alloc(n);
         L.r.alloc(n);
@@ -385,6 +401,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         if (last) break;
 
         // strength graph
+        ProfScope pr_agg("setup_aggregate", s, 0);
         Csr S;
         S.n_rows = S.n_cols = n;
         S.row_ptr.alloc(n + 1);
@@ -420,7 +437,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
             if (round == 63) fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: MIS-2 did not finish");
         }
         DBuf<int> root_id(n + 1), agg1(n), agg(n);
-        k_root_flags<<<grid_for(n, B), B, 0, s>>>(n, state.get(), root_id.get());
+        k_root_flags<<<grid_for(n + 1, B), B, 0, s>>>(n, state.get(), root_id.get());
         DPP_LAUNCH_CK();
         const int64_t n_agg = exclusive_scan(root_id.get(), root_id.get(), n + 1, s, hs);
         k_agg_pass1<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), state.get(),
@@ -434,6 +451,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         if (n_agg <= 0 || n_agg >= n) break;  // no coarsening possible: this level is the last
 
         // prolongator
+        ProfScope pr_rap("setup_prolong_rap", s, 0);
         Csr P0;
         P0.n_rows = n;
         P0.n_cols = n_agg;
@@ -445,7 +463,10 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
                                               P0.val.get());
         DPP_LAUNCH_CK();
         Csr Pm;
-        spgemm(view(L.A), view(P0), Pm, true, s, hs);
+        {
+            ProfScope q(l == 0 ? "spgemm_AP0_L0" : "spgemm_AP0_Lc", s, 0);
+            spgemm(view(L.A), view(P0), Pm, true, s, hs);
+        }
         const double omega = 4.0 / (3.0 * L.lmax);
         k_smooth_p<<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), Pm.val.get(),
                                                 agg.get(), L.dinv.get(), omega);
@@ -453,9 +474,15 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         L.P = std::move(Pm);
         transpose(L.P, L.R, s, hs);
         Csr AP;
-        spgemm(view(L.A), view(L.P), AP, true, s, hs);
+        {
+            ProfScope q(l == 0 ? "spgemm_AP_L0" : "spgemm_AP_Lc", s, 0);
+            spgemm(view(L.A), view(L.P), AP, true, s, hs);
+        }
         Csr Ac;
-        spgemm(view(L.R), view(AP), Ac, true, s, hs);
+        {
+            ProfScope q(l == 0 ? "spgemm_RAP_L0" : "spgemm_RAP_Lc", s, 0);
+            spgemm(view(L.R), view(AP), Ac, true, s, hs);
+        }
         pc.levels.emplace_back();
         pc.levels.back().A = std::move(Ac);
     }
@@ -465,6 +492,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: coarsest level has more than 4096 rows; "
                                        "raise max_levels or lower strength_theta");
     pc.coarse_n = C.A.n_rows;
+    ProfScope pr("setup_coarse_inverse", s, 0);
     dense_inverse(C.A, pc.coarse_inv, s);
 }
 

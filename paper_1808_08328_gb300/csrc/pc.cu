@@ -65,7 +65,10 @@ void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
         pc.mass_lmax = 0.5 * (P.dim + 2);
     }
     Csr S;
-    build_selfp(P, pc.mdiag.get(), S, s, pc.hs);
+    {
+        ProfScope pr("setup_selfp", s, 0);
+        build_selfp(P, pc.mdiag.get(), S, s, pc.hs);
+    }
     amg_setup(pc, std::move(S), s);
     pc.yu.alloc(nn);
     pc.su.alloc(nn);
