@@ -30,14 +30,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DoF/s to rel. residual 1e-10"
 WORKLOADS = {
-    # name: (dim, n, seed, beta, description)
+    # name: (dim, n, seed, beta, description, precision)
     "3d64_lognormal_fp64": (3, 64, 0, 1.0, "3D unit cube 64^3 x 6 Kuhn tets, log k1~N(0,1), "
                                            "log k2~N(-3,1), mu=beta=1, FP64 field-split+SA-AMG FGMRES"),
+    "3d64_lognormal_mixed": (3, 64, 0, 1.0, "same 3D 64^3 mesh and fields; FP32 values, K x and "
+                                            "preconditioner inside FP64 FGMRES with refinement", 1),
     "2d32_mms_fp64": (2, 32, 0, 1.0, "2D unit square 32x32 x 2 tris, homogeneous k1=1 k2=0.1, MMS data"),
     "3d32_lognormal_fp64": (3, 32, 0, 1.0, "3D unit cube 32^3 x 6 Kuhn tets, log-normal k"),
     "3d48_lognormal_fp64": (3, 48, 0, 1.0, "3D unit cube 48^3 x 6 Kuhn tets, log-normal k "
                                            "(profiling size: pair values 160 MB > L2)"),
+    "3d48_lognormal_mixed": (3, 48, 0, 1.0, "3D 48^3 log-normal, mixed precision (profiling size)", 1),
 }
+
+
+def precision_of(spec) -> int:
+    return spec[5] if len(spec) > 5 else 0
 CPU_SAMPLE = (3, 12, 0, 1.0)   # the oracle's bounded sample of the same recipe: 3D 12^3 cubes
 
 
@@ -221,13 +228,15 @@ def bench_gb300(args):
     B.dpp_destroy_problem(sysm.prob)
     sysm.prob = 0
     stream = torch.cuda.current_stream(dev).cuda_stream
-    pc_opts = B.dpp_pc_opts_default()
+    prec = precision_of(spec)
     s_opts = B.dpp_solve_opts_default()
     s_opts.rtol = 1e-10
     x = torch.zeros((P.mesh.n_nodes, P.mesh.dofs_per_node), dtype=torch.float64, device=dev)
 
-    def step(d=desc, xv=x, so=s_opts):
-        prob = B.dpp_assemble(d, B.DPP_FP64, stream)
+    def step(d=desc, xv=x, so=s_opts, precision=prec):
+        pc_opts = B.dpp_pc_opts_default()
+        pc_opts.precision = precision
+        prob = B.dpp_assemble(d, precision, stream)
         pc = B.dpp_setup_pc(prob, pc_opts, stream)
         info = B.dpp_solve(prob, pc, so, xv, stream)
         B.dpp_destroy_pc(pc)
@@ -262,10 +271,13 @@ def bench_gb300(args):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = B.dpp_launch_count() - l0
-    fam = {f: B.dpp_profile_read(f) for f in ("apply_K", "amg_csr_spmv", "mass_cheb")}
+    fam = {f: B.dpp_profile_read(f) for f in ("apply_K", "amg_csr_spmv", "mass_cheb",
+                                              "apply_K_fp32", "amg_csr_spmv_fp32",
+                                              "mass_cheb_fp32")}
+    fam = {k: v for k, v in fam.items() if v["launches"]}
     phases = {f: B.dpp_profile_read(f)["ms"] / args.steps
               for f in ("assemble", "setup_selfp", "setup_amg", "setup_power", "setup_aggregate",
-                        "setup_prolong_rap", "setup_coarse_inverse", "spgemm_numeric",
+                        "setup_prolong_rap", "setup_coarse_inverse", "setup_tune", "spgemm_numeric",
                         "spgemm_pattern", "spgemm_alloc", "spgemm_fill", "spgemm_fill_pattern")}
     B.dpp_profile_enable(False)
     clk = clocks.stop()
@@ -311,6 +323,29 @@ def bench_gb300(args):
         e2e = {"value": world * dofs * args.steps / te, "unit": "DoF/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the other precision mode on the same inputs (a short timed run for the summary)
+    modes = {("mixed" if prec else "fp64"): world * dofs * args.steps / (ms * 1e-3)}
+    if not args.no_modes:
+        other = 0 if prec else 1
+        x_other = torch.zeros_like(x)
+        step(desc, x_other, s_opts, other)
+        torch.cuda.synchronize(dev)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(torch.cuda.current_stream(dev))
+        for _ in range(args.steps):
+            step(desc, x_other, s_opts, other)
+        e3.record(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        modes["mixed" if other else "fp64"] = world * dofs * args.steps / (e2.elapsed_time(e3) * 1e-3)
+        xa, xb = (x, x_other) if prec == 0 else (x_other, x)
+        d_ = P.mesh.dim
+        sl = {"u1": slice(0, d_), "p1": slice(d_, d_ + 1), "u2": slice(d_ + 1, 2 * d_ + 1),
+              "p2": slice(2 * d_ + 1, 2 * d_ + 2)}
+        modes["mixed_vs_fp64_rel_l2"] = {
+            k: float(torch.linalg.norm(xb[:, v] - xa[:, v]) / torch.linalg.norm(xa[:, v]))
+            for k, v in sl.items()}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -333,7 +368,8 @@ def bench_gb300(args):
     line = {
         "metric": METRIC, "value": world * dofs * args.steps / (ms * 1e-3), "unit": "DoF/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "dofs": dofs, "description": spec[4],
                    "rtol": 1e-10, "step": "assemble+setup_pc+solve",
@@ -346,7 +382,7 @@ def bench_gb300(args):
                   "levels": last.levels, "ms_assemble": last.ms_assemble,
                   "ms_setup": last.ms_setup, "ms_solve": last.ms_solve,
                   "setup_solve_dof_per_s": dofs / ((last.ms_setup + last.ms_solve) * 1e-3)},
-        "kernels": kernels, "phases_ms_per_step": phases,
+        "kernels": kernels, "phases_ms_per_step": phases, "modes": modes,
     }
     print(json.dumps(line))
     if dist:
@@ -363,6 +399,7 @@ def main():
     ap.add_argument("--workload", default="3d64_lognormal_fp64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="skip the other-precision summary")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)

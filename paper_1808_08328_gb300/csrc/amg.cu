@@ -27,27 +27,45 @@
 #include "amg.cuh"
 
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace dpp {
 
 namespace {
 
 // ------------------------------------------------------------------ CSR SpMV
-// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x
-template <int L, int MODE>
+// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x. T: values, vectors and arithmetic.
+// L lanes share a row; each lane walks its entries four at a time with four
+// independent partial sums, so that several gathers are in flight.
+template <int L, int MODE, class T>
 __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __restrict__ rp,
                                                   const int* __restrict__ col,
-                                                  const double* __restrict__ val,
-                                                  const double* __restrict__ x,
-                                                  const double* __restrict__ b,
-                                                  double* __restrict__ y) {
+                                                  const T* __restrict__ val,
+                                                  const T* __restrict__ x,
+                                                  const T* __restrict__ b, T* __restrict__ y) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = t / L;
     const int lane = (int)(t % L);
     const bool active = row < n_rows;  // inactive lanes still join the shuffles
-    double acc = 0.0;
-    if (active)
-        for (int p = rp[row] + lane; p < rp[row + 1]; p += L) acc += val[p] * __ldg(x + col[p]);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    if (active) {
+        int p = rp[row] + lane;
+        const int e = rp[row + 1];
+        for (; p + 3 * L < e; p += 4 * L) {
+            const int c0 = col[p], c1 = col[p + L], c2 = col[p + 2 * L], c3 = col[p + 3 * L];
+            const T v0 = val[p], v1 = val[p + L], v2 = val[p + 2 * L], v3 = val[p + 3 * L];
+            a0 += v0 * __ldg(x + c0);
+            a1 += v1 * __ldg(x + c1);
+            a2 += v2 * __ldg(x + c2);
+            a3 += v3 * __ldg(x + c3);
+        }
+        for (; p < e; p += L) a0 += val[p] * __ldg(x + col[p]);
+    }
+    T acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
     if (active && lane == 0) {
@@ -57,25 +75,28 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
     }
 }
 
-template <int MODE>
-void spmv_lanes(int lanes, const Csr& A, const double* x, const double* b, double* y,
-                cudaStream_t s) {
-    const double alg = (double)A.nnz * 12.0 + (double)(A.n_rows + 1) * 4.0 +
-                       (double)A.n_cols * 8.0 + (double)A.n_rows * 8.0 * (MODE == 0 ? 1 : 2);
-    ProfScope prof("amg_csr_spmv", s, alg);
+template <class T> const T* vals(const Csr& A);
+template <> const double* vals<double>(const Csr& A) { return A.val.get(); }
+template <> const float* vals<float>(const Csr& A) { return A.val32.get(); }
+
+template <int MODE, class T>
+void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStream_t s) {
+    const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (double)(A.n_rows + 1) * 4.0 +
+                       (double)A.n_cols * sizeof(T) + (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : 2);
+    ProfScope prof(sizeof(T) == 8 ? "amg_csr_spmv" : "amg_csr_spmv_fp32", s, alg);
     const int B = 256;
     const int64_t thr = A.n_rows * lanes;
     const int g = grid_for(thr, B);
     const int* rp = A.row_ptr.get();
     const int* cl = A.col.get();
-    const double* v = A.val.get();
+    const T* v = vals<T>(A);
     switch (lanes) {
-        case 1: k_csr_spmv<1, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 2: k_csr_spmv<2, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 4: k_csr_spmv<4, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 8: k_csr_spmv<8, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 16: k_csr_spmv<16, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        default: k_csr_spmv<32, MODE><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 1: k_csr_spmv<1, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 2: k_csr_spmv<2, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 4: k_csr_spmv<4, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 8: k_csr_spmv<8, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 16: k_csr_spmv<16, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        default: k_csr_spmv<32, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
     }
     DPP_LAUNCH_CK();
 }
@@ -104,21 +125,27 @@ __global__ void k_diag_inv(int64_t n, const int* __restrict__ rp, const int* __r
 }
 
 // Chebyshev vector step: zero_init: d = c2 Dinv b, x = d.  else: d = c1 d + c2 Dinv r, x += d
-__global__ void k_cheb_update(int64_t n, const double* __restrict__ dinv,
-                              const double* __restrict__ r, double* __restrict__ d,
-                              double* __restrict__ x, double c1, double c2, int zero_init) {
+template <class T>
+__global__ void k_cheb_update(int64_t n, const T* __restrict__ dinv, const T* __restrict__ r,
+                              T* __restrict__ d, T* __restrict__ x, T c1, T c2, int zero_init) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         if (zero_init) {
-            double v = c2 * dinv[i] * r[i];
+            T v = c2 * dinv[i] * r[i];
             d[i] = v;
             x[i] = v;
         } else {
-            double v = c1 * d[i] + c2 * dinv[i] * r[i];
+            T v = c1 * d[i] + c2 * dinv[i] * r[i];
             d[i] = v;
             x[i] += v;
         }
     }
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (float)in[i];
 }
 
 __global__ void k_fill_int(int64_t n, int v, int* __restrict__ x) {
@@ -306,16 +333,17 @@ __global__ void k_gj_elim(int n, int k, double* __restrict__ M, const double* __
     M[t] -= f[i] * M[(int64_t)k * n + j];
 }
 
-// x = Minv b, one warp per row
-__global__ void k_dense_mv(int n, const double* __restrict__ M, const double* __restrict__ b,
-                           double* __restrict__ x) {
+// x = Minv b, one warp per row; Minv and the accumulation stay FP64 in both modes
+template <class T>
+__global__ void k_dense_mv(int n, const double* __restrict__ M, const T* __restrict__ b,
+                           T* __restrict__ x) {
     int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (row >= n) return;
     double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += M[row * n + j] * b[j];
+    for (int j = lane; j < n; j += 32) acc += M[row * n + j] * (double)b[j];
     acc = warp_sum(acc);
-    if (lane == 0) x[row] = acc;
+    if (lane == 0) x[row] = (T)acc;
 }
 
 inline int sgrid(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 8 * kSMs); }
@@ -338,7 +366,7 @@ double power_lmax(const Csr& A, const double* dinv, int lanes, cudaStream_t s, H
     k_scale_rsqrt<<<sgrid(n), 256, 0, s>>>(n, v.get(), v.get(), nrm.get());
     DPP_LAUNCH_CK();
     for (int it = 0; it < 15; ++it) {
-        spmv_lanes<0>(lanes, A, v.get(), nullptr, w.get(), s);
+        spmv_lanes<0, double>(lanes, A, v.get(), nullptr, w.get(), s);
         k_dinv_scale<<<sgrid(n), 256, 0, s>>>(n, dinv, w.get());
         DPP_LAUNCH_CK();
         dot(R, w.get(), w.get(), n, nrm.get(), s);   // ||D^-1 A v||^2 with ||v|| = 1
@@ -498,55 +526,204 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
 
 namespace {
 
-void cheb_smooth(const PcImpl& pc, Level& L, const double* b, double* x, bool zero_init,
-                 cudaStream_t s) {
+template <class T> T* lv(DBuf<double>& d, DBuf<float>& f);
+template <> double* lv<double>(DBuf<double>& d, DBuf<float>&) { return d.get(); }
+template <> float* lv<float>(DBuf<double>&, DBuf<float>& f) { return f.get(); }
+
+template <class T>
+void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s) {
     const int deg = std::max(1, pc.opts.cheb_degree_amg);
     const double hi = 1.1 * L.lmax, lo = L.lmax / pc.opts.cheb_ratio;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     const int64_t n = L.A.n_rows;
+    T* r = lv<T>(L.r, L.r32);
+    T* d = lv<T>(L.d, L.d32);
+    const T* dinv = lv<T>(L.dinv, L.dinv32);
     double rho = 1.0 / sigma;
     for (int k = 0; k < deg; ++k) {
         if (k == 0) {
             if (zero_init) {
-                k_cheb_update<<<sgrid(n), 256, 0, s>>>(n, L.dinv.get(), b, L.d.get(), x, 0.0,
-                                                       1.0 / theta, 1);
+                k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, b, d, x, T(0), T(1.0 / theta), 1);
             } else {
-                spmv_lanes<1>(L.lanes, L.A, x, b, L.r.get(), s);
-                k_cheb_update<<<sgrid(n), 256, 0, s>>>(n, L.dinv.get(), L.r.get(), L.d.get(), x,
-                                                       0.0, 1.0 / theta, 0);
+                spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s);
+                k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, r, d, x, T(0), T(1.0 / theta), 0);
             }
         } else {
             const double rho_new = 1.0 / (2.0 * sigma - rho);
-            spmv_lanes<1>(L.lanes, L.A, x, b, L.r.get(), s);
-            k_cheb_update<<<sgrid(n), 256, 0, s>>>(n, L.dinv.get(), L.r.get(), L.d.get(), x,
-                                                   rho_new * rho, 2.0 * rho_new / delta, 0);
+            spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s);
+            k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, r, d, x, T(rho_new * rho),
+                                                      T(2.0 * rho_new / delta), 0);
             rho = rho_new;
         }
         DPP_LAUNCH_CK();
     }
 }
 
-void vcycle_level(PcImpl& pc, size_t l, const double* b, double* x, cudaStream_t s) {
+template <class T>
+void vcycle_level(PcImpl& pc, size_t l, const T* b, T* x, cudaStream_t s) {
     Level& L = pc.levels[l];
     if (l + 1 == pc.levels.size()) {
         const int n = (int)pc.coarse_n;
-        k_dense_mv<<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, pc.coarse_inv.get(), b, x);
+        k_dense_mv<T><<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, pc.coarse_inv.get(), b, x);
         DPP_LAUNCH_CK();
         return;
     }
     Level& C = pc.levels[l + 1];
-    cheb_smooth(pc, L, b, x, true, s);
-    spmv_lanes<1>(L.lanes, L.A, x, b, L.r.get(), s);
-    spmv_lanes<0>(pick_lanes(L.R), L.R, L.r.get(), nullptr, C.b.get(), s);
-    vcycle_level(pc, l + 1, C.b.get(), C.x.get(), s);
-    spmv_lanes<2>(pick_lanes(L.P), L.P, C.x.get(), nullptr, x, s);
-    cheb_smooth(pc, L, b, x, false, s);
+    T* r = lv<T>(L.r, L.r32);
+    T* cb = lv<T>(C.b, C.b32);
+    T* cx = lv<T>(C.x, C.x32);
+    cheb_smooth<T>(pc, L, b, x, true, s);
+    spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s);
+    spmv_lanes<0, T>(L.lanes_R, L.R, r, nullptr, cb, s);
+    vcycle_level<T>(pc, l + 1, cb, cx, s);
+    spmv_lanes<2, T>(L.lanes_P, L.P, cx, nullptr, x, s);
+    cheb_smooth<T>(pc, L, b, x, false, s);
+}
+
+void to_f32(const DBuf<double>& in, DBuf<float>& out, cudaStream_t s) {
+    out.alloc(in.n);
+    if (in.n) {
+        k_d2f<<<sgrid((int64_t)in.n), 256, 0, s>>>((int64_t)in.n, in.get(), out.get());
+        DPP_LAUNCH_CK();
+    }
+}
+
+// ------------------------------------------------------------------ autotuner
+// Lanes per row of the CSR SpMV, chosen per matrix by timing every candidate
+// on the device. Choices are cached for the process per size class (precision,
+// operator kind, log2 rows, mean row length). If the environment variable
+// DPP_TUNE_CACHE names a file, the cache is read from it and new choices are
+// appended to it as JSON lines.
+struct TuneKey {
+    int fp32, kind, log2_rows, avg_nnz;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(fp32, kind, log2_rows, avg_nnz) < std::tie(o.fp32, o.kind, o.log2_rows, o.avg_nnz);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("DPP_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        TuneKey k;
+        int lanes = 0;
+        if (std::sscanf(line, "{\"fp32\": %d, \"kind\": %d, \"log2_rows\": %d, \"avg_nnz\": %d, \"lanes\": %d}",
+                        &k.fp32, &k.kind, &k.log2_rows, &k.avg_nnz, &lanes) == 5 &&
+            (lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+            g_tune[k] = lanes;
+    }
+    std::fclose(f);
+}
+
+void tune_store_locked(const TuneKey& k, int lanes) {
+    g_tune[k] = lanes;
+    const char* path = std::getenv("DPP_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"fp32\": %d, \"kind\": %d, \"log2_rows\": %d, \"avg_nnz\": %d, \"lanes\": %d}\n",
+                 k.fp32, k.kind, k.log2_rows, k.avg_nnz, lanes);
+    std::fclose(f);
+}
+
+template <int MODE, class T>
+int tune_lanes(const Csr& A, const T* x, const T* b, T* y, int kind, cudaStream_t s) {
+    TuneKey key;
+    key.fp32 = sizeof(T) == 4;
+    key.kind = kind;
+    key.log2_rows = 0;
+    for (int64_t r = A.n_rows; r > 1; r >>= 1) ++key.log2_rows;
+    key.avg_nnz = (int)std::lround(A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    const int cands[5] = {2, 4, 8, 16, 32};
+    cudaEvent_t e0, e1;
+    DPP_CK(cudaEventCreate(&e0));
+    DPP_CK(cudaEventCreate(&e1));
+    int best = pick_lanes(A);
+    float best_ms = 1e30f;
+    for (int c : cands) {
+        spmv_lanes<MODE, T>(c, A, x, b, y, s);  // warm
+        DPP_CK(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) spmv_lanes<MODE, T>(c, A, x, b, y, s);
+        DPP_CK(cudaEventRecord(e1, s));
+        DPP_CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        DPP_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_store_locked(key, best);
+    return best;
+}
+
+template <class T>
+void tune_levels(PcImpl& pc, cudaStream_t s) {
+    for (size_t l = 0; l < pc.levels.size(); ++l) {
+        Level& L = pc.levels[l];
+        T* x = lv<T>(L.x, L.x32);
+        T* b = lv<T>(L.b, L.b32);
+        T* r = lv<T>(L.r, L.r32);
+        DPP_CK(cudaMemsetAsync(x, 0, L.A.n_rows * sizeof(T), s));
+        DPP_CK(cudaMemsetAsync(b, 0, L.A.n_rows * sizeof(T), s));
+        L.lanes = tune_lanes<1, T>(L.A, x, b, r, 0, s);
+        if (l + 1 < pc.levels.size()) {
+            Level& C = pc.levels[l + 1];
+            T* cx = lv<T>(C.x, C.x32);
+            T* cb = lv<T>(C.b, C.b32);
+            DPP_CK(cudaMemsetAsync(cx, 0, C.A.n_rows * sizeof(T), s));
+            L.lanes_R = tune_lanes<0, T>(L.R, r, nullptr, cb, 1, s);
+            L.lanes_P = tune_lanes<2, T>(L.P, cx, nullptr, x, 2, s);
+        }
+    }
+    DPP_CK(cudaStreamSynchronize(s));
 }
 
 }  // namespace
 
-void amg_vcycle(PcImpl& pc, const double* b, double* x, cudaStream_t s) {
-    vcycle_level(pc, 0, b, x, s);
+void amg_tune(PcImpl& pc, cudaStream_t s) {
+    ProfScope pr("setup_tune", s, 0);
+    if (pc.precision == DPP_MIXED_FP32_FP64) tune_levels<float>(pc, s);
+    else tune_levels<double>(pc, s);
 }
+
+void amg_make_fp32(PcImpl& pc, cudaStream_t s) {
+    for (size_t l = 0; l < pc.levels.size(); ++l) {
+        Level& L = pc.levels[l];
+        to_f32(L.A.val, L.A.val32, s);
+        to_f32(L.dinv, L.dinv32, s);
+        if (l + 1 < pc.levels.size()) {
+            to_f32(L.P.val, L.P.val32, s);
+            to_f32(L.R.val, L.R.val32, s);
+        }
+        const int64_t n = L.A.n_rows;
+        L.x32.alloc(n);
+        L.b32.alloc(n);
+        L.r32.alloc(n);
+        L.d32.alloc(n);
+    }
+    DPP_CK(cudaStreamSynchronize(s));
+}
+
+template <class T>
+void amg_vcycle(PcImpl& pc, const T* b, T* x, cudaStream_t s) {
+    vcycle_level<T>(pc, 0, b, x, s);
+}
+template void amg_vcycle<double>(PcImpl&, const double*, double*, cudaStream_t);
+template void amg_vcycle<float>(PcImpl&, const float*, float*, cudaStream_t);
 
 }  // namespace dpp

@@ -32,7 +32,13 @@ void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t
                  HostScratch& hs);
 
 void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s);
-// x = (one V-cycle) b on level 0; b is not modified.
-void amg_vcycle(PcImpl& pc, const double* b, double* x, cudaStream_t s);
+// FP32 copies of every level (values, 1/diag, work vectors) for the mixed mode.
+void amg_make_fp32(PcImpl& pc, cudaStream_t s);
+// Autotune the CSR SpMV lanes of every level matrix for the pc's precision.
+void amg_tune(PcImpl& pc, cudaStream_t s);
+// x = (one V-cycle) b on level 0; b is not modified. T = double uses the FP64
+// hierarchy; T = float the FP32 copies (the coarsest solve stays FP64).
+template <class T>
+void amg_vcycle(PcImpl& pc, const T* b, T* x, cudaStream_t s);
 
 }  // namespace dpp

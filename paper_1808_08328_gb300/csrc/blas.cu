@@ -99,6 +99,19 @@ __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int k,
     }
 }
 
+__global__ void k_multi_axpy_f32(const float* __restrict__ Z, int64_t ld, int k,
+                                 const double* __restrict__ h, double* __restrict__ x, int64_t n) {
+    __shared__ double hs[64];
+    if (threadIdx.x < k) hs[threadIdx.x] = h[threadIdx.x];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double acc = 0.0;
+        for (int j = 0; j < k; ++j) acc += hs[j] * (double)Z[(int64_t)j * ld + i];
+        x[i] += acc;
+    }
+}
+
 __global__ void k_scale_copy(const double* __restrict__ x, double* __restrict__ y, int64_t n,
                              const double* __restrict__ num, const double* __restrict__ den) {
     const double a = den ? (*num / *den) : *num;
@@ -162,6 +175,14 @@ void multi_axpy_add(const double* Z, int64_t ld, int k, const double* y, double*
     if (k <= 0) return;
     if (k > 64) fail(DPP_ERR_INVALID_ARGUMENT, "multi_axpy: k > 64");
     k_multi_axpy<<<stream_grid(n), 256, 0, s>>>(Z, ld, k, y, x, n, 1.0);
+    DPP_LAUNCH_CK();
+}
+
+void multi_axpy_add_f32(const float* Z, int64_t ld, int k, const double* y, double* x, int64_t n,
+                        cudaStream_t s) {
+    if (k <= 0) return;
+    if (k > 64) fail(DPP_ERR_INVALID_ARGUMENT, "multi_axpy: k > 64");
+    k_multi_axpy_f32<<<stream_grid(n), 256, 0, s>>>(Z, ld, k, y, x, n);
     DPP_LAUNCH_CK();
 }
 

@@ -58,7 +58,8 @@ struct Level {
     DBuf<double> dinv;        // 1 / diag(A)
     DBuf<float> dinv32;
     double lmax = 0;          // estimate of the largest eigenvalue of D^-1 A
-    int lanes = 4;            // CSR SpMV lanes per row
+    int lanes = 4;            // CSR SpMV lanes per row of A (autotuned)
+    int lanes_P = 4, lanes_R = 4;  // lanes per row of P and R (autotuned)
     // V-cycle work vectors (length n_rows)
     DBuf<double> x, b, r, d;
     DBuf<float> x32, b32, r32, d32;
@@ -78,6 +79,8 @@ struct PcImpl {
     DBuf<double> yu, su, tmp, dcheb;
     DBuf<double> tp, yp;      // split pressures [2][n_nodes]
     DBuf<double> mdiag;       // [n_nodes][2]: 1/m1_aa, 1/m2_aa (mass Jacobi)
+    // FP32 copies for the mixed-precision preconditioner
+    DBuf<float> yu32, su32, tmp32, dcheb32, tp32, yp32, mdiag32, r32;
     HostScratch hs;
     double ms_setup = 0;
 };

@@ -8,25 +8,31 @@ namespace dpp {
 void assemble_problem(ProblemImpl& P, const dpp_problem_desc& d, cudaStream_t s);
 
 // ---- node-pair (SELL-32) operators on node-interleaved vectors ----
-// y = K x (transpose: K^T x). If b != nullptr: y = b - K x. use32: FP32 values.
+// y = K x (transpose: K^T x). If b != nullptr: y = b - K x. use32: FP32 values
+// (arithmetic stays FP64 because x is FP64).
 void apply_K(const ProblemImpl& P, const double* x, double* y, const double* b, bool transpose,
              bool use32, cudaStream_t s);
-// One Chebyshev step on the velocity block A = blockdiag(K1_uu, K2_uu).
-// first: x_out = c2 * Dinv r, d = x_out. else: res = r - A x_in;
-// d = c1 d + c2 Dinv res; x_out = x_in + d. Only u slots are touched.
-void mass_cheb_step(const ProblemImpl& P, const double* mdiag, const double* r, const double* x_in,
-                    double* x_out, double* d, double c1, double c2, bool first, bool use32,
-                    cudaStream_t s);
+// y = K32 x with FP32 values, FP32 x and FP32 arithmetic, FP64 output.
+void apply_K32(const ProblemImpl& P, const float* x, double* y, bool transpose, cudaStream_t s);
+// One Chebyshev step on the velocity block A = blockdiag(K1_uu, K2_uu), in type T
+// (values of the same type). first: x_out = c2 * Dinv r, d = x_out. else:
+// res = r - A x_in; d = c1 d + c2 Dinv res; x_out = x_in + d. Only u slots change.
+template <class T>
+void mass_cheb_step(const ProblemImpl& P, const T* mdiag, const T* r, const T* xin, T* xout, T* d,
+                    double c1, double c2, bool first, cudaStream_t s);
 // tp[net][a] = r_p(net)[a] - (C y_u)(net)[a]   (sign of C flipped if transpose)
-void apply_C_resid(const ProblemImpl& P, const double* r, const double* yu, double* tp,
-                   bool transpose, bool use32, cudaStream_t s);
+template <class T>
+void apply_C_resid(const ProblemImpl& P, const T* r, const T* yu, T* tp, bool transpose,
+                   cudaStream_t s);
 // su_u = r_u - B yp   (yp split [2][n]; sign of B flipped if transpose); p slots of su untouched
-void apply_B_resid(const ProblemImpl& P, const double* r, const double* yp, double* su,
-                   bool transpose, bool use32, cudaStream_t s);
-// mdiag[a][net] = 1 / m_net(a, a)
+template <class T>
+void apply_B_resid(const ProblemImpl& P, const T* r, const T* yp, T* su, bool transpose,
+                   cudaStream_t s);
+// mdiag[a][net] = 1 / m_net(a, a) (or the row sum when lumped)
 void mass_diag_inv(const ProblemImpl& P, double* mdiag, bool lumped, cudaStream_t s);
 // z_p(net)[a] = yp[net][a] (copy split pressures into interleaved p slots)
-void scatter_p(const ProblemImpl& P, const double* yp, double* z, cudaStream_t s);
+template <class T>
+void scatter_p(const ProblemImpl& P, const T* yp, T* z, cudaStream_t s);
 
 // ---- vector kernels (n doubles) ----
 struct Reducer {
@@ -51,5 +57,8 @@ void scale_copy(const double* x, double* y, int64_t n, const double* num, const 
 void axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s);
 void fill(double* x, double v, int64_t n, cudaStream_t s);
 void to_float(const double* in, float* out, int64_t n, cudaStream_t s);
+// x += sum_j y[j] Z_j with FP32 Z (FP64 y and x)
+void multi_axpy_add_f32(const float* Z, int64_t ld, int k, const double* y, double* x, int64_t n,
+                        cudaStream_t s);
 
 }  // namespace dpp

@@ -25,26 +25,37 @@ namespace dpp {
 
 namespace {
 
-void mass_chebyshev(const ProblemImpl& P, const PcImpl& pc, const double* r, double* target,
-                    double* tmp, double* dvec, cudaStream_t s) {
+template <class T>
+void mass_chebyshev(const ProblemImpl& P, const PcImpl& pc, const T* mdiag, const T* r, T* target,
+                    T* tmp, T* dvec, cudaStream_t s) {
     const int deg = std::max(1, pc.opts.cheb_degree_mass);
     const double lo = pc.mass_lmin, hi = pc.mass_lmax;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     double rho = 1.0 / sigma;
-    const double* xin = nullptr;
+    const T* xin = nullptr;
     for (int k = 0; k < deg; ++k) {
-        double* xout = ((deg - 1 - k) % 2 == 0) ? target : tmp;
+        T* xout = ((deg - 1 - k) % 2 == 0) ? target : tmp;
         if (k == 0) {
-            mass_cheb_step(P, pc.mdiag.get(), r, nullptr, xout, dvec, 0.0, 1.0 / theta, true,
-                           false, s);
+            mass_cheb_step<T>(P, mdiag, r, nullptr, xout, dvec, 0.0, 1.0 / theta, true, s);
         } else {
             const double rho_new = 1.0 / (2.0 * sigma - rho);
-            mass_cheb_step(P, pc.mdiag.get(), r, xin, xout, dvec, rho_new * rho,
-                           2.0 * rho_new / delta, false, false, s);
+            mass_cheb_step<T>(P, mdiag, r, xin, xout, dvec, rho_new * rho, 2.0 * rho_new / delta,
+                              false, s);
             rho = rho_new;
         }
         xin = xout;
     }
+}
+
+__global__ void k_d2f_pc(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (float)in[i];
+}
+
+void d2f(const double* in, float* out, int64_t n, cudaStream_t s) {
+    k_d2f_pc<<<(int)std::min<int64_t>((n + 255) / 256, 8 * kSMs), 256, 0, s>>>(n, in, out);
+    DPP_LAUNCH_CK();
 }
 
 }  // namespace
@@ -77,22 +88,60 @@ void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
     pc.tp.alloc(2 * n);
     pc.yp.alloc(2 * n);
     DPP_CK(cudaMemsetAsync(pc.su.get(), 0, nn * sizeof(double), s));
+    if (pc.precision == DPP_MIXED_FP32_FP64) {
+        // FP32 pair values (if the problem was assembled in FP64 only) and FP32 hierarchy
+        auto& Pm = const_cast<ProblemImpl&>(P);
+        if (!Pm.sell_val32.get()) {
+            Pm.sell_val32.alloc(P.sell_val.n);
+            d2f(P.sell_val.get(), Pm.sell_val32.get(), (int64_t)P.sell_val.n, s);
+        }
+        amg_make_fp32(pc, s);
+        pc.mdiag32.alloc(2 * n);
+        d2f(pc.mdiag.get(), pc.mdiag32.get(), 2 * n, s);
+        pc.yu32.alloc(nn);
+        pc.su32.alloc(nn);
+        pc.tmp32.alloc(nn);
+        pc.dcheb32.alloc(nn);
+        pc.tp32.alloc(2 * n);
+        pc.yp32.alloc(2 * n);
+        pc.r32.alloc(nn);
+        DPP_CK(cudaMemsetAsync(pc.su32.get(), 0, nn * sizeof(float), s));
+    }
+    amg_tune(pc, s);
     DPP_CK(cudaStreamSynchronize(s));
 }
 
+// z = P^-1 r in FP64 (values, vectors and arithmetic).
 void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
               cudaStream_t s) {
     // 1. y_u = Ainv r_u
-    mass_chebyshev(P, pc, r, pc.yu.get(), pc.tmp.get(), pc.dcheb.get(), s);
+    mass_chebyshev<double>(P, pc, pc.mdiag.get(), r, pc.yu.get(), pc.tmp.get(), pc.dcheb.get(), s);
     // 2. t_p = r_p - C y_u   (split pressures [p1 | p2])
-    apply_C_resid(P, r, pc.yu.get(), pc.tp.get(), transpose, false, s);
+    apply_C_resid<double>(P, r, pc.yu.get(), pc.tp.get(), transpose, s);
     // 3. y_p = Sinv t_p: one V-cycle on blockdiag(S_p1, S_p2)
-    amg_vcycle(pc, pc.tp.get(), pc.yp.get(), s);
+    amg_vcycle<double>(pc, pc.tp.get(), pc.yp.get(), s);
     // 4. s_u = r_u - B y_p ;  z_u = Ainv s_u
-    apply_B_resid(P, r, pc.yp.get(), pc.su.get(), transpose, false, s);
-    mass_chebyshev(P, pc, pc.su.get(), z, pc.tmp.get(), pc.dcheb.get(), s);
+    apply_B_resid<double>(P, r, pc.yp.get(), pc.su.get(), transpose, s);
+    mass_chebyshev<double>(P, pc, pc.mdiag.get(), pc.su.get(), z, pc.tmp.get(), pc.dcheb.get(), s);
     // 5. z_p = y_p
-    scatter_p(P, pc.yp.get(), z, s);
+    scatter_p<double>(P, pc.yp.get(), z, s);
+}
+
+// z32 = P^-1 r in FP32 (mixed mode): r is converted once, every preconditioner
+// step runs on FP32 values and vectors, and the coarsest solve stays FP64.
+void pc_apply32(const ProblemImpl& P, PcImpl& pc, const double* r, float* z, bool transpose,
+                cudaStream_t s) {
+    if (pc.precision != DPP_MIXED_FP32_FP64) fail(DPP_ERR_BAD_STATE, "pc has no FP32 hierarchy");
+    float* r32 = pc.r32.get();
+    d2f(r, r32, P.n_nodes * P.ns, s);
+    mass_chebyshev<float>(P, pc, pc.mdiag32.get(), r32, pc.yu32.get(), pc.tmp32.get(),
+                          pc.dcheb32.get(), s);
+    apply_C_resid<float>(P, r32, pc.yu32.get(), pc.tp32.get(), transpose, s);
+    amg_vcycle<float>(pc, pc.tp32.get(), pc.yp32.get(), s);
+    apply_B_resid<float>(P, r32, pc.yp32.get(), pc.su32.get(), transpose, s);
+    mass_chebyshev<float>(P, pc, pc.mdiag32.get(), pc.su32.get(), z, pc.tmp32.get(),
+                          pc.dcheb32.get(), s);
+    scatter_p<float>(P, pc.yp32.get(), z, s);
 }
 
 }  // namespace dpp

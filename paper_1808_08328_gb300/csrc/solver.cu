@@ -16,6 +16,16 @@
 // scalars copied back per iteration. The converged test uses the FP64 true
 // residual ||f - K x||_2 / ||f||_2, evaluated when the estimate reaches the
 // tolerance and at every restart.
+//
+// Mixed precision (GMRES-IR in the sense of Carson & Higham, SIAM J. Sci.
+// Comput. 40(2), 2018): every restart cycle is one refinement step. The outer
+// residual r = f - K x uses FP64 values and arithmetic. Inside the cycle,
+// z_j = P^-1 v_j runs in the FP32 preconditioner (FP32 values, vectors and
+// arithmetic; FP64 coarsest solve) and is stored in FP32, and w = K z_j uses
+// the FP32 values with FP32 arithmetic. The Arnoldi basis V, CGS2, the
+// Hessenberg matrix and the Givens rotations stay FP64. A cycle ends when its
+// estimate has dropped by inner_rtol relative to the cycle's starting
+// residual. Then x += Z y in FP64 and the FP64 residual is recomputed.
 #include "amg.cuh"
 
 #include <cmath>
@@ -24,6 +34,8 @@ namespace dpp {
 
 void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
               cudaStream_t s);
+void pc_apply32(const ProblemImpl& P, PcImpl& pc, const double* r, float* z, bool transpose,
+                cudaStream_t s);
 
 namespace {
 
@@ -31,12 +43,14 @@ struct Workspace {
     int m = 0;
     int64_t n = 0;
     DBuf<double> V, Z, w, r, dscal;  // dscal: [0..m] h, [m+1..2m+1] h', [2m+2] ||w||^2, [2m+3] ||r||^2
+    DBuf<float> Z32;                 // preconditioned vectors in the mixed mode
     Reducer R;
-    void init(int m_, int64_t n_) {
+    void init(int m_, int64_t n_, bool mixed) {
         m = m_;
         n = n_;
         V.alloc((size_t)(m + 1) * n);
-        Z.alloc((size_t)m * n);
+        if (mixed) Z32.alloc((size_t)m * n);
+        else Z.alloc((size_t)m * n);
         w.alloc(n);
         r.alloc(n);
         dscal.alloc(2 * m + 8);
@@ -57,8 +71,9 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
                   HostScratch& hs) {
     const int64_t n = P.n_nodes * P.ns;
     const int m = std::min(std::max(o.restart, 1), 64);
+    const bool mixed = pc.precision == DPP_MIXED_FP32_FP64;
     Workspace W;
-    W.init(m, n);
+    W.init(m, n, mixed);
     info.iterations = 0;
     info.restarts = 0;
     const double bnorm = device_norm(W, rhs, n, s, hs);
@@ -82,6 +97,9 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
         if (info.iterations >= o.max_iters) { st = DPP_ERR_NOT_CONVERGED; break; }
         double* V = W.V.get();
         double* Z = W.Z.get();
+        float* Z32 = W.Z32.get();
+        const double cycle_target = mixed ? std::max(o.inner_rtol * beta, 0.5 * o.rtol * bnorm)
+                                          : o.rtol * bnorm;
         axpby(1.0 / beta, W.r.get(), 0.0, V, n, s);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
@@ -89,10 +107,20 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
         bool breakdown = false, nonfinite = false;
         for (j = 0; j < m; ++j) {
             double* vj = V + (size_t)j * n;
-            double* zj = Z + (size_t)j * n;
-            pc_apply(P, pc, vj, zj, transpose, s);
-            apply_K(P, zj, W.w.get(), nullptr, transpose, false, s);
+            {
+                ProfScope pp("krylov_pc", s, 0);
+                if (mixed) {
+                    float* zj = Z32 + (size_t)j * n;
+                    pc_apply32(P, pc, vj, zj, transpose, s);
+                    apply_K32(P, zj, W.w.get(), transpose, s);
+                } else {
+                    double* zj = Z + (size_t)j * n;
+                    pc_apply(P, pc, vj, zj, transpose, s);
+                    apply_K(P, zj, W.w.get(), nullptr, transpose, false, s);
+                }
+            }
             double* hd = W.dscal.get();
+            ProfScope po("krylov_orth", s, 0);
             multidot(W.R, V, n, j + 1, W.w.get(), n, hd, s);
             multi_axpy_sub(V, n, j + 1, hd, W.w.get(), n, s);
             multidot(W.R, V, n, j + 1, W.w.get(), n, hd + m + 1, s);
@@ -122,10 +150,10 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
             g[j] = cs[j] * g[j];
             ++info.iterations;
             ncol = j + 1;
-            const double est = std::fabs(g[j + 1]) / bnorm;
+            const double est = std::fabs(g[j + 1]);
             if (hn <= 1e-300 * std::max(1.0, rr)) { breakdown = true; break; }  // exact subspace
             if (j + 1 < m) axpby(1.0 / hn, W.w.get(), 0.0, V + (size_t)(j + 1) * n, n, s);
-            if (est <= o.rtol || info.iterations >= o.max_iters) break;
+            if (est <= cycle_target || info.iterations >= o.max_iters) break;
             (void)every;
         }
         if (nonfinite) { st = DPP_ERR_NONFINITE; break; }
@@ -137,11 +165,12 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
         }
         double* yd = W.dscal.get();
         DPP_CK(cudaMemcpyAsync(yd, y.data(), ncol * sizeof(double), cudaMemcpyHostToDevice, s));
-        multi_axpy_add(Z, n, ncol, yd, x, n, s);
+        if (mixed) multi_axpy_add_f32(Z32, n, ncol, yd, x, n, s);
+        else multi_axpy_add(Z, n, ncol, yd, x, n, s);
         apply_K(P, x, W.r.get(), rhs, transpose, false, s);
         beta = device_norm(W, W.r.get(), n, s, hs);
         ++info.restarts;
-        if (breakdown && beta / bnorm > o.rtol) {
+        if (breakdown && !mixed && beta / bnorm > o.rtol) {
             info.rel_residual = beta / bnorm;
             st = DPP_ERR_BREAKDOWN;
             break;

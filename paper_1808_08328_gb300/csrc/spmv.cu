@@ -11,16 +11,24 @@
 //
 // Layout: one thread per node row. A warp covers the 32 rows of one SELL
 // slice, so every value and column load is one coalesced 128-256 B
-// transaction. x is gathered per column node as (2d+2) contiguous doubles.
+// transaction. x is gathered per column node as (2d+2) contiguous values.
+//
+// Precision: the FP64 path keeps values, vectors and arithmetic in FP64. The
+// mixed path (FP32 values, FP32 preconditioner vectors) does its arithmetic in
+// FP32. On GB300 the FP64 pipe, not HBM, bounds the FP64 kernels; the FP32
+// kernels are HBM-bound.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace dpp {
 
 namespace {
 
+// (2d+2)-value node loads and stores with the widest aligned vector type.
 template <int NS>
-__device__ __forceinline__ void load_node(const double* __restrict__ x, int b, double (&v)[NS]) {
-    const double2* p = reinterpret_cast<const double2*>(x + (int64_t)b * NS);
+__device__ __forceinline__ void load_node(const double* __restrict__ x, int64_t b, double (&v)[NS]) {
+    const double2* p = reinterpret_cast<const double2*>(x + b * NS);
 #pragma unroll
     for (int k = 0; k < NS / 2; ++k) {
         double2 t = __ldg(p + k);
@@ -28,22 +36,79 @@ __device__ __forceinline__ void load_node(const double* __restrict__ x, int b, d
         v[2 * k + 1] = t.y;
     }
 }
-
 template <int NS>
-__device__ __forceinline__ void store_node(double* __restrict__ y, int64_t a, const double (&v)[NS]) {
-    double2* p = reinterpret_cast<double2*>(y + a * NS);
+__device__ __forceinline__ void load_node(const float* __restrict__ x, int64_t b, float (&v)[NS]) {
+    if constexpr (NS % 4 == 0) {
+        const float4* p = reinterpret_cast<const float4*>(x + b * NS);
 #pragma unroll
-    for (int k = 0; k < NS / 2; ++k) p[k] = make_double2(v[2 * k], v[2 * k + 1]);
+        for (int k = 0; k < NS / 4; ++k) {
+            float4 t = __ldg(p + k);
+            v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+        }
+    } else {
+        const float2* p = reinterpret_cast<const float2*>(x + b * NS);
+#pragma unroll
+        for (int k = 0; k < NS / 2; ++k) {
+            float2 t = __ldg(p + k);
+            v[2 * k] = t.x; v[2 * k + 1] = t.y;
+        }
+    }
+}
+template <int NS, class T>
+__device__ __forceinline__ void load_node_as(const T* __restrict__ x, int64_t b, float (&v)[NS]) {
+    if constexpr (std::is_same<T, float>::value) {
+        load_node<NS>(x, b, v);
+    } else {
+        double t[NS];
+        load_node<NS>(x, b, t);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) v[k] = (float)t[k];
+    }
+}
+template <int NS, class T>
+__device__ __forceinline__ void load_node_as(const T* __restrict__ x, int64_t b, double (&v)[NS]) {
+    if constexpr (std::is_same<T, double>::value) {
+        load_node<NS>(x, b, v);
+    } else {
+        float t[NS];
+        load_node<NS>(x, b, t);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) v[k] = (double)t[k];
+    }
 }
 
-template <int DIM, class VT, bool TRANS, bool RESID>
+template <int NS, class AT>
+__device__ __forceinline__ void store_node(double* __restrict__ y, int64_t a, const AT (&v)[NS]) {
+    double2* p = reinterpret_cast<double2*>(y + a * NS);
+#pragma unroll
+    for (int k = 0; k < NS / 2; ++k) p[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+}
+template <int NS, class AT>
+__device__ __forceinline__ void store_node(float* __restrict__ y, int64_t a, const AT (&v)[NS]) {
+    if constexpr (NS % 4 == 0) {
+        float4* p = reinterpret_cast<float4*>(y + a * NS);
+#pragma unroll
+        for (int k = 0; k < NS / 4; ++k)
+            p[k] = make_float4((float)v[4 * k], (float)v[4 * k + 1], (float)v[4 * k + 2],
+                               (float)v[4 * k + 3]);
+    } else {
+        float2* p = reinterpret_cast<float2*>(y + a * NS);
+#pragma unroll
+        for (int k = 0; k < NS / 2; ++k) p[k] = make_float2((float)v[2 * k], (float)v[2 * k + 1]);
+    }
+}
+
+// y = K x (or b - K x). Arithmetic in FP32 when both values and x are FP32.
+template <int DIM, class VT, class XT, class YT, bool TRANS, bool RESID>
 __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slices,
                                                  const int* __restrict__ slice_ptr,
                                                  const int* __restrict__ sell_col,
                                                  const VT* __restrict__ val,
-                                                 const double* __restrict__ x,
-                                                 const double* __restrict__ b,
-                                                 double* __restrict__ y) {
+                                                 const XT* __restrict__ x,
+                                                 const YT* __restrict__ b, YT* __restrict__ y) {
+    using AT = typename std::conditional<std::is_same<VT, float>::value &&
+                                             std::is_same<XT, float>::value,
+                                         float, double>::type;
     constexpr int NS = 2 * DIM + 2;
     constexpr int NV = pair_values(DIM);
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,28 +116,28 @@ __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slice
     if (s >= n_slices) return;
     const int lane = (int)(a & 31);
     const int g0 = slice_ptr[s], g1 = slice_ptr[s + 1];
-    double acc[NS];
+    AT acc[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NS; ++k) acc[k] = AT(0);
     for (int g = g0; g < g1; ++g) {
         const int cb = sell_col[(int64_t)g * kSell + lane];
         if (cb < 0) continue;
         const VT* v = val + (int64_t)g * NV * kSell + lane;
-        const double m1 = (double)v[0], m2 = (double)v[kSell];
-        double bu[DIM], cu[DIM];
+        const AT m1 = (AT)v[0], m2 = (AT)v[kSell];
+        AT bu[DIM], cu[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            bu[k] = (double)v[(2 + k) * kSell];
-            cu[k] = (double)v[(2 + DIM + k) * kSell];
+            bu[k] = (AT)v[(2 + k) * kSell];
+            cu[k] = (AT)v[(2 + DIM + k) * kSell];
             if (TRANS) { bu[k] = -bu[k]; cu[k] = -cu[k]; }
         }
-        const double d1 = (double)v[(2 + 2 * DIM) * kSell];
-        const double d2 = (double)v[(3 + 2 * DIM) * kSell];
-        const double e = (double)v[(4 + 2 * DIM) * kSell];
-        double xb[NS];
-        load_node<NS>(x, cb, xb);
-        const double p1 = xb[DIM], p2 = xb[2 * DIM + 1];
-        double cp1 = d1 * p1 + e * p2, cp2 = d2 * p2 + e * p1;
+        const AT d1 = (AT)v[(2 + 2 * DIM) * kSell];
+        const AT d2 = (AT)v[(3 + 2 * DIM) * kSell];
+        const AT e = (AT)v[(4 + 2 * DIM) * kSell];
+        AT xb[NS];
+        load_node_as<NS, XT>(x, cb, xb);
+        const AT p1 = xb[DIM], p2 = xb[2 * DIM + 1];
+        AT cp1 = d1 * p1 + e * p2, cp2 = d2 * p2 + e * p1;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             acc[k] += m1 * xb[k] + bu[k] * p1;
@@ -85,44 +150,46 @@ __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slice
     }
     if (a >= n_rows) return;
     if (RESID) {
-        double bb[NS];
-        load_node<NS>(b, (int)a, bb);
+        double out[NS], bb[NS];
+        load_node_as<NS, YT>(b, a, bb);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) acc[k] = bb[k] - acc[k];
+        for (int k = 0; k < NS; ++k) out[k] = bb[k] - (double)acc[k];
+        store_node<NS>(y, a, out);
+    } else {
+        store_node<NS>(y, a, acc);
     }
-    store_node<NS>(y, a, acc);
 }
 
 // Chebyshev step on A = blockdiag(K1_uu, K2_uu); each velocity component of
-// network i sees the same scalar matrix with entries m_i.
-template <int DIM, class VT>
+// network i sees the same scalar matrix with entries m_i. T: vector and
+// arithmetic type; the values have the same type.
+template <int DIM, class T>
 __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_slices,
                                                    const int* __restrict__ slice_ptr,
                                                    const int* __restrict__ sell_col,
-                                                   const VT* __restrict__ val,
-                                                   const double* __restrict__ mdiag,
-                                                   const double* __restrict__ r,
-                                                   const double* __restrict__ xin,
-                                                   double* __restrict__ xout,
-                                                   double* __restrict__ d, double c1, double c2,
-                                                   int first) {
+                                                   const T* __restrict__ val,
+                                                   const T* __restrict__ mdiag,
+                                                   const T* __restrict__ r,
+                                                   const T* __restrict__ xin,
+                                                   T* __restrict__ xout, T* __restrict__ d,
+                                                   T c1, T c2, int first) {
     constexpr int NS = 2 * DIM + 2;
     constexpr int NV = pair_values(DIM);
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t s = a >> 5;
     if (s >= n_slices) return;
     const int lane = (int)(a & 31);
-    double acc[NS];
+    T acc[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NS; ++k) acc[k] = T(0);
     if (!first) {
         const int g0 = slice_ptr[s], g1 = slice_ptr[s + 1];
         for (int g = g0; g < g1; ++g) {
             const int cb = sell_col[(int64_t)g * kSell + lane];
             if (cb < 0) continue;
-            const VT* v = val + (int64_t)g * NV * kSell + lane;
-            const double m1 = (double)v[0], m2 = (double)v[kSell];
-            double xb[NS];
+            const T* v = val + (int64_t)g * NV * kSell + lane;
+            const T m1 = v[0], m2 = v[kSell];
+            T xb[NS];
             load_node<NS>(xin, cb, xb);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
@@ -132,12 +199,12 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
         }
     }
     if (a >= n_rows) return;
-    double rr[NS], dd[NS], xx[NS];
-    load_node<NS>(r, (int)a, rr);
-    const double i1 = mdiag[2 * a], i2 = mdiag[2 * a + 1];
+    T rr[NS], dd[NS], xx[NS];
+    load_node<NS>(r, a, rr);
+    const T i1 = mdiag[2 * a], i2 = mdiag[2 * a + 1];
     if (first) {
 #pragma unroll
-        for (int k = 0; k < NS; ++k) dd[k] = 0.0;
+        for (int k = 0; k < NS; ++k) dd[k] = T(0);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             dd[k] = c2 * i1 * rr[k];
@@ -147,8 +214,8 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
         store_node<NS>(xout, a, dd);
         return;
     }
-    load_node<NS>(d, (int)a, dd);
-    load_node<NS>(xin, (int)a, xx);
+    load_node<NS>(d, a, dd);
+    load_node<NS>(xin, a, xx);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         dd[k] = c1 * dd[k] + c2 * i1 * (rr[k] - acc[k]);
@@ -160,14 +227,13 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
     store_node<NS>(xout, a, xx);
 }
 
-template <int DIM, class VT, bool TRANS>
+template <int DIM, class T, bool TRANS>
 __global__ void __launch_bounds__(128) k_C_resid(int64_t n_rows, int64_t n_slices,
                                                  const int* __restrict__ slice_ptr,
                                                  const int* __restrict__ sell_col,
-                                                 const VT* __restrict__ val,
-                                                 const double* __restrict__ r,
-                                                 const double* __restrict__ yu,
-                                                 double* __restrict__ tp) {
+                                                 const T* __restrict__ val,
+                                                 const T* __restrict__ r,
+                                                 const T* __restrict__ yu, T* __restrict__ tp) {
     constexpr int NS = 2 * DIM + 2;
     constexpr int NV = pair_values(DIM);
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,16 +241,16 @@ __global__ void __launch_bounds__(128) k_C_resid(int64_t n_rows, int64_t n_slice
     if (s >= n_slices) return;
     const int lane = (int)(a & 31);
     const int g0 = slice_ptr[s], g1 = slice_ptr[s + 1];
-    double c1 = 0, c2 = 0;
+    T c1 = 0, c2 = 0;
     for (int g = g0; g < g1; ++g) {
         const int cb = sell_col[(int64_t)g * kSell + lane];
         if (cb < 0) continue;
-        const VT* v = val + (int64_t)g * NV * kSell + lane;
-        double xb[NS];
+        const T* v = val + (int64_t)g * NV * kSell + lane;
+        T xb[NS];
         load_node<NS>(yu, cb, xb);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            const double cu = (double)v[(2 + DIM + k) * kSell];
+            const T cu = v[(2 + DIM + k) * kSell];
             c1 += cu * xb[k];
             c2 += cu * xb[DIM + 1 + k];
         }
@@ -195,14 +261,13 @@ __global__ void __launch_bounds__(128) k_C_resid(int64_t n_rows, int64_t n_slice
     tp[n_rows + a] = r[a * NS + 2 * DIM + 1] - c2;
 }
 
-template <int DIM, class VT, bool TRANS>
+template <int DIM, class T, bool TRANS>
 __global__ void __launch_bounds__(128) k_B_resid(int64_t n_rows, int64_t n_slices,
                                                  const int* __restrict__ slice_ptr,
                                                  const int* __restrict__ sell_col,
-                                                 const VT* __restrict__ val,
-                                                 const double* __restrict__ r,
-                                                 const double* __restrict__ yp,
-                                                 double* __restrict__ su) {
+                                                 const T* __restrict__ val,
+                                                 const T* __restrict__ r,
+                                                 const T* __restrict__ yp, T* __restrict__ su) {
     constexpr int NS = 2 * DIM + 2;
     constexpr int NV = pair_values(DIM);
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,23 +275,23 @@ __global__ void __launch_bounds__(128) k_B_resid(int64_t n_rows, int64_t n_slice
     if (s >= n_slices) return;
     const int lane = (int)(a & 31);
     const int g0 = slice_ptr[s], g1 = slice_ptr[s + 1];
-    double acc1[DIM], acc2[DIM];
+    T acc1[DIM], acc2[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) acc1[k] = acc2[k] = 0.0;
+    for (int k = 0; k < DIM; ++k) acc1[k] = acc2[k] = T(0);
     for (int g = g0; g < g1; ++g) {
         const int cb = sell_col[(int64_t)g * kSell + lane];
         if (cb < 0) continue;
-        const VT* v = val + (int64_t)g * NV * kSell + lane;
-        const double p1 = yp[cb], p2 = yp[n_rows + cb];
+        const T* v = val + (int64_t)g * NV * kSell + lane;
+        const T p1 = yp[cb], p2 = yp[n_rows + cb];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            const double bu = (double)v[(2 + k) * kSell];
+            const T bu = v[(2 + k) * kSell];
             acc1[k] += bu * p1;
             acc2[k] += bu * p2;
         }
     }
     if (a >= n_rows) return;
-    const double sg = TRANS ? -1.0 : 1.0;
+    const T sg = TRANS ? T(-1) : T(1);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         su[a * NS + k] = r[a * NS + k] - sg * acc1[k];
@@ -254,8 +319,8 @@ __global__ void k_mass_diag(int64_t n_rows, const int* __restrict__ row_ptr,
     mdiag[2 * a + 1] = 1.0 / s2;
 }
 
-template <int DIM>
-__global__ void k_scatter_p(int64_t n_rows, const double* __restrict__ yp, double* __restrict__ z) {
+template <int DIM, class T>
+__global__ void k_scatter_p(int64_t n_rows, const T* __restrict__ yp, T* __restrict__ z) {
     constexpr int NS = 2 * DIM + 2;
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n_rows) return;
@@ -263,24 +328,37 @@ __global__ void k_scatter_p(int64_t n_rows, const double* __restrict__ yp, doubl
     z[a * NS + 2 * DIM + 1] = yp[n_rows + a];
 }
 
-template <int DIM, class VT>
-void apply_K_t(const ProblemImpl& P, const VT* val, const double* x, double* y, const double* b,
-               bool tr, cudaStream_t s) {
+template <class VT> const VT* vals_of(const ProblemImpl& P);
+template <> const double* vals_of<double>(const ProblemImpl& P) { return P.sell_val.get(); }
+template <> const float* vals_of<float>(const ProblemImpl& P) { return P.sell_val32.get(); }
+
+template <int DIM, class VT, class XT, class YT>
+void apply_K_dim(const ProblemImpl& P, const XT* x, YT* y, const YT* b, bool tr, cudaStream_t s) {
     // algorithmic bytes: every pair's values and column once, x and y once (b once if given)
-    const double vecb = (double)P.n_nodes * P.ns * 8.0;
-    const double alg = (double)P.n_pairs * (P.nv * (double)sizeof(VT) + 4.0) + vecb * (b ? 3 : 2);
+    const double vecn = (double)P.n_nodes * P.ns;
+    const double alg = (double)P.n_pairs * (P.nv * (double)sizeof(VT) + 4.0) +
+                       vecn * (double)(sizeof(XT) + sizeof(YT) + (b ? sizeof(YT) : 0));
     ProfScope prof(sizeof(VT) == 8 ? "apply_K" : "apply_K_fp32", s, alg);
     const int B = 128;
     const int grid = grid_for(P.n_slices * kSell, B);
+    const VT* val = vals_of<VT>(P);
+#define DPP_LAUNCH_APPLY(TR, RS)                                                          \
+    k_apply_K<DIM, VT, XT, YT, TR, RS><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices,          \
+                                                          P.slice_ptr.get(),              \
+                                                          P.sell_col.get(), val, x, b, y)
     if (tr) {
-        if (b) k_apply_K<DIM, VT, true, true><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(), val, x, b, y);
-        else k_apply_K<DIM, VT, true, false><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(), val, x, b, y);
+        if (b) DPP_LAUNCH_APPLY(true, true);
+        else DPP_LAUNCH_APPLY(true, false);
     } else {
-        if (b) k_apply_K<DIM, VT, false, true><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(), val, x, b, y);
-        else k_apply_K<DIM, VT, false, false><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(), val, x, b, y);
+        if (b) DPP_LAUNCH_APPLY(false, true);
+        else DPP_LAUNCH_APPLY(false, false);
     }
+#undef DPP_LAUNCH_APPLY
     DPP_LAUNCH_CK();
 }
+
+template <int DIM>
+struct DimTag { static constexpr int value = DIM; };
 
 }  // namespace
 
@@ -288,79 +366,75 @@ void apply_K(const ProblemImpl& P, const double* x, double* y, const double* b, 
              cudaStream_t s) {
     if (use32 && !P.sell_val32.get()) fail(DPP_ERR_BAD_STATE, "FP32 values were not assembled");
     if (P.dim == 2) {
-        if (use32) apply_K_t<2, float>(P, P.sell_val32.get(), x, y, b, tr, s);
-        else apply_K_t<2, double>(P, P.sell_val.get(), x, y, b, tr, s);
+        if (use32) apply_K_dim<2, float, double, double>(P, x, y, b, tr, s);
+        else apply_K_dim<2, double, double, double>(P, x, y, b, tr, s);
     } else {
-        if (use32) apply_K_t<3, float>(P, P.sell_val32.get(), x, y, b, tr, s);
-        else apply_K_t<3, double>(P, P.sell_val.get(), x, y, b, tr, s);
+        if (use32) apply_K_dim<3, float, double, double>(P, x, y, b, tr, s);
+        else apply_K_dim<3, double, double, double>(P, x, y, b, tr, s);
     }
 }
 
-#define DPP_DISPATCH_DV(DIMV, USE32, CALL)                     \
-    do {                                                        \
-        if ((DIMV) == 2) {                                      \
-            constexpr int DIM = 2;                              \
-            if (USE32) { using VT = float; CALL; }              \
-            else { using VT = double; CALL; }                   \
-        } else {                                                \
-            constexpr int DIM = 3;                              \
-            if (USE32) { using VT = float; CALL; }              \
-            else { using VT = double; CALL; }                   \
-        }                                                       \
-    } while (0)
+void apply_K32(const ProblemImpl& P, const float* x, double* y, bool tr, cudaStream_t s) {
+    if (!P.sell_val32.get()) fail(DPP_ERR_BAD_STATE, "FP32 values were not assembled");
+    if (P.dim == 2) apply_K_dim<2, float, float, double>(P, x, y, nullptr, tr, s);
+    else apply_K_dim<3, float, float, double>(P, x, y, nullptr, tr, s);
+}
 
-template <class VT> static const VT* vals_of(const ProblemImpl& P);
-template <> const double* vals_of<double>(const ProblemImpl& P) { return P.sell_val.get(); }
-template <> const float* vals_of<float>(const ProblemImpl& P) { return P.sell_val32.get(); }
-
-void mass_cheb_step(const ProblemImpl& P, const double* mdiag, const double* r, const double* xin,
-                    double* xout, double* d, double c1, double c2, bool first, bool use32,
-                    cudaStream_t s) {
-    const double vecb = (double)P.n_nodes * P.ns * 8.0;
-    const double alg = first ? 3 * vecb
-                             : (double)P.n_pairs * (2.0 * (use32 ? 4 : 8) + 4.0) + 5 * vecb;
-    ProfScope prof("mass_cheb", s, alg);
+template <class T>
+void mass_cheb_step(const ProblemImpl& P, const T* mdiag, const T* r, const T* xin, T* xout, T* d,
+                    double c1, double c2, bool first, cudaStream_t s) {
+    const double vecb = (double)P.n_nodes * P.ns * sizeof(T);
+    const double alg = first ? 3 * vecb : (double)P.n_pairs * (2.0 * sizeof(T) + 4.0) + 5 * vecb;
+    ProfScope prof(sizeof(T) == 8 ? "mass_cheb" : "mass_cheb_fp32", s, alg);
     const int B = 128;
     const int grid = grid_for(P.n_slices * kSell, B);
-    DPP_DISPATCH_DV(P.dim, use32,
-                    (k_mass_cheb<DIM, VT><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices,
-                                                             P.slice_ptr.get(), P.sell_col.get(),
-                                                             vals_of<VT>(P), mdiag, r, xin, xout,
-                                                             d, c1, c2, first ? 1 : 0)));
+    const T* val = vals_of<T>(P);
+    if (P.dim == 2)
+        k_mass_cheb<2, T><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                             P.sell_col.get(), val, mdiag, r, xin, xout, d, (T)c1,
+                                             (T)c2, first ? 1 : 0);
+    else
+        k_mass_cheb<3, T><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                             P.sell_col.get(), val, mdiag, r, xin, xout, d, (T)c1,
+                                             (T)c2, first ? 1 : 0);
     DPP_LAUNCH_CK();
 }
 
-void apply_C_resid(const ProblemImpl& P, const double* r, const double* yu, double* tp, bool tr,
-                   bool use32, cudaStream_t s) {
+template <class T>
+void apply_C_resid(const ProblemImpl& P, const T* r, const T* yu, T* tp, bool tr, cudaStream_t s) {
     const int B = 128;
     const int grid = grid_for(P.n_slices * kSell, B);
-    if (tr)
-        DPP_DISPATCH_DV(P.dim, use32,
-                        (k_C_resid<DIM, VT, true><<<grid, B, 0, s>>>(
-                            P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(),
-                            vals_of<VT>(P), r, yu, tp)));
-    else
-        DPP_DISPATCH_DV(P.dim, use32,
-                        (k_C_resid<DIM, VT, false><<<grid, B, 0, s>>>(
-                            P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(),
-                            vals_of<VT>(P), r, yu, tp)));
+    const T* val = vals_of<T>(P);
+    auto go = [&](auto tag) {
+        constexpr int DIM = decltype(tag)::value;
+        if (tr)
+            k_C_resid<DIM, T, true><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                                       P.sell_col.get(), val, r, yu, tp);
+        else
+            k_C_resid<DIM, T, false><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                                        P.sell_col.get(), val, r, yu, tp);
+    };
+    if (P.dim == 2) go(DimTag<2>());
+    else go(DimTag<3>());
     DPP_LAUNCH_CK();
 }
 
-void apply_B_resid(const ProblemImpl& P, const double* r, const double* yp, double* su, bool tr,
-                   bool use32, cudaStream_t s) {
+template <class T>
+void apply_B_resid(const ProblemImpl& P, const T* r, const T* yp, T* su, bool tr, cudaStream_t s) {
     const int B = 128;
     const int grid = grid_for(P.n_slices * kSell, B);
-    if (tr)
-        DPP_DISPATCH_DV(P.dim, use32,
-                        (k_B_resid<DIM, VT, true><<<grid, B, 0, s>>>(
-                            P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(),
-                            vals_of<VT>(P), r, yp, su)));
-    else
-        DPP_DISPATCH_DV(P.dim, use32,
-                        (k_B_resid<DIM, VT, false><<<grid, B, 0, s>>>(
-                            P.n_nodes, P.n_slices, P.slice_ptr.get(), P.sell_col.get(),
-                            vals_of<VT>(P), r, yp, su)));
+    const T* val = vals_of<T>(P);
+    auto go = [&](auto tag) {
+        constexpr int DIM = decltype(tag)::value;
+        if (tr)
+            k_B_resid<DIM, T, true><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                                       P.sell_col.get(), val, r, yp, su);
+        else
+            k_B_resid<DIM, T, false><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                                        P.sell_col.get(), val, r, yp, su);
+    };
+    if (P.dim == 2) go(DimTag<2>());
+    else go(DimTag<3>());
     DPP_LAUNCH_CK();
 }
 
@@ -377,11 +451,24 @@ void mass_diag_inv(const ProblemImpl& P, double* mdiag, bool lumped, cudaStream_
     DPP_LAUNCH_CK();
 }
 
-void scatter_p(const ProblemImpl& P, const double* yp, double* z, cudaStream_t s) {
+template <class T>
+void scatter_p(const ProblemImpl& P, const T* yp, T* z, cudaStream_t s) {
     const int B = 256;
-    if (P.dim == 2) k_scatter_p<2><<<grid_for(P.n_nodes, B), B, 0, s>>>(P.n_nodes, yp, z);
-    else k_scatter_p<3><<<grid_for(P.n_nodes, B), B, 0, s>>>(P.n_nodes, yp, z);
+    if (P.dim == 2) k_scatter_p<2, T><<<grid_for(P.n_nodes, B), B, 0, s>>>(P.n_nodes, yp, z);
+    else k_scatter_p<3, T><<<grid_for(P.n_nodes, B), B, 0, s>>>(P.n_nodes, yp, z);
     DPP_LAUNCH_CK();
 }
+
+#define DPP_INSTANTIATE(T)                                                                       \
+    template void mass_cheb_step<T>(const ProblemImpl&, const T*, const T*, const T*, T*, T*,    \
+                                    double, double, bool, cudaStream_t);                         \
+    template void apply_C_resid<T>(const ProblemImpl&, const T*, const T*, T*, bool,             \
+                                   cudaStream_t);                                                \
+    template void apply_B_resid<T>(const ProblemImpl&, const T*, const T*, T*, bool,             \
+                                   cudaStream_t);                                                \
+    template void scatter_p<T>(const ProblemImpl&, const T*, T*, cudaStream_t);
+DPP_INSTANTIATE(double)
+DPP_INSTANTIATE(float)
+#undef DPP_INSTANTIATE
 
 }  // namespace dpp
