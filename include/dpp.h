@@ -191,6 +191,13 @@ dpp_status dpp_problem_sizes(dpp_problem prob, int64_t out[6]);
 dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, double* y,
                        dpp_stream_t stream);
 
+/* y = K32 x with the FP32 copy of the pair values, FP32 x and FP32 arithmetic,
+ * FP64 y: the operator of the mixed-precision inner iteration. Requires a
+ * problem assembled with DPP_MIXED_FP32_FP64 (else DPP_ERR_BAD_STATE).
+ * x: device float [n_nodes][2d+2], 16-byte aligned; y: device double. */
+dpp_status dpp_apply_K32(dpp_problem prob, int32_t transpose, const float* x, double* y,
+                         dpp_stream_t stream);
+
 /* Copy f (device, [n_nodes][2d+2]) into `f`. */
 dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream);
 

@@ -32,7 +32,7 @@ Every function states which of the paper's passages it follows.
 """
 from .quadrature import cell_rule, facet_rule
 from .assembly import (Geometry, geometry, element_matrices, element_rhs_body,
-                       assemble, assemble_rhs, slot_index, to_nodal, from_nodal)
+                       assemble, assemble_rhs, assemble_rows, slot_index, to_nodal, from_nodal)
 from .solve import solve_direct, solve_dense, residual
 from .errors import (p1_mass_matrix, interp_l2_errors, field_rel_errors, field_slices,
                      mass_balance, FIELDS)
@@ -42,7 +42,7 @@ from .adjoint import (objective, objective_grad_x, adjoint_solve, adjoint_gradie
 
 __all__ = [
     "cell_rule", "facet_rule", "Geometry", "geometry", "element_matrices", "element_rhs_body",
-    "assemble", "assemble_rhs", "slot_index", "to_nodal", "from_nodal",
+    "assemble", "assemble_rhs", "assemble_rows", "slot_index", "to_nodal", "from_nodal",
     "solve_direct", "solve_dense", "residual",
     "p1_mass_matrix", "interp_l2_errors", "field_rel_errors", "field_slices", "mass_balance",
     "FIELDS", "field_split_blocks", "selfp_schur",

@@ -257,3 +257,24 @@ def to_nodal(x: np.ndarray, n_nodes: int) -> np.ndarray:
 def from_nodal(xn: np.ndarray) -> np.ndarray:
     """Node-interleaved [n_nodes, 2d+2] -> slot-major vector."""
     return np.ascontiguousarray(np.asarray(xn).T).ravel()
+
+
+def assemble_rows(problem, nodes):
+    """Exact rows of K and entries of f for the given nodes (oracle, sampled check).
+
+    Only the cells and boundary facets that touch the sampled nodes are
+    assembled. The sampled rows receive every contribution they have, so they
+    equal the rows of the full system. Returns (K_rows CSR [len(nodes)*ns,
+    ns*n_nodes] in slot-major numbering, f_rows, row_ids).
+    """
+    m = problem.mesh
+    nodes = np.asarray(nodes, dtype=np.int64)
+    cmask = np.isin(m.cells, nodes).any(axis=1)
+    fmask = np.isin(m.bfacets, nodes).any(axis=1)
+    K, f = assemble(m.coords, m.cells[cmask], m.bfacets[fmask], problem.logk1[cmask],
+                    problem.logk2[cmask], problem.mu, problem.beta, problem.gamma_b, problem.p01,
+                    problem.p02)
+    n = m.n_nodes
+    ns = 2 * m.dim + 2
+    rows = (np.arange(ns)[:, None] * n + nodes[None, :]).ravel()
+    return K[rows], f[rows], rows

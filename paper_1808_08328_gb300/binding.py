@@ -90,6 +90,7 @@ _SIGS = {
     "dpp_last_error": (C.c_char_p, []),
     "dpp_problem_sizes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "dpp_apply_K": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "dpp_apply_K32": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "dpp_get_rhs": (C.c_int, [_P, _P, _P]),
     "dpp_export_pairs": (C.c_int, [_P, _P, _P, _P, _P]),
     "dpp_pc_apply": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
@@ -224,6 +225,10 @@ def dpp_problem_sizes(prob: int) -> dict:
 
 def dpp_apply_K(prob: int, transpose: bool, x, y, stream: int = 0) -> None:
     _check(load().dpp_apply_K(prob, 1 if transpose else 0, _ptr(x), _ptr(y), stream or None))
+
+
+def dpp_apply_K32(prob: int, transpose: bool, x, y, stream: int = 0) -> None:
+    _check(load().dpp_apply_K32(prob, 1 if transpose else 0, _ptr(x), _ptr(y), stream or None))
 
 
 def dpp_get_rhs(prob: int, f, stream: int = 0) -> None:

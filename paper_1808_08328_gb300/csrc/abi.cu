@@ -342,6 +342,17 @@ dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, dou
     });
 }
 
+dpp_status dpp_apply_K32(dpp_problem prob, int32_t transpose, const float* x, double* y,
+                         dpp_stream_t stream) {
+    return guarded("dpp_apply_K32", [&]() -> dpp_status {
+        require(prob && x && y, "null argument");
+        require_aligned(x, "x");
+        require_aligned(y, "y");
+        apply_K32(prob->impl, x, y, transpose != 0, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
 dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream) {
     return guarded("dpp_get_rhs", [&]() -> dpp_status {
         require(prob && f, "null argument");

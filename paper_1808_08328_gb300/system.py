@@ -135,6 +135,12 @@ class DPPSystem:
         B.dpp_apply_K(self.prob, transpose, x, y, _stream(self.device))
         return y
 
+    def apply_K32(self, x: torch.Tensor, transpose: bool = False) -> torch.Tensor:
+        x = x.to(self.device, torch.float32).contiguous()
+        y = torch.empty(x.shape, dtype=torch.float64, device=self.device)
+        B.dpp_apply_K32(self.prob, transpose, x, y, _stream(self.device))
+        return y
+
     def rhs(self) -> torch.Tensor:
         f = torch.empty((self.n_nodes, self.ns), dtype=torch.float64, device=self.device)
         B.dpp_get_rhs(self.prob, f, _stream(self.device))
