@@ -162,6 +162,16 @@ dpp_status dpp_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts, do
                      dpp_solve_info* info, dpp_stream_t stream);
 
 /*
+ * As dpp_solve, but for K x = b with a caller-supplied right-hand side b
+ * (device, [n_nodes][2d+2], 16-byte aligned) instead of the assembled f.
+ * It reuses the assembled operator and preconditioner for further
+ * right-hand sides, for example corrections K d = f - K x0. opts->rtol is
+ * relative to ||b||_2. x follows opts->x_memory like dpp_solve's x.
+ */
+dpp_status dpp_solve_rhs(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts, const double* b,
+                         double* x, dpp_solve_info* info, dpp_stream_t stream);
+
+/*
  * Adjoint of the solve for J(x) with a given gradient dJdx (device,
  * [n_nodes][2d+2]). It solves K^T lambda = dJdx with the same preconditioner
  * (S_p is unchanged when B and C change sign). It then forms, for every cell

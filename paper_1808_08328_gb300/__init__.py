@@ -14,7 +14,7 @@ from .binding import (DppError, DPP_FP64, DPP_MIXED_FP32_FP64, DPP_MEM_DEVICE, D
                       dpp_destroy_problem, dpp_export_pairs, dpp_get_rhs, dpp_last_error,
                       dpp_pc_apply, dpp_pc_export_level, dpp_pc_level_sizes, dpp_pc_opts_default,
                       dpp_problem_desc, dpp_problem_sizes, dpp_setup_pc, dpp_solve,
-                      dpp_solve_opts_default, dpp_status_string)
+                      dpp_solve_opts_default, dpp_solve_rhs, dpp_status_string)
 
 
 def __getattr__(name):

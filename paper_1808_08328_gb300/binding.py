@@ -82,6 +82,8 @@ _SIGS = {
     "dpp_assemble": (C.c_int, [C.POINTER(dpp_problem_desc), C.c_int32, _P, C.POINTER(_P)]),
     "dpp_setup_pc": (C.c_int, [_P, C.POINTER(dpp_pc_opts), _P, C.POINTER(_P)]),
     "dpp_solve": (C.c_int, [_P, _P, C.POINTER(dpp_solve_opts), _P, C.POINTER(dpp_solve_info), _P]),
+    "dpp_solve_rhs": (C.c_int, [_P, _P, C.POINTER(dpp_solve_opts), _P, _P,
+                                C.POINTER(dpp_solve_info), _P]),
     "dpp_adjoint_solve": (C.c_int, [_P, _P, C.POINTER(dpp_solve_opts), _P, _P, _P, _P, _P, _P,
                                     C.POINTER(dpp_solve_info), _P]),
     "dpp_destroy_problem": (None, [_P]),
@@ -184,6 +186,15 @@ def dpp_solve(prob: int, pc: int, opts: dpp_solve_opts | None, x, stream: int = 
     info = dpp_solve_info()
     st = load().dpp_solve(prob, pc, C.byref(opts) if opts is not None else None, _ptr(x),
                           C.byref(info), stream or None)
+    _check(st, allow)
+    return info
+
+
+def dpp_solve_rhs(prob: int, pc: int, opts: dpp_solve_opts | None, b, x, stream: int = 0,
+                  allow=(DPP_OK,)) -> dpp_solve_info:
+    info = dpp_solve_info()
+    st = load().dpp_solve_rhs(prob, pc, C.byref(opts) if opts is not None else None, _ptr(b),
+                              _ptr(x), C.byref(info), stream or None)
     _check(st, allow)
     return info
 

@@ -282,6 +282,16 @@ dpp_status dpp_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts, do
     return solve_common("dpp_solve", prob, pc, opts, nullptr, x, false, info, stream);
 }
 
+dpp_status dpp_solve_rhs(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts, const double* b,
+                         double* x, dpp_solve_info* info, dpp_stream_t stream) {
+    if (!b || ((uintptr_t)b & 15u)) {
+        g_last_error = "dpp_solve_rhs: b must be a non-null, 16-byte aligned device pointer";
+        if (info) { std::memset(info, 0, sizeof(*info)); info->status = DPP_ERR_INVALID_ARGUMENT; }
+        return DPP_ERR_INVALID_ARGUMENT;
+    }
+    return solve_common("dpp_solve_rhs", prob, pc, opts, b, x, false, info, stream);
+}
+
 dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* opts,
                              const double* x, const double* dJdx, double* lambda,
                              double* dJ_dlogk1, double* dJ_dlogk2, double* dJ_dbeta,

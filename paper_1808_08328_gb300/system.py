@@ -109,6 +109,17 @@ class DPPSystem:
         info = B.dpp_solve(self.prob, self.pc, o, x, _stream(self.device), allow=allow)
         return x, info.as_dict()
 
+    def solve_rhs(self, b: torch.Tensor, check: bool = True, **opts):
+        """Solve K x = b for a given right-hand side (x0 = 0). Returns (x, info)."""
+        if not self.pc:
+            self.setup_pc()
+        o = self.solve_opts(**opts)
+        b = b.to(self.device, torch.float64).contiguous()
+        x = torch.zeros_like(b)
+        allow = (B.DPP_OK,) if check else tuple(range(9))
+        info = B.dpp_solve_rhs(self.prob, self.pc, o, b, x, _stream(self.device), allow=allow)
+        return x, info.as_dict()
+
     def adjoint(self, x: torch.Tensor, dJdx: torch.Tensor, check: bool = True, **opts):
         """Adjoint solve: (lambda, dJ/dlogk1, dJ/dlogk2, dJ/dbeta, info)."""
         if not self.pc:
