@@ -41,6 +41,15 @@ WORKLOADS = {
                                            "(profiling size: pair values 160 MB > L2)"),
     "3d48_lognormal_mixed": (3, 48, 0, 1.0, "3D 48^3 log-normal, mixed precision (profiling size)", 1),
 }
+BATCH = dict(n_inst=256, seed=0, desc="256 2D unit-square instances, N ~ U{16..128} per instance, "
+                                      "log k1~N(0,1), log k2~N(-3,1), beta log-uniform in [0.1,10], "
+                                      "FP64 outer / FP32 inner, one dpp_solve_batched call")
+
+
+def batch_problems(n_inst, seed):
+    import inputs
+    return [inputs.heterogeneous_problem(2, n, seed=si, beta=b)
+            for (n, si, b) in inputs.batch_recipe(n_inst, seed)]
 
 
 def precision_of(spec) -> int:
@@ -345,6 +354,25 @@ def bench_gb300(args):
         modes["mixed_vs_fp64_rel_l2"] = {
             k: float(torch.linalg.norm(xb[:, v] - xa[:, v]) / torch.linalg.norm(xa[:, v]))
             for k, v in sl.items()}
+        # batched workload: one dpp_solve_batched call per step
+        from paper_1808_08328_gb300.system import DPPBatch
+        bt = DPPBatch(batch_problems(BATCH["n_inst"], BATCH["seed"]), device=dev)
+        _, binfo, bst = bt.solve(precision=1, rtol=1e-10)  # warm
+        torch.cuda.synchronize(dev)
+        e2.record(torch.cuda.current_stream(dev))
+        bsteps = max(1, args.steps // 2)
+        for _ in range(bsteps):
+            _, binfo, bst = bt.solve(precision=1, rtol=1e-10)
+        e3.record(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        bms = e2.elapsed_time(e3) / bsteps
+        modes["batched"] = world * bt.n_dofs / (bms * 1e-3)
+        modes["batched_config"] = {"instances": BATCH["n_inst"], "dofs": bt.n_dofs,
+                                   "ms_per_step": bms, "status": bst,
+                                   "max_rel_residual": max(i["rel_residual"] for i in binfo),
+                                   "max_iterations": max(i["iterations"] for i in binfo),
+                                   "description": BATCH["desc"]}
+        del bt
 
     if rank != 0:
         if dist:

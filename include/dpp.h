@@ -185,6 +185,28 @@ dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* 
                              double* dJ_dlogk1, double* dJ_dlogk2, double* dJ_dbeta,
                              dpp_solve_info* info, dpp_stream_t stream);
 
+/*
+ * Solve n_inst independent systems (for example permeability realisations on
+ * meshes of different sizes) in one batched pass. descs[i] describes instance i
+ * exactly as for dpp_assemble; dim and gamma_b must agree across instances, and
+ * mu and beta may differ. The instances are assembled as one block-diagonal
+ * union. One preconditioner (pc_opts, including its precision) is built on the
+ * union; because no strength edge joins two instances, each instance keeps its
+ * own aggregates. Every instance then runs its own FGMRES, with its own inner
+ * products, Givens rotations, least-squares solves and convergence test on
+ * ||f_i - K_i x_i|| / ||f_i|| <= rtol, in lock step with the others. One restart
+ * cycle is one replay of a captured CUDA graph. xs[i]: [n_nodes_i][2d+2]
+ * (device or host per opts->x_memory; the initial guess unless opts->x0_zero).
+ * infos[i] receives that instance's status, iterations and residual. An
+ * instance with invalid input gets INVALID_ARGUMENT or NONFINITE and is left
+ * out; the others are still solved. Returns DPP_OK when every instance
+ * converged, else the first failing status. restart is limited to 62.
+ * Synchronises `stream`.
+ */
+dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
+                             const dpp_pc_opts* pc_opts, const dpp_solve_opts* opts,
+                             double* const* xs, dpp_solve_info* infos, dpp_stream_t stream);
+
 void dpp_destroy_problem(dpp_problem prob);
 void dpp_destroy_pc(dpp_pc pc);
 const char* dpp_status_string(int32_t status);

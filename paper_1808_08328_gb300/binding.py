@@ -86,6 +86,9 @@ _SIGS = {
                                 C.POINTER(dpp_solve_info), _P]),
     "dpp_adjoint_solve": (C.c_int, [_P, _P, C.POINTER(dpp_solve_opts), _P, _P, _P, _P, _P, _P,
                                     C.POINTER(dpp_solve_info), _P]),
+    "dpp_solve_batched": (C.c_int, [C.c_int32, C.POINTER(dpp_problem_desc), C.POINTER(dpp_pc_opts),
+                                    C.POINTER(dpp_solve_opts), C.POINTER(C.c_void_p),
+                                    C.POINTER(dpp_solve_info), _P]),
     "dpp_destroy_problem": (None, [_P]),
     "dpp_destroy_pc": (None, [_P]),
     "dpp_status_string": (C.c_char_p, [C.c_int32]),
@@ -207,6 +210,20 @@ def dpp_adjoint_solve(prob: int, pc: int, opts: dpp_solve_opts | None, x, dJdx, 
                                   C.byref(info), stream or None)
     _check(st, allow)
     return info
+
+
+def dpp_solve_batched(descs, pc_opts: dpp_pc_opts | None, opts: dpp_solve_opts | None, xs,
+                      stream: int = 0, allow=(DPP_OK,)):
+    """Batched solve; descs: list of dpp_problem_desc, xs: list of x buffers."""
+    n = len(descs)
+    darr = (dpp_problem_desc * n)(*descs)
+    xarr = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (dpp_solve_info * n)()
+    st = load().dpp_solve_batched(n, darr, C.byref(pc_opts) if pc_opts is not None else None,
+                                  C.byref(opts) if opts is not None else None, xarr, infos,
+                                  stream or None)
+    _check(st, allow)
+    return st, [i.as_dict() for i in infos]
 
 
 def dpp_destroy_problem(prob: int) -> None:

@@ -19,6 +19,12 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
                   HostScratch& hs);
 void adjoint_gradients(const ProblemImpl& P, const double* x, const double* lambda, double* g1,
                        double* g2, double* gbeta, cudaStream_t s);
+void assemble_union(ProblemImpl& P, int n, const dpp_problem_desc* descs, std::vector<int>& codes,
+                    cudaStream_t s);
+void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, double* x,
+                    std::vector<int>& status, std::vector<int>& iters,
+                    std::vector<double>& relres, int64_t& graph_launches, cudaStream_t s,
+                    HostScratch& hs);
 }  // namespace dpp
 
 namespace dpp {
@@ -322,6 +328,102 @@ dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* 
         DPP_CK(cudaStreamSynchronize(s));
         return DPP_OK;
     });
+}
+
+dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
+                             const dpp_pc_opts* pc_opts, const dpp_solve_opts* opts,
+                             double* const* xs, dpp_solve_info* infos, dpp_stream_t stream) {
+    std::vector<int> codes;
+    dpp_status st = guarded("dpp_solve_batched", [&]() -> dpp_status {
+        require(n_inst >= 1 && descs && xs && infos, "null argument or n_inst < 1");
+        for (int i = 0; i < n_inst; ++i) std::memset(&infos[i], 0, sizeof(dpp_solve_info));
+        dpp_pc_opts po;
+        dpp_pc_opts_default(&po);
+        if (pc_opts) po = *pc_opts;
+        dpp_solve_opts o;
+        dpp_solve_opts_default(&o);
+        if (opts) o = *opts;
+        require(o.rtol > 0 && o.rtol < 1 && o.restart >= 1 && o.restart <= 62 && o.max_iters >= 1,
+                "bad solve options (rtol in (0,1), restart in [1,62], max_iters >= 1)");
+        require(o.x_memory == DPP_MEM_DEVICE || o.x_memory == DPP_MEM_HOST, "bad x_memory");
+        require(po.precision == DPP_FP64 || po.precision == DPP_MIXED_FP32_FP64, "bad precision");
+        ensure_device();
+        cudaStream_t user = (cudaStream_t)stream;
+        // graph capture needs a stream other than the legacy default stream
+        cudaStream_t s = nullptr;
+        DPP_CK(cudaStreamSynchronize(user));
+        DPP_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        struct StreamGuard {
+            cudaStream_t s;
+            ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+        } guard{s};
+        dpp_problem_s prob;
+        dpp_pc_s pc;
+        EventTimer ta(s);
+        prob.impl.precision = po.precision;
+        assemble_union(prob.impl, n_inst, descs, codes, s);
+        const double ms_asm = ta.stop();
+        EventTimer tb(s);
+        pc.impl.opts = po;
+        pc.impl.precision = po.precision;
+        pc.owner = &prob;
+        pc_setup(pc.impl, prob.impl, s);
+        const double ms_setup = tb.stop();
+        const ProblemImpl& P = prob.impl;
+        const int64_t n = P.n_nodes * P.ns;
+        DBuf<double> x(n);
+        // initial guesses (live instances in order)
+        std::vector<int> live;
+        for (int i = 0; i < n_inst; ++i)
+            if (!codes[i]) live.push_back(i);
+        if (!o.x0_zero)
+            for (size_t k = 0; k < live.size(); ++k) {
+                const int64_t cnt = (P.inst_node_off[k + 1] - P.inst_node_off[k]) * P.ns;
+                DPP_CK(cudaMemcpyAsync(x.get() + P.inst_node_off[k] * P.ns, xs[live[k]],
+                                       cnt * sizeof(double),
+                                       o.x_memory == DPP_MEM_HOST ? cudaMemcpyHostToDevice
+                                                                  : cudaMemcpyDeviceToDevice, s));
+            }
+        EventTimer tc(s);
+        std::vector<int> status, iters;
+        std::vector<double> relres;
+        int64_t graph_launches = 0;
+        fgmres_batched(P, pc.impl, o, x.get(), status, iters, relres, graph_launches, s,
+                       prob.impl.hs);
+        for (int64_t k = 0; k < graph_launches; ++k) count_launch();
+        for (size_t k = 0; k < live.size(); ++k) {
+            const int64_t cnt = (P.inst_node_off[k + 1] - P.inst_node_off[k]) * P.ns;
+            DPP_CK(cudaMemcpyAsync(xs[live[k]], x.get() + P.inst_node_off[k] * P.ns,
+                                   cnt * sizeof(double),
+                                   o.x_memory == DPP_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                              : cudaMemcpyDeviceToDevice, s));
+        }
+        const double ms_solve = tc.stop();
+        dpp_status worst = DPP_OK;
+        for (int i = 0; i < n_inst; ++i) {
+            dpp_solve_info& inf = infos[i];
+            inf.ms_assemble = ms_asm;
+            inf.ms_setup = ms_setup;
+            inf.ms_solve = ms_solve;
+            inf.levels = (int)pc.impl.levels.size();
+            if (codes[i]) {
+                inf.status = codes[i];
+                worst = (dpp_status)codes[i];
+            }
+        }
+        for (size_t k = 0; k < live.size(); ++k) {
+            dpp_solve_info& inf = infos[live[k]];
+            inf.status = status[k];
+            inf.iterations = iters[k];
+            inf.rel_residual = relres[k];
+            inf.restarts = (iters[k] + o.restart - 1) / o.restart;
+            if (status[k] != DPP_OK && worst == DPP_OK) worst = (dpp_status)status[k];
+        }
+        DPP_CK(cudaStreamSynchronize(s));
+        if (worst != DPP_OK) g_last_error = "dpp_solve_batched: at least one instance failed (see infos)";
+        return worst;
+    });
+    return st;
 }
 
 void dpp_destroy_problem(dpp_problem p) { delete p; }

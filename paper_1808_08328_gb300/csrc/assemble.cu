@@ -229,6 +229,7 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
                                  const int* __restrict__ nc_ptr, const int* __restrict__ nc_list,
                                  const int* __restrict__ cells, const double* __restrict__ geo,
                                  const double* __restrict__ kk, double mu, double beta,
+                                 const double* __restrict__ mub,
                                  const int* __restrict__ slice_ptr, double* __restrict__ sell_val) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
@@ -238,7 +239,7 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
     const int j = (int)(p - row_ptr[a]);
     const double cm = 1.0 / ((DIM + 1) * (DIM + 2));  // (phi_a; phi_b) / |K| for a != b
     const double c1 = 1.0 / (DIM + 1);
-    double m1 = 0, m2 = 0, d1 = 0, d2 = 0, mass = 0, bu[DIM], cu[DIM];
+    double m1 = 0, m2 = 0, d1 = 0, d2 = 0, mass = 0, bmass = 0, bu[DIM], cu[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) bu[k] = cu[k] = 0;
     for (int q = nc_ptr[a]; q < nc_ptr[a + 1]; ++q) {
@@ -260,18 +261,21 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
         double dot = 0;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) dot += ga[k] * gb[k];
-        m1 += 0.5 * mu / k1 * mab;
-        m2 += 0.5 * mu / k2 * mab;
-        d1 += 0.5 * k1 / mu * vol * dot;
-        d2 += 0.5 * k2 / mu * vol * dot;
-        mass += mab;
+        // batched problems carry mu and beta per cell (one value per instance)
+        const double muc = mub ? mub[2 * c] : mu;
+        m1 += 0.5 * muc / k1 * mab;
+        m2 += 0.5 * muc / k2 * mab;
+        d1 += 0.5 * k1 / muc * vol * dot;
+        d2 += 0.5 * k2 / muc * vol * dot;
+        if (mub) bmass += mub[2 * c + 1] / muc * mab;
+        else mass += mab;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             bu[k] -= vol * c1 * (ga[k] + 0.5 * gb[k]);
             cu[k] += vol * c1 * (gb[k] + 0.5 * ga[k]);
         }
     }
-    const double bm = beta / mu * mass;
+    const double bm = mub ? bmass : beta / mu * mass;
     const int64_t grp = (int64_t)slice_ptr[a >> 5] + j;
     double* o = sell_val + grp * NV * kSell + (a & 31);
     o[0 * kSell] = m1;
@@ -356,7 +360,8 @@ __global__ void k_rhs(int64_t n_nodes, const int* __restrict__ nc_ptr,
                       const int* __restrict__ nf_ptr, const int* __restrict__ nf_list,
                       const int* __restrict__ bf, const double* __restrict__ nA,
                       const double* __restrict__ p01, const double* __restrict__ p02, double mu,
-                      double gb0, double gb1, double gb2, double* __restrict__ f) {
+                      const double* __restrict__ mub, double gb0, double gb1, double gb2,
+                      double* __restrict__ f) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= n_nodes) return;
     constexpr int S = GeoLayout<DIM>::stride;
@@ -374,9 +379,10 @@ __global__ void k_rhs(int64_t n_nodes, const int* __restrict__ nc_ptr,
         double gdot = 0;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) gdot += g[1 + la * DIM + k] * gbv[k];
+        const double muc = mub ? mub[2 * c] : mu;
         vsum += vol / (DIM + 1);
-        fp1 += 0.5 * vol * kk[2 * c] / mu * gdot;
-        fp2 += 0.5 * vol * kk[2 * c + 1] / mu * gdot;
+        fp1 += 0.5 * vol * kk[2 * c] / muc * gdot;
+        fp2 += 0.5 * vol * kk[2 * c + 1] / muc * gdot;
     }
     double fu1[DIM], fu2[DIM];
 #pragma unroll
@@ -523,7 +529,8 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
     DPP_CK(cudaMemsetAsync(P.sell_val.get(), 0, P.sell_val.bytes(), s));
     k_assemble_pairs<DIM><<<grid_for(P.n_pairs, B), B, 0, s>>>(
         P.pair_row.get(), P.col.get(), P.row_ptr.get(), P.n_pairs, P.nc_ptr.get(),
-        P.nc_list.get(), P.cells.get(), P.geo.get(), P.kk.get(), P.mu, P.beta, P.slice_ptr.get(),
+        P.nc_list.get(), P.cells.get(), P.geo.get(), P.kk.get(), P.mu, P.beta, P.cell_mu_beta.get(),
+        P.slice_ptr.get(),
         P.sell_val.get());
     DPP_LAUNCH_CK();
     if (P.precision == DPP_MIXED_FP32_FP64) {
@@ -545,18 +552,18 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
     k_rhs<DIM><<<grid_for(P.n_nodes, B), B, 0, s>>>(
         P.n_nodes, P.nc_ptr.get(), P.nc_list.get(), P.cells.get(), P.geo.get(), P.kk.get(),
         P.nf_ptr.get(), P.nf_list.get(), P.bfacets.get(), P.facet_nA.get(), P.p01.get(),
-        P.p02.get(), P.mu, P.gb[0], P.gb[1], P.gb[2], P.f.get());
+        P.p02.get(), P.mu, P.cell_mu_beta.get(), P.gb[0], P.gb[1], P.gb[2], P.f.get());
     DPP_LAUNCH_CK();
     check_status(P, s, "dpp_assemble");
 }
 
 }  // namespace
 
+void assemble_uploaded(ProblemImpl& P, cudaStream_t s);
+
 void assemble_problem(ProblemImpl& P, const dpp_problem_desc& d, cudaStream_t s) {
     const bool host = d.memory == DPP_MEM_HOST;
     P.dim = d.dim;
-    P.ns = 2 * d.dim + 2;
-    P.nv = pair_values(d.dim);
     P.n_nodes = d.n_nodes;
     P.n_cells = d.n_cells;
     P.n_bfacets = d.n_bfacets;
@@ -570,9 +577,17 @@ void assemble_problem(ProblemImpl& P, const dpp_problem_desc& d, cudaStream_t s)
     upload(P.logk2, d.log_k2, (size_t)d.n_cells, host, s);
     upload(P.p01, d.p01, (size_t)d.n_nodes, host, s);
     upload(P.p02, d.p02, (size_t)d.n_nodes, host, s);
+    assemble_uploaded(P, s);
+}
+
+// Assembly from arrays already in P (coords, cells, bfacets, log k, p0, sizes,
+// dim, mu, beta, gamma b, and the optional per-cell mu/beta of batches).
+void assemble_uploaded(ProblemImpl& P, cudaStream_t s) {
+    P.ns = 2 * P.dim + 2;
+    P.nv = pair_values(P.dim);
     P.dstatus.alloc(1);
     DPP_CK(cudaMemsetAsync(P.dstatus.get(), 0, sizeof(int), s));
-    if (d.dim == 2) assemble_dim<2>(P, s);
+    if (P.dim == 2) assemble_dim<2>(P, s);
     else assemble_dim<3>(P, s);
 }
 

@@ -1,0 +1,562 @@
+// Batched solves: many independent DPP systems (permeability realisations,
+// meshes of uneven size) in one union problem and one lock-step FGMRES.
+//
+// Union: instance b's nodes and cells are shifted by the totals of the
+// instances before it, so the union K is block-diagonal. Assembly, the selfp
+// Schur blocks (Eqs. "S4_sp1", "S4_sp2") and the smoothed-aggregation hierarchy
+// run unchanged on the union. No strength edge joins two instances, so no
+// aggregate spans two instances and every level stays block-diagonal. mu and
+// beta may differ between instances; they travel as per-cell values.
+//
+// Krylov: every instance runs its own right-preconditioned FGMRES(m): its
+// own inner products, Hessenberg matrix, Givens rotations, least-squares
+// solve and convergence test. All instances share every kernel launch.
+// Reductions are segmented by a chunk table whose chunks never straddle two
+// instances: each block reduces one chunk, then one pass adds an instance's
+// chunk partials in chunk order. The result is deterministic. The small
+// per-instance algebra runs as one device thread per instance. A restart cycle
+// (m Arnoldi steps, the update of x, the FP64 true residual and the
+// convergence flags) has no host synchronisation, so it is captured once as a
+// CUDA graph and replayed; the host reads one counter (instances still active)
+// per cycle. An instance stops contributing once its residual estimate meets
+// its target; its later basis vectors are zero.
+#include <cmath>
+#include <cstring>
+
+#include "amg.cuh"
+
+namespace dpp {
+
+void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s);
+void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
+              cudaStream_t s);
+void pc_apply32(const ProblemImpl& P, PcImpl& pc, const double* r, float* z, bool transpose,
+                cudaStream_t s);
+void set_last_error_message(const char* m);
+
+namespace {
+
+constexpr int kChunk = 4096;   // vector entries per reduction chunk
+constexpr int kSegThreads = 256;
+
+// ------------------------------------------------------------------ union construction
+__global__ void k_check_instance_cells(const int* __restrict__ cells, int64_t n_cells, int nv,
+                                       const int* __restrict__ cell_inst,
+                                       const int64_t* __restrict__ inst_nodes,
+                                       const double* __restrict__ lk1,
+                                       const double* __restrict__ lk2, int* __restrict__ flag) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    const int b = cell_inst[c];
+    int bad = 0;
+    for (int v = 0; v < nv; ++v) {
+        int a = cells[c * nv + v];
+        if (a < 0 || a >= inst_nodes[b]) bad |= kDevBadIndex;
+    }
+    if (!isfinite(lk1[c]) || !isfinite(lk2[c])) bad |= kDevNonFinite;
+    if (bad) atomicOr(&flag[b], bad);
+}
+
+__global__ void k_check_instance_nodes(const double* __restrict__ X, int64_t n, int dim,
+                                       const int* __restrict__ node_inst,
+                                       const double* __restrict__ p01,
+                                       const double* __restrict__ p02, int* __restrict__ flag) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    bool bad = !isfinite(p01[a]) || !isfinite(p02[a]);
+    for (int k = 0; k < dim; ++k) bad |= !isfinite(X[a * dim + k]);
+    if (bad) atomicOr(&flag[node_inst[a]], kDevNonFinite);
+}
+
+__global__ void k_check_instance_facets(const int* __restrict__ f, int64_t n, int dim,
+                                        const int* __restrict__ facet_inst,
+                                        const int64_t* __restrict__ inst_nodes,
+                                        int* __restrict__ flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = facet_inst[i];
+    for (int k = 0; k < dim; ++k) {
+        int a = f[i * dim + k];
+        if (a < 0 || a >= inst_nodes[b]) atomicOr(&flag[b], kDevBadIndex);
+    }
+}
+
+__global__ void k_offset_ids(int* __restrict__ ids, int64_t n, int per,
+                             const int* __restrict__ owner, const int64_t* __restrict__ off) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n * per) ids[i] += (int)off[owner[i / per]];
+}
+
+__global__ void k_fill_owner(int* __restrict__ owner, int64_t begin, int64_t end, int value) {
+    int64_t i = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < end) owner[i] = value;
+}
+
+__global__ void k_fill_mub(double* __restrict__ mub, int64_t begin, int64_t end, double mu,
+                           double beta) {
+    int64_t c = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < end) {
+        mub[2 * c] = mu;
+        mub[2 * c + 1] = beta;
+    }
+}
+
+// ------------------------------------------------------------------ segmented Krylov kernels
+// partial[chunk][j] = sum over the chunk of V_j * w (j < nvec), V row-major [nvec][ld]
+template <class VT>
+__global__ void __launch_bounds__(kSegThreads)
+k_seg_dots(const int64_t* __restrict__ beg, const int64_t* __restrict__ end, const VT* __restrict__ V,
+           int64_t ld, int nvec, const double* __restrict__ w, double* __restrict__ partial,
+           int pld) {
+    __shared__ double sh[kSegThreads / 32];
+    const int c = blockIdx.x;
+    const int64_t b0 = beg[c], b1 = end[c];
+    for (int j = 0; j < nvec; ++j) {
+        const VT* v = V + (int64_t)j * ld;
+        double acc = 0.0;
+        for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) acc += (double)v[i] * w[i];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) partial[(int64_t)c * pld + j] = acc;
+    }
+}
+
+// out[b][j] = sum over b's chunks (in order) of partial[chunk][j]
+__global__ void k_seg_finish(int nb, const int* __restrict__ inst_ch, const double* __restrict__ partial,
+                             int pld, int nvec, double* __restrict__ out, int old) {
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    for (int j = threadIdx.x; j < nvec; j += blockDim.x) {
+        double s = 0.0;
+        for (int c = inst_ch[b]; c < inst_ch[b + 1]; ++c) s += partial[(int64_t)c * pld + j];
+        out[(int64_t)b * old + j] = s;
+    }
+}
+
+// w += sign * sum_j coef[b][j] V_j over each chunk (b = the chunk's instance)
+template <class VT>
+__global__ void __launch_bounds__(kSegThreads)
+k_seg_axpy(const int* __restrict__ inst, const int64_t* __restrict__ beg,
+           const int64_t* __restrict__ end, const VT* __restrict__ V, int64_t ld, int nvec,
+           const double* __restrict__ coef, int cld, double sign, double* __restrict__ w) {
+    __shared__ double cs[64];
+    const int c = blockIdx.x;
+    const int b = inst[c];
+    if (threadIdx.x < nvec) cs[threadIdx.x] = sign * coef[(int64_t)b * cld + threadIdx.x];
+    __syncthreads();
+    for (int64_t i = beg[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < nvec; ++j) acc += cs[j] * (double)V[(int64_t)j * ld + i];
+        w[i] += acc;
+    }
+}
+
+// y = x / div[b] (0 where div[b] == 0: the instance is frozen or done)
+__global__ void __launch_bounds__(kSegThreads)
+k_seg_scale(const int* __restrict__ inst, const int64_t* __restrict__ beg,
+            const int64_t* __restrict__ end, const double* __restrict__ x,
+            const double* __restrict__ div, double* __restrict__ y) {
+    const int c = blockIdx.x;
+    const double d = div[inst[c]];
+    const double a = (d != 0.0) ? 1.0 / d : 0.0;
+    for (int64_t i = beg[c] + threadIdx.x; i < end[c]; i += blockDim.x) y[i] = a * x[i];
+}
+
+struct BatchDev {
+    double *H, *cs, *sn, *g, *y, *hcol, *hcol2, *nrm2, *hn, *beta, *bnorm, *target, *relres;
+    int *ncol, *active, *status, *iters, *n_active;
+};
+
+// Column j of every instance's Hessenberg matrix: rotations, residual estimate,
+// freeze test. One thread per instance.
+__global__ void k_batch_givens(int nb, int j, int m, BatchDev d) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    if (!d.active[b] || d.ncol[b] <= j) {  // done, or frozen earlier in this cycle
+        d.hn[b] = 0.0;
+        return;
+    }
+    double* H = d.H + (int64_t)b * (m + 1) * m;
+    double* cs = d.cs + (int64_t)b * m;
+    double* sn = d.sn + (int64_t)b * m;
+    double* g = d.g + (int64_t)b * (m + 1);
+    auto h = [&](int i) -> double& { return H[(int64_t)i * m + j]; };
+    for (int i = 0; i <= j; ++i) h(i) = d.hcol[(int64_t)b * (m + 2) + i] + d.hcol2[(int64_t)b * (m + 2) + i];
+    const double hn = sqrt(fmax(d.nrm2[b], 0.0));
+    h(j + 1) = hn;
+    for (int i = 0; i < j; ++i) {
+        double t = cs[i] * h(i) + sn[i] * h(i + 1);
+        h(i + 1) = -sn[i] * h(i) + cs[i] * h(i + 1);
+        h(i) = t;
+    }
+    const double a = h(j), c = h(j + 1);
+    const double rr = hypot(a, c);
+    cs[j] = (rr > 0) ? a / rr : 1.0;
+    sn[j] = (rr > 0) ? c / rr : 0.0;
+    h(j) = rr;
+    h(j + 1) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    d.iters[b] += 1;
+    const double est = fabs(g[j + 1]);
+    if (!isfinite(est) || !isfinite(hn)) {
+        d.status[b] = DPP_ERR_NONFINITE;
+        d.active[b] = 0;
+        d.ncol[b] = j;
+        d.hn[b] = 0.0;
+        return;
+    }
+    if (est <= d.target[b] || hn <= 1e-300 * fmax(1.0, rr) || j + 1 == m) {
+        d.ncol[b] = j + 1;
+        d.hn[b] = 0.0;  // later basis vectors of this instance are zero
+    } else {
+        d.hn[b] = hn;
+    }
+}
+
+// y = H^-1 g over the instance's ncol columns (zero for instances that are done)
+__global__ void k_batch_lsq(int nb, int m, BatchDev d) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double* y = d.y + (int64_t)b * m;
+    for (int i = 0; i < m; ++i) y[i] = 0.0;
+    if (!d.active[b]) return;
+    const double* H = d.H + (int64_t)b * (m + 1) * m;
+    const double* g = d.g + (int64_t)b * (m + 1);
+    const int n = d.ncol[b];
+    for (int i = n - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k < n; ++k) t -= H[(int64_t)i * m + k] * y[k];
+        y[i] = t / H[(int64_t)i * m + i];
+    }
+}
+
+// After the true residual: convergence test, next cycle's start values, and
+// the count of instances still active.
+__global__ void k_batch_check(int nb, int m, double rtol, double inner_rtol, int mixed,
+                              int max_iters, BatchDev d) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const double nrm = sqrt(fmax(d.nrm2[b], 0.0));
+    const double rel = (d.bnorm[b] > 0) ? nrm / d.bnorm[b] : 0.0;
+    d.ncol[b] = m;
+    double* g = d.g + (int64_t)b * (m + 1);
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    if (!d.active[b]) {
+        d.beta[b] = 0.0;
+        return;
+    }
+    d.relres[b] = rel;
+    if (!isfinite(nrm)) {
+        d.status[b] = DPP_ERR_NONFINITE;
+        d.active[b] = 0;
+        d.beta[b] = 0.0;
+        return;
+    }
+    if (rel <= rtol) {
+        d.status[b] = DPP_OK;
+        d.active[b] = 0;
+        d.beta[b] = 0.0;
+        return;
+    }
+    if (d.iters[b] >= max_iters) {
+        d.status[b] = DPP_ERR_NOT_CONVERGED;
+        d.active[b] = 0;
+        d.beta[b] = 0.0;
+        return;
+    }
+    d.beta[b] = nrm;
+    g[0] = nrm;
+    d.target[b] = mixed ? fmax(inner_rtol * nrm, 0.5 * rtol * d.bnorm[b]) : rtol * d.bnorm[b];
+    atomicAdd(d.n_active, 1);
+}
+
+__global__ void k_sqrt_copy(int nb, const double* __restrict__ a, double* __restrict__ out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) out[b] = sqrt(fmax(a[b], 0.0));
+}
+
+__global__ void k_batch_init(int nb, BatchDev d) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    d.active[b] = 1;
+    d.status[b] = DPP_ERR_NOT_CONVERGED;
+    d.iters[b] = 0;
+    d.relres[b] = 1.0;
+}
+
+inline int g1(int n) { return (n + 127) / 128; }
+
+template <class T>
+void upload_at(T* dst, const T* src, size_t n, bool host, cudaStream_t s) {
+    if (n) DPP_CK(cudaMemcpyAsync(dst, src, n * sizeof(T),
+                                  host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+}
+
+}  // namespace
+
+// Build the union problem from the valid instances. Returns per-instance
+// validation codes (0 = ok) in `codes` (host, size n).
+void assemble_union(ProblemImpl& P, int n, const dpp_problem_desc* descs, std::vector<int>& codes,
+                    cudaStream_t s) {
+    codes.assign(n, 0);
+    const int dim = descs[0].dim;
+    for (int b = 0; b < n; ++b) {
+        const dpp_problem_desc& d = descs[b];
+        bool ok = d.dim == dim && (d.dim == 2 || d.dim == 3) &&
+                  (d.memory == DPP_MEM_DEVICE || d.memory == DPP_MEM_HOST) && d.n_nodes > 0 &&
+                  d.n_cells > 0 && d.n_bfacets >= 0 && d.coords && d.cells && d.log_k1 &&
+                  d.log_k2 && d.p01 && d.p02 && (d.n_bfacets == 0 || d.bfacets) && d.mu > 0 &&
+                  std::isfinite(d.mu) && d.beta >= 0 && std::isfinite(d.beta);
+        for (int k = 0; k < dim && ok; ++k) ok = d.gamma_b[k] == descs[0].gamma_b[k];
+        if (!ok) codes[b] = DPP_ERR_INVALID_ARGUMENT;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<int> live;
+        for (int b = 0; b < n; ++b)
+            if (!codes[b]) live.push_back(b);
+        if (live.empty()) fail(DPP_ERR_INVALID_ARGUMENT, "dpp_solve_batched: no valid instance");
+        const int nl = (int)live.size();
+        std::vector<int64_t> noff(nl + 1, 0), coff(nl + 1, 0), foff(nl + 1, 0), nnodes(nl);
+        for (int i = 0; i < nl; ++i) {
+            const auto& d = descs[live[i]];
+            noff[i + 1] = noff[i] + d.n_nodes;
+            coff[i + 1] = coff[i] + d.n_cells;
+            foff[i + 1] = foff[i] + d.n_bfacets;
+            nnodes[i] = d.n_nodes;
+        }
+        if (noff[nl] >= (1LL << 30) || coff[nl] >= (1LL << 30))
+            fail(DPP_ERR_INVALID_ARGUMENT, "dpp_solve_batched: union mesh too large for int32 ids");
+        P.dim = dim;
+        P.n_nodes = noff[nl];
+        P.n_cells = coff[nl];
+        P.n_bfacets = foff[nl];
+        P.mu = 1.0;
+        P.beta = 0.0;
+        for (int k = 0; k < 3; ++k) P.gb[k] = (k < dim) ? descs[live[0]].gamma_b[k] : 0.0;
+        const int nv = dim + 1;
+        P.coords.alloc(P.n_nodes * dim);
+        P.cells.alloc(P.n_cells * nv);
+        P.bfacets.alloc(std::max<int64_t>(P.n_bfacets * dim, 1));
+        P.logk1.alloc(P.n_cells);
+        P.logk2.alloc(P.n_cells);
+        P.p01.alloc(P.n_nodes);
+        P.p02.alloc(P.n_nodes);
+        P.cell_mu_beta.alloc(2 * P.n_cells);
+        DBuf<int> cell_inst(P.n_cells), node_inst(P.n_nodes), facet_inst(std::max<int64_t>(P.n_bfacets, 1));
+        DBuf<int64_t> d_nnodes(nl), d_noff(nl);
+        DPP_CK(cudaMemcpyAsync(d_nnodes.get(), nnodes.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemcpyAsync(d_noff.get(), noff.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        for (int i = 0; i < nl; ++i) {
+            const auto& d = descs[live[i]];
+            const bool host = d.memory == DPP_MEM_HOST;
+            upload_at(P.coords.get() + noff[i] * dim, d.coords, (size_t)d.n_nodes * dim, host, s);
+            upload_at(P.cells.get() + coff[i] * nv, d.cells, (size_t)d.n_cells * nv, host, s);
+            upload_at(P.bfacets.get() + foff[i] * dim, d.bfacets, (size_t)d.n_bfacets * dim, host, s);
+            upload_at(P.logk1.get() + coff[i], d.log_k1, (size_t)d.n_cells, host, s);
+            upload_at(P.logk2.get() + coff[i], d.log_k2, (size_t)d.n_cells, host, s);
+            upload_at(P.p01.get() + noff[i], d.p01, (size_t)d.n_nodes, host, s);
+            upload_at(P.p02.get() + noff[i], d.p02, (size_t)d.n_nodes, host, s);
+            k_fill_owner<<<grid_for(d.n_cells, 256), 256, 0, s>>>(cell_inst.get(), coff[i], coff[i + 1], i);
+            DPP_LAUNCH_CK();
+            k_fill_owner<<<grid_for(d.n_nodes, 256), 256, 0, s>>>(node_inst.get(), noff[i], noff[i + 1], i);
+            DPP_LAUNCH_CK();
+            if (d.n_bfacets) {
+                k_fill_owner<<<grid_for(d.n_bfacets, 256), 256, 0, s>>>(facet_inst.get(), foff[i], foff[i + 1], i);
+                DPP_LAUNCH_CK();
+            }
+            k_fill_mub<<<grid_for(d.n_cells, 256), 256, 0, s>>>(P.cell_mu_beta.get(), coff[i], coff[i + 1], d.mu, d.beta);
+            DPP_LAUNCH_CK();
+        }
+        // per-instance validation before the ids are shifted
+        DBuf<int> flags(nl);
+        DPP_CK(cudaMemsetAsync(flags.get(), 0, nl * sizeof(int), s));
+        k_check_instance_cells<<<grid_for(P.n_cells, 256), 256, 0, s>>>(
+            P.cells.get(), P.n_cells, nv, cell_inst.get(), d_nnodes.get(), P.logk1.get(), P.logk2.get(), flags.get());
+        DPP_LAUNCH_CK();
+        k_check_instance_nodes<<<grid_for(P.n_nodes, 256), 256, 0, s>>>(
+            P.coords.get(), P.n_nodes, dim, node_inst.get(), P.p01.get(), P.p02.get(), flags.get());
+        DPP_LAUNCH_CK();
+        if (P.n_bfacets) {
+            k_check_instance_facets<<<grid_for(P.n_bfacets, 256), 256, 0, s>>>(
+                P.bfacets.get(), P.n_bfacets, dim, facet_inst.get(), d_nnodes.get(), flags.get());
+            DPP_LAUNCH_CK();
+        }
+        std::vector<int> hf(nl);
+        DPP_CK(cudaMemcpyAsync(hf.data(), flags.get(), nl * sizeof(int), cudaMemcpyDeviceToHost, s));
+        DPP_CK(cudaStreamSynchronize(s));
+        bool any_bad = false;
+        for (int i = 0; i < nl; ++i)
+            if (hf[i]) {
+                codes[live[i]] = (hf[i] & kDevBadIndex) ? DPP_ERR_INVALID_ARGUMENT : DPP_ERR_NONFINITE;
+                any_bad = true;
+            }
+        if (any_bad) {
+            if (pass == 1) fail(DPP_ERR_INVALID_ARGUMENT, "dpp_solve_batched: validation did not settle");
+            continue;  // rebuild without the rejected instances
+        }
+        k_offset_ids<<<grid_for(P.n_cells * nv, 256), 256, 0, s>>>(P.cells.get(), P.n_cells, nv,
+                                                                   cell_inst.get(), d_noff.get());
+        DPP_LAUNCH_CK();
+        if (P.n_bfacets) {
+            k_offset_ids<<<grid_for(P.n_bfacets * dim, 256), 256, 0, s>>>(
+                P.bfacets.get(), P.n_bfacets, dim, facet_inst.get(), d_noff.get());
+            DPP_LAUNCH_CK();
+        }
+        P.n_inst = nl;
+        P.inst_node_off = noff;
+        P.inst_cell_off = coff;
+        P.inst_mu.resize(nl);
+        P.inst_beta.resize(nl);
+        for (int i = 0; i < nl; ++i) {
+            P.inst_mu[i] = descs[live[i]].mu;
+            P.inst_beta[i] = descs[live[i]].beta;
+        }
+        assemble_uploaded(P, s);
+        return;
+    }
+}
+
+// Lock-step FGMRES over the instances of a union problem. Per-instance results
+// go to status/iters/relres (host vectors, size n_inst).
+void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, double* x,
+                    std::vector<int>& status, std::vector<int>& iters,
+                    std::vector<double>& relres, int64_t& graph_launches, cudaStream_t s,
+                    HostScratch& hs) {
+    const int nb = P.n_inst;
+    const int64_t n = P.n_nodes * P.ns;
+    const int m = std::min(std::max(o.restart, 1), 62);
+    const bool mixed = pc.precision == DPP_MIXED_FP32_FP64;
+    // chunk table over vector entries
+    std::vector<int64_t> cb, ce;
+    std::vector<int> ci, ich(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        const int64_t e0 = P.inst_node_off[b] * P.ns, e1 = P.inst_node_off[b + 1] * P.ns;
+        ich[b] = (int)cb.size();
+        for (int64_t e = e0; e < e1; e += kChunk) {
+            cb.push_back(e);
+            ce.push_back(std::min<int64_t>(e + kChunk, e1));
+            ci.push_back(b);
+        }
+    }
+    ich[nb] = (int)cb.size();
+    const int nch = (int)cb.size();
+    DBuf<int64_t> d_cb(nch), d_ce(nch);
+    DBuf<int> d_ci(nch), d_ich(nb + 1);
+    DPP_CK(cudaMemcpyAsync(d_cb.get(), cb.data(), nch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DPP_CK(cudaMemcpyAsync(d_ce.get(), ce.data(), nch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    DPP_CK(cudaMemcpyAsync(d_ci.get(), ci.data(), nch * sizeof(int), cudaMemcpyHostToDevice, s));
+    DPP_CK(cudaMemcpyAsync(d_ich.get(), ich.data(), (nb + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    const int pld = m + 2;
+    DBuf<double> V((size_t)(m + 1) * n), Z(mixed ? 1 : (size_t)m * n), w(n), r(n), partial((size_t)nch * pld);
+    DBuf<float> Z32(mixed ? (size_t)m * n : 1);
+    DBuf<double> H((size_t)nb * (m + 1) * m), cs((size_t)nb * m), sn((size_t)nb * m), g((size_t)nb * (m + 1)),
+        y((size_t)nb * m), hcol((size_t)nb * pld), hcol2((size_t)nb * pld), nrm2(nb), hn(nb), beta(nb),
+        bnorm(nb), target(nb), rel(nb);
+    DBuf<int> ncol(nb), active(nb), st(nb), it(nb), n_active(1);
+    BatchDev d{H.get(), cs.get(), sn.get(), g.get(), y.get(), hcol.get(), hcol2.get(), nrm2.get(),
+               hn.get(), beta.get(), bnorm.get(), target.get(), rel.get(), ncol.get(), active.get(),
+               st.get(), it.get(), n_active.get()};
+    const double* f = P.f.get();
+    auto seg_dot = [&](const double* Vv, int64_t ld, int nvec, const double* wv, double* out, int old) {
+        k_seg_dots<double><<<nch, kSegThreads, 0, s>>>(d_cb.get(), d_ce.get(), Vv, ld, nvec, wv, partial.get(), pld);
+        DPP_LAUNCH_CK();
+        k_seg_finish<<<nb, 64, 0, s>>>(nb, d_ich.get(), partial.get(), pld, nvec, out, old);
+        DPP_LAUNCH_CK();
+    };
+    // ||f_b||, initial x, residual and flags
+    seg_dot(f, 0, 1, f, nrm2.get(), 1);
+    k_sqrt_copy<<<g1(nb), 128, 0, s>>>(nb, nrm2.get(), bnorm.get());
+    DPP_LAUNCH_CK();
+    if (o.x0_zero) DPP_CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    k_batch_init<<<g1(nb), 128, 0, s>>>(nb, d);
+    DPP_LAUNCH_CK();
+    auto tail = [&]() {  // true residual, convergence test, v_0 of the next cycle
+        apply_K(P, x, r.get(), f, false, false, s);
+        seg_dot(r.get(), 0, 1, r.get(), nrm2.get(), 1);
+        DPP_CK(cudaMemsetAsync(n_active.get(), 0, sizeof(int), s));
+        k_batch_check<<<g1(nb), 128, 0, s>>>(nb, m, o.rtol, o.inner_rtol, mixed ? 1 : 0, o.max_iters, d);
+        DPP_LAUNCH_CK();
+        k_seg_scale<<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), r.get(), beta.get(), V.get());
+        DPP_LAUNCH_CK();
+    };
+    tail();
+    // one restart cycle, captured once and replayed
+    auto cycle = [&]() {
+        for (int j = 0; j < m; ++j) {
+            double* vj = V.get() + (size_t)j * n;
+            if (mixed) {
+                float* zj = Z32.get() + (size_t)j * n;
+                pc_apply32(P, pc, vj, zj, false, s);
+                apply_K32(P, zj, w.get(), false, s);
+            } else {
+                double* zj = Z.get() + (size_t)j * n;
+                pc_apply(P, pc, vj, zj, false, s);
+                apply_K(P, zj, w.get(), nullptr, false, false, s);
+            }
+            seg_dot(V.get(), n, j + 1, w.get(), hcol.get(), pld);
+            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1, hcol.get(), pld, -1.0, w.get());
+            DPP_LAUNCH_CK();
+            seg_dot(V.get(), n, j + 1, w.get(), hcol2.get(), pld);
+            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1, hcol2.get(), pld, -1.0, w.get());
+            DPP_LAUNCH_CK();
+            seg_dot(w.get(), 0, 1, w.get(), nrm2.get(), 1);
+            k_batch_givens<<<g1(nb), 128, 0, s>>>(nb, j, m, d);
+            DPP_LAUNCH_CK();
+            if (j + 1 < m) {
+                k_seg_scale<<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), w.get(), hn.get(),
+                                                        V.get() + (size_t)(j + 1) * n);
+                DPP_LAUNCH_CK();
+            }
+        }
+        k_batch_lsq<<<g1(nb), 128, 0, s>>>(nb, m, d);
+        DPP_LAUNCH_CK();
+        if (mixed)
+            k_seg_axpy<float><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z32.get(), n, m, y.get(), m, 1.0, x);
+        else
+            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z.get(), n, m, y.get(), m, 1.0, x);
+        DPP_LAUNCH_CK();
+        tail();
+    };
+    int active_now = read_scalar(n_active.get(), s, hs);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t graph_kernels = 0;
+    const int max_cycles = (o.max_iters + m - 1) / m + 1;
+    try {
+        if (active_now > 0) {
+            DPP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                cycle();
+            } catch (...) {
+                cudaStreamEndCapture(s, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            DPP_CK(cudaStreamEndCapture(s, &graph));
+            DPP_CK(cudaGraphInstantiate(&exec, graph, 0));
+            size_t nn = 0;
+            DPP_CK(cudaGraphGetNodes(graph, nullptr, &nn));
+            graph_kernels = nn;
+        }
+        for (int cyc = 0; cyc < max_cycles && active_now > 0; ++cyc) {
+            DPP_CK(cudaGraphLaunch(exec, s));
+            graph_launches += (int64_t)graph_kernels;
+            active_now = read_scalar(n_active.get(), s, hs);
+        }
+    } catch (...) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    status.resize(nb);
+    iters.resize(nb);
+    relres.resize(nb);
+    DPP_CK(cudaMemcpyAsync(status.data(), st.get(), nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaMemcpyAsync(iters.data(), it.get(), nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaMemcpyAsync(relres.data(), rel.get(), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaStreamSynchronize(s));
+}
+
+}  // namespace dpp

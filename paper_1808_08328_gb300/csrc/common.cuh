@@ -53,6 +53,9 @@ struct ProfScope {
     cudaEvent_t a = nullptr, b = nullptr;
     ProfScope(const char* family, cudaStream_t st, double alg_bytes) {
         if (!profiling_enabled()) return;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+            return;  // no event records inside a graph capture
         fam = family;
         s = st;
         bytes = alg_bytes;

@@ -43,6 +43,11 @@ struct ProblemImpl {
     DBuf<double> sell_val;  // [n_groups][nv][32]
     DBuf<float> sell_val32; // FP32 copy (mixed precision)
 
+    DBuf<double> cell_mu_beta;  // [n_cells][2]: per-cell mu, beta (batched problems only)
+    // batched problems: instance b owns nodes inst_node_off[b] .. inst_node_off[b+1]-1
+    int n_inst = 1;
+    std::vector<int64_t> inst_node_off, inst_cell_off;
+    std::vector<double> inst_mu, inst_beta;
     DBuf<double> geo;       // [n_cells][GeoLayout<dim>::stride]
     DBuf<double> kk;        // [n_cells][2]: k1, k2
     DBuf<double> f;         // [n_nodes][ns]

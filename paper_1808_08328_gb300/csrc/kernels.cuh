@@ -6,6 +6,7 @@
 namespace dpp {
 
 void assemble_problem(ProblemImpl& P, const dpp_problem_desc& d, cudaStream_t s);
+void assemble_uploaded(ProblemImpl& P, cudaStream_t s);
 
 // ---- node-pair (SELL-32) operators on node-interleaved vectors ----
 // y = K x (transpose: K^T x). If b != nullptr: y = b - K x. use32: FP32 values

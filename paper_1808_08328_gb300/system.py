@@ -232,3 +232,58 @@ class DPPSolve(torch.autograd.Function):
         _, g1, g2, gb, _ = sysm.adjoint(x, grad_x.contiguous(), **ctx.opts.get("solve", {}))
         sysm.close()
         return g1, g2, gb.reshape(1), None, None
+
+
+class DPPBatch:
+    """Device-resident inputs of many problems for dpp_solve_batched.
+
+    ``problems``: objects with the fields of a problem description (mesh with
+    coords/cells/bfacets, logk1, logk2, mu, beta, gamma_b, p01, p02).
+    """
+
+    def __init__(self, problems, device="cuda"):
+        self.device = torch.device(device)
+        dev = self.device
+        self.keep, self.descs, self.xs = [], [], []
+        for p in problems:
+            m = p.mesh
+            t = dict(coords=_dev(m.coords, torch.float64, dev), cells=_dev(m.cells, torch.int32, dev),
+                     bfacets=_dev(m.bfacets, torch.int32, dev),
+                     log_k1=_dev(p.logk1, torch.float64, dev),
+                     log_k2=_dev(p.logk2, torch.float64, dev), p01=_dev(p.p01, torch.float64, dev),
+                     p02=_dev(p.p02, torch.float64, dev))
+            self.keep.append(t)
+            d = B.dpp_problem_desc()
+            d.dim = int(m.coords.shape[1])
+            d.memory = B.DPP_MEM_DEVICE
+            d.n_nodes = int(m.coords.shape[0])
+            d.n_cells = int(m.cells.shape[0])
+            d.n_bfacets = int(m.bfacets.shape[0])
+            for k in ("coords", "cells", "bfacets", "log_k1", "log_k2", "p01", "p02"):
+                setattr(d, k, t[k].data_ptr() if t[k].numel() else None)
+            d.mu, d.beta = float(p.mu), float(p.beta)
+            gb = list(np.asarray(p.gamma_b, dtype=np.float64).ravel()) + [0.0] * 3
+            for k in range(3):
+                d.gamma_b[k] = gb[k]
+            self.descs.append(d)
+            self.xs.append(torch.zeros((d.n_nodes, 2 * d.dim + 2), dtype=torch.float64, device=dev))
+        self.n_dofs = sum(int(x.numel()) for x in self.xs)
+
+    def solve(self, precision: int = B.DPP_FP64, pc_opts: dict | None = None, **solve_opts):
+        """Returns (list of x tensors, list of per-instance info dicts, status)."""
+        po = B.dpp_pc_opts_default()
+        po.precision = precision
+        for k, v in (pc_opts or {}).items():
+            setattr(po, k, v)
+        so = B.dpp_solve_opts_default()
+        for k, v in solve_opts.items():
+            setattr(so, k, v)
+        st, infos = B.dpp_solve_batched(self.descs, po, so, self.xs, _stream(self.device),
+                                        allow=tuple(range(9)))
+        return self.xs, infos, st
+
+
+def solve_batched(problems, precision: int = B.DPP_FP64, device="cuda", pc_opts: dict | None = None,
+                  **solve_opts):
+    """One-shot batched solve; see DPPBatch."""
+    return DPPBatch(problems, device).solve(precision, pc_opts, **solve_opts)

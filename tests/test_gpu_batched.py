@@ -1,0 +1,82 @@
+"""Batched solves (dpp_solve_batched) against per-instance oracle solves.
+
+A batch of 2D instances of uneven size (N = 6 ... 24 squares per edge), with
+log-normal fields drawn from separate seeds and beta log-uniform in
+[0.1, 10], is solved in one call. This is the recipe of the batched workload
+at sizes the oracle factors in seconds. Every instance must meet the single-solve
+bar: per-field relative L2 error <= 1e-8 against its own direct solve, at its
+own true relative residual <= 1e-10. The faults are injected on the host: a NaN
+in one instance's log k, an out-of-range node id in another, and an iteration
+cap. They must give per-instance statuses and leave the other instances
+correct.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from oracle.assembly import assemble_problem
+
+from gpu_helpers import needs_gpu, system_cls, torch
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+def _batch(seed=0, sizes=(6, 11, 17, 24, 9)):
+    out = []
+    g = inputs.rng(seed)
+    for i, n in enumerate(sizes):
+        beta = float(10.0 ** g.uniform(-1.0, 1.0))
+        out.append(inputs.heterogeneous_problem(2, n, seed=seed + 1 + i, beta=beta))
+    return out
+
+
+def _check(P, x):
+    K, f = assemble_problem(P)
+    ref = oracle.to_nodal(oracle.solve_direct(K, f), P.mesh.n_nodes)
+    xn = x.cpu().numpy()
+    assert oracle.residual(K, oracle.from_nodal(xn), f) <= 1.5e-10
+    err = oracle.field_rel_errors(xn, ref)
+    assert max(err.values()) <= 1e-8, err
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_batched_matches_per_instance_oracle(precision):
+    system_cls()
+    from paper_1808_08328_gb300.system import solve_batched
+    probs = _batch()
+    xs, infos, st = solve_batched(probs, precision=precision, rtol=1e-10)
+    assert st == 0
+    for P, x, inf in zip(probs, xs, infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        _check(P, x)
+
+
+def test_batched_faults_are_per_instance():
+    system_cls()
+    from paper_1808_08328_gb300 import binding as B
+    from paper_1808_08328_gb300.system import solve_batched
+    probs = _batch(seed=5)
+    lk = probs[1].logk1.copy()
+    lk[3] = np.nan
+    probs[1] = probs[1].with_(logk1=lk)
+    mesh = probs[3].mesh
+    bad = mesh.cells.copy()
+    bad[0, 0] = mesh.n_nodes + 7
+    probs[3] = probs[3].with_(mesh=inputs.Mesh(mesh.dim, mesh.coords, bad, mesh.bfacets, mesh.n))
+    xs, infos, st = solve_batched(probs, rtol=1e-10)
+    assert infos[1]["status"] == B.DPP_ERR_NONFINITE
+    assert infos[3]["status"] == B.DPP_ERR_INVALID_ARGUMENT
+    assert st != 0
+    for i in (0, 2, 4):
+        assert infos[i]["status"] == 0
+        _check(probs[i], xs[i])
+
+
+def test_batched_iteration_cap():
+    system_cls()
+    from paper_1808_08328_gb300 import binding as B
+    from paper_1808_08328_gb300.system import solve_batched
+    xs, infos, st = solve_batched(_batch(seed=9), rtol=1e-10, max_iters=2, restart=2)
+    assert st == B.DPP_ERR_NOT_CONVERGED
+    assert all(i["status"] == B.DPP_ERR_NOT_CONVERGED for i in infos)
