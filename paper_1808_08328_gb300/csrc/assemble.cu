@@ -158,11 +158,15 @@ __global__ void k_sell_cols(const int* __restrict__ row_ptr, const int* __restri
         sell_col[(int64_t)(g0 + j) * kSell + lane] = (j < len) ? col[rs + j] : -1;
 }
 
+// Per-cell factors of the pair values (index: meaning):
+// 0: |K|/(d+1)  1: |K|/((d+1)(d+2))  2: mu/(2 k1)  3: mu/(2 k2)  4: k1 |K|/(2 mu)
+// 5: k2 |K|/(2 mu)  6: beta/mu  7: unused
 template <int DIM>
 __global__ void k_cell_geometry(const double* __restrict__ X, const int* __restrict__ cells,
                                 int64_t n_cells, const double* __restrict__ lk1,
-                                const double* __restrict__ lk2, double* __restrict__ geo,
-                                double* __restrict__ kk, int* status) {
+                                const double* __restrict__ lk2, double mu, double beta,
+                                const double* __restrict__ mub, double* __restrict__ geo,
+                                double* __restrict__ kk, double* __restrict__ coef, int* status) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     constexpr int S = GeoLayout<DIM>::stride;
@@ -218,18 +222,30 @@ __global__ void k_cell_geometry(const double* __restrict__ X, const int* __restr
     for (int v = 0; v <= DIM; ++v)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) o[1 + v * DIM + k] = g[v][k];
-    kk[2 * c] = exp(lk1[c]);
-    kk[2 * c + 1] = exp(lk2[c]);
+    const double k1 = exp(lk1[c]), k2 = exp(lk2[c]);
+    kk[2 * c] = k1;
+    kk[2 * c + 1] = k2;
+    const double muc = mub ? mub[2 * c] : mu, bc = mub ? mub[2 * c + 1] : beta;
+    double* cf = coef + c * kCellCoef;
+    cf[0] = vol / (DIM + 1);
+    cf[1] = vol / ((DIM + 1) * (DIM + 2));
+    cf[2] = 0.5 * muc / k1;
+    cf[3] = 0.5 * muc / k2;
+    cf[4] = 0.5 * k1 / muc * vol;
+    cf[5] = 0.5 * k2 / muc * vol;
+    cf[6] = bc / muc;
+    cf[7] = 0.0;
 }
 
 // One thread per node pair: fixed-order gather over the cells of the row node.
+// The per-cell factors come precomputed from k_cell_geometry (no division here;
+// FP64 division is costly on GB300's FP64 pipe).
 template <int DIM>
 __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __restrict__ col,
                                  const int* __restrict__ row_ptr, int64_t n_pairs,
                                  const int* __restrict__ nc_ptr, const int* __restrict__ nc_list,
                                  const int* __restrict__ cells, const double* __restrict__ geo,
-                                 const double* __restrict__ kk, double mu, double beta,
-                                 const double* __restrict__ mub,
+                                 const double* __restrict__ coef,
                                  const int* __restrict__ slice_ptr, double* __restrict__ sell_val) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
@@ -237,45 +253,45 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
     constexpr int NV = pair_values(DIM);
     const int a = pair_row[p], b = col[p];
     const int j = (int)(p - row_ptr[a]);
-    const double cm = 1.0 / ((DIM + 1) * (DIM + 2));  // (phi_a; phi_b) / |K| for a != b
-    const double c1 = 1.0 / (DIM + 1);
-    double m1 = 0, m2 = 0, d1 = 0, d2 = 0, mass = 0, bmass = 0, bu[DIM], cu[DIM];
+    const double self = (a == b) ? 2.0 : 1.0;
+    double m1 = 0, m2 = 0, d1 = 0, d2 = 0, bm = 0, bu[DIM], cu[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) bu[k] = cu[k] = 0;
     for (int q = nc_ptr[a]; q < nc_ptr[a + 1]; ++q) {
         const int c = nc_list[q];
         int la = -1, lb = -1;
+        if constexpr (DIM == 3) {
+            const int4 v = *reinterpret_cast<const int4*>(cells + (int64_t)c * 4);
+            la = (v.x == a) ? 0 : (v.y == a) ? 1 : (v.z == a) ? 2 : 3;
+            lb = (v.x == b) ? 0 : (v.y == b) ? 1 : (v.z == b) ? 2 : (v.w == b) ? 3 : -1;
+        } else {
 #pragma unroll
-        for (int v = 0; v <= DIM; ++v) {
-            int n = cells[(int64_t)c * (DIM + 1) + v];
-            if (n == a) la = v;
-            if (n == b) lb = v;
+            for (int v = 0; v <= DIM; ++v) {
+                int n = cells[(int64_t)c * (DIM + 1) + v];
+                if (n == a) la = v;
+                if (n == b) lb = v;
+            }
         }
         if (lb < 0) continue;
         const double* g = geo + (int64_t)c * S;
-        const double vol = g[0];
         const double* ga = g + 1 + la * DIM;
         const double* gb = g + 1 + lb * DIM;
-        const double k1 = kk[2 * c], k2 = kk[2 * c + 1];
-        const double mab = vol * cm * (a == b ? 2.0 : 1.0);
+        const double* cf = coef + (int64_t)c * kCellCoef;
+        const double mab = cf[1] * self;           // (phi_a; phi_b)_K
         double dot = 0;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) dot += ga[k] * gb[k];
-        // batched problems carry mu and beta per cell (one value per instance)
-        const double muc = mub ? mub[2 * c] : mu;
-        m1 += 0.5 * muc / k1 * mab;
-        m2 += 0.5 * muc / k2 * mab;
-        d1 += 0.5 * k1 / muc * vol * dot;
-        d2 += 0.5 * k2 / muc * vol * dot;
-        if (mub) bmass += mub[2 * c + 1] / muc * mab;
-        else mass += mab;
+        m1 += cf[2] * mab;                          // 1/2 mu/k1 (phi_a; phi_b)
+        m2 += cf[3] * mab;
+        d1 += cf[4] * dot;                          // 1/2 k1/mu |K| g_a.g_b
+        d2 += cf[5] * dot;
+        bm += cf[6] * mab;                          // beta/mu (phi_a; phi_b)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            bu[k] -= vol * c1 * (ga[k] + 0.5 * gb[k]);
-            cu[k] += vol * c1 * (gb[k] + 0.5 * ga[k]);
+            bu[k] -= cf[0] * (ga[k] + 0.5 * gb[k]);  // cf[0] = |K|/(d+1)
+            cu[k] += cf[0] * (gb[k] + 0.5 * ga[k]);
         }
     }
-    const double bm = mub ? bmass : beta / mu * mass;
     const int64_t grp = (int64_t)slice_ptr[a >> 5] + j;
     double* o = sell_val + grp * NV * kSell + (a & 31);
     o[0 * kSell] = m1;
@@ -519,9 +535,10 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
     // 5. cell geometry and permeabilities
     P.geo.alloc(P.n_cells * GeoLayout<DIM>::stride);
     P.kk.alloc(P.n_cells * 2);
+    P.ccoef.alloc(P.n_cells * kCellCoef);
     k_cell_geometry<DIM><<<grid_for(P.n_cells, B), B, 0, s>>>(
-        P.coords.get(), P.cells.get(), P.n_cells, P.logk1.get(), P.logk2.get(), P.geo.get(),
-        P.kk.get(), P.dstatus.get());
+        P.coords.get(), P.cells.get(), P.n_cells, P.logk1.get(), P.logk2.get(), P.mu, P.beta,
+        P.cell_mu_beta.get(), P.geo.get(), P.kk.get(), P.ccoef.get(), P.dstatus.get());
     DPP_LAUNCH_CK();
 
     // 6. pair values
@@ -529,8 +546,7 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
     DPP_CK(cudaMemsetAsync(P.sell_val.get(), 0, P.sell_val.bytes(), s));
     k_assemble_pairs<DIM><<<grid_for(P.n_pairs, B), B, 0, s>>>(
         P.pair_row.get(), P.col.get(), P.row_ptr.get(), P.n_pairs, P.nc_ptr.get(),
-        P.nc_list.get(), P.cells.get(), P.geo.get(), P.kk.get(), P.mu, P.beta, P.cell_mu_beta.get(),
-        P.slice_ptr.get(),
+        P.nc_list.get(), P.cells.get(), P.geo.get(), P.ccoef.get(), P.slice_ptr.get(),
         P.sell_val.get());
     DPP_LAUNCH_CK();
     if (P.precision == DPP_MIXED_FP32_FP64) {

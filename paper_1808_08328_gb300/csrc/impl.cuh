@@ -11,6 +11,9 @@ template <int DIM> struct GeoLayout;
 template <> struct GeoLayout<2> { static constexpr int stride = 8; };
 template <> struct GeoLayout<3> { static constexpr int stride = 16; };
 
+// Per-cell factors of the pair values, written by the geometry kernel.
+constexpr int kCellCoef = 8;
+
 // Values stored per node pair (a, b): m1, m2, Kup[d], Kpu[d], d1, d2, e.
 __host__ __device__ constexpr int pair_values(int dim) { return 2 + 2 * dim + 3; }
 
@@ -50,6 +53,7 @@ struct ProblemImpl {
     std::vector<double> inst_mu, inst_beta;
     DBuf<double> geo;       // [n_cells][GeoLayout<dim>::stride]
     DBuf<double> kk;        // [n_cells][2]: k1, k2
+    DBuf<double> ccoef;     // [n_cells][kCellCoef]: factors of the pair values
     DBuf<double> f;         // [n_nodes][ns]
     DBuf<int> dstatus;      // device status word
     HostScratch hs;
