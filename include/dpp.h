@@ -92,12 +92,12 @@ typedef struct {
 
 /* Preconditioner options (Section 4.2, Method 2; defaults from dpp_pc_opts_default). */
 typedef struct {
-    int32_t cheb_degree_mass;  /* Chebyshev-Jacobi degree for A^-1 (default 3) */
+    int32_t cheb_degree_mass;  /* Chebyshev-Jacobi degree for A^-1 (default 2) */
     int32_t cheb_degree_amg;   /* Chebyshev-Jacobi pre/post smoothing degree (default 2) */
     int32_t coarse_max_rows;   /* stop coarsening at or below this many rows (default 384) */
     int32_t max_levels;        /* hierarchy depth cap (default 12) */
     double strength_theta;     /* SA symmetric strength threshold (default 0.02) */
-    double cheb_ratio;         /* AMG smoothing interval [lmax/ratio, 1.1 lmax] (default 20) */
+    double cheb_ratio;         /* AMG smoothing interval [lmax/ratio, 1.1 lmax] (default 10) */
     int32_t use_lumped_diag;   /* 0: diag(K_uu) as written (default); 1: row-sum lumping */
     int32_t precision;         /* dpp_precision of the hierarchy values */
 } dpp_pc_opts;

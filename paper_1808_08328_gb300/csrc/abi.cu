@@ -127,12 +127,12 @@ extern "C" {
 
 void dpp_pc_opts_default(dpp_pc_opts* o) {
     if (!o) return;
-    o->cheb_degree_mass = 3;
+    o->cheb_degree_mass = 2;
     o->cheb_degree_amg = 2;
     o->coarse_max_rows = 384;
     o->max_levels = 12;
     o->strength_theta = 0.02;
-    o->cheb_ratio = 20.0;
+    o->cheb_ratio = 10.0;
     o->use_lumped_diag = 0;
     o->precision = DPP_FP64;
 }

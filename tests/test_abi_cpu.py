@@ -44,7 +44,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_defaults_and_status_strings(lib):
     o = lib.dpp_pc_opts_default()
-    assert o.cheb_degree_mass == 3 and o.cheb_degree_amg == 2 and o.precision == lib.DPP_FP64
+    assert o.cheb_degree_mass == 2 and o.cheb_degree_amg == 2 and o.precision == lib.DPP_FP64
+    assert o.cheb_ratio == 10.0
     s = lib.dpp_solve_opts_default()
     assert s.rtol == 1e-10 and s.restart == 30 and s.x0_zero == 1
     assert lib.dpp_status_string(lib.DPP_ERR_NOT_CONVERGED) == "DPP_ERR_NOT_CONVERGED"
