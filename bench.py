@@ -280,9 +280,9 @@ def bench_gb300(args):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     launches = B.dpp_launch_count() - l0
-    fam = {f: B.dpp_profile_read(f) for f in ("apply_K", "amg_csr_spmv", "mass_cheb",
-                                              "apply_K_fp32", "amg_csr_spmv_fp32",
-                                              "mass_cheb_fp32")}
+    fam = {f: B.dpp_profile_read(f) for f in ("apply_K", "amg_spmv_L0", "amg_csr_spmv",
+                                              "mass_cheb", "apply_K_fp32", "amg_spmv_L0_fp32",
+                                              "amg_csr_spmv_fp32", "mass_cheb_fp32")}
     fam = {k: v for k, v in fam.items() if v["launches"]}
     phases = {f: B.dpp_profile_read(f)["ms"] / args.steps
               for f in ("assemble", "setup_selfp", "setup_amg", "setup_power", "setup_aggregate",

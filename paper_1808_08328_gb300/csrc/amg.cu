@@ -80,10 +80,11 @@ template <> const double* vals<double>(const Csr& A) { return A.val.get(); }
 template <> const float* vals<float>(const Csr& A) { return A.val32.get(); }
 
 template <int MODE, class T>
-void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStream_t s) {
+void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStream_t s,
+                const char* family = nullptr) {
     const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (double)(A.n_rows + 1) * 4.0 +
                        (double)A.n_cols * sizeof(T) + (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : 2);
-    ProfScope prof(sizeof(T) == 8 ? "amg_csr_spmv" : "amg_csr_spmv_fp32", s, alg);
+    ProfScope prof(family ? family : (sizeof(T) == 8 ? "amg_csr_spmv" : "amg_csr_spmv_fp32"), s, alg);
     const int B = 256;
     const int64_t thr = A.n_rows * lanes;
     const int g = grid_for(thr, B);
@@ -532,7 +533,8 @@ template <> double* lv<double>(DBuf<double>& d, DBuf<float>&) { return d.get(); 
 template <> float* lv<float>(DBuf<double>&, DBuf<float>& f) { return f.get(); }
 
 template <class T>
-void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s) {
+void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s,
+                 const char* fam = nullptr) {
     const int deg = std::max(1, pc.opts.cheb_degree_amg);
     const double hi = 1.1 * L.lmax, lo = L.lmax / pc.opts.cheb_ratio;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -546,12 +548,12 @@ void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, c
             if (zero_init) {
                 k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, b, d, x, T(0), T(1.0 / theta), 1);
             } else {
-                spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s);
+                spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
                 k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, r, d, x, T(0), T(1.0 / theta), 0);
             }
         } else {
             const double rho_new = 1.0 / (2.0 * sigma - rho);
-            spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s);
+            spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
             k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, r, d, x, T(rho_new * rho),
                                                       T(2.0 * rho_new / delta), 0);
             rho = rho_new;
@@ -573,12 +575,13 @@ void vcycle_level(PcImpl& pc, size_t l, const T* b, T* x, cudaStream_t s) {
     T* r = lv<T>(L.r, L.r32);
     T* cb = lv<T>(C.b, C.b32);
     T* cx = lv<T>(C.x, C.x32);
-    cheb_smooth<T>(pc, L, b, x, true, s);
-    spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s);
+    const char* fam = (l == 0) ? (sizeof(T) == 8 ? "amg_spmv_L0" : "amg_spmv_L0_fp32") : nullptr;
+    cheb_smooth<T>(pc, L, b, x, true, s, fam);
+    spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
     spmv_lanes<0, T>(L.lanes_R, L.R, r, nullptr, cb, s);
     vcycle_level<T>(pc, l + 1, cb, cx, s);
     spmv_lanes<2, T>(L.lanes_P, L.P, cx, nullptr, x, s);
-    cheb_smooth<T>(pc, L, b, x, false, s);
+    cheb_smooth<T>(pc, L, b, x, false, s, fam);
 }
 
 void to_f32(const DBuf<double>& in, DBuf<float>& out, cudaStream_t s) {
