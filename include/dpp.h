@@ -30,6 +30,12 @@
  *   - Work is ordered on `stream` (NULL = the legacy default stream). Calls that
  *     must report a host-visible result (dpp_solve*, dpp_setup_pc and
  *     dpp_assemble's size discovery) synchronise that stream before they return.
+ *   - The library's own device memory (handles, work vectors, setup
+ *     temporaries) comes from a library-owned, stream-ordered CUDA memory
+ *     pool per device: allocations and frees are ordered on the call's stream
+ *     and never synchronise the device, and freed memory stays cached for
+ *     reuse until dpp_release_cached_memory. A handle must not be used from
+ *     two streams at once; dpp_destroy_* first waits for the whole device.
  *   - No call aborts, exits or traps. Errors come back as dpp_status, and
  *     dpp_last_error() gives a thread-local message. Input arrays are checked
  *     on the device for index range and finiteness before any kernel uses
@@ -283,6 +289,11 @@ dpp_status dpp_adjoint_gradients_noalloc(dpp_problem prob, const double* x, cons
                                          dpp_stream_t stream);
 
 /* ---------------- instrumentation (no counterpart in the paper) ---------------- */
+
+/* Wait for the current device, then return the memory cached in the
+ * library's pool for that device (see the conventions above) to the driver.
+ * Live handles keep their memory. Errors: CUDA. */
+dpp_status dpp_release_cached_memory(void);
 
 /* Number of kernels this library has launched since it was loaded (every
  * launch site is counted once). */

@@ -102,6 +102,7 @@ _SIGS = {
     "dpp_pc_level_sizes": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64)]),
     "dpp_pc_export_level": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
     "dpp_adjoint_gradients_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "dpp_release_cached_memory": (C.c_int, []),
     "dpp_launch_count": (C.c_int64, []),
     "dpp_profile_enable": (C.c_int, [C.c_int32]),
     "dpp_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -287,6 +288,10 @@ def dpp_adjoint_gradients_noalloc(prob: int, x, lam, g1, g2, gb, stream: int = 0
     """Adjoint sensitivities with no device allocation (fixed library scratch)."""
     _check(load().dpp_adjoint_gradients_noalloc(prob, _ptr(x), _ptr(lam), _ptr(g1), _ptr(g2),
                                                 _ptr(gb), stream or None))
+
+
+def dpp_release_cached_memory() -> None:
+    _check(load().dpp_release_cached_memory())
 
 
 def dpp_launch_count() -> int:

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstring>
 #include <map>
+#include <cstdlib>
 #include <mutex>
 #include <new>
 
@@ -41,6 +42,58 @@ std::map<std::string, Family> g_prof;
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) fail(DPP_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        DPP_CK(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = UINT64_MAX;  // keep freed memory for reuse until dpp_release_cached_memory
+        DPP_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+}  // namespace
+
+cudaStream_t& current_stream() {
+    thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
+void* pool_alloc(size_t bytes) {
+    cudaStream_t s = current_stream();
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DPP_CK(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        fail(DPP_ERR_CUDA, "internal: device allocation while the stream is being captured");
+    int dev = 0;
+    DPP_CK(cudaGetDevice(&dev));
+    void* p = nullptr;
+    DPP_CK(cudaMallocFromPoolAsync(&p, bytes, device_pool(dev), s));
+    // DPP_POISON_ALLOC=1 fills every new buffer with 0xFF bytes (NaN for
+    // floating point, -1 for integers), so that a read of memory the library
+    // never wrote shows up in its results.
+    static const bool poison = [] {
+        const char* e = std::getenv("DPP_POISON_ALLOC");
+        return e && e[0] == '1';
+    }();
+    if (poison) DPP_CK(cudaMemsetAsync(p, 0xFF, bytes, s));
+    return p;
+}
+
+void pool_free(void* p) { cudaFreeAsync(p, current_stream()); }
+
 void set_last_error_message(const char* m);
 bool profiling_enabled() { return g_profiling.load(std::memory_order_relaxed); }
 void profile_record(const char* family, cudaEvent_t a, cudaEvent_t b, double bytes) {
@@ -169,6 +222,7 @@ const char* dpp_last_error(void) { return g_last_error.c_str(); }
 dpp_status dpp_assemble(const dpp_problem_desc* d, int32_t precision, dpp_stream_t stream,
                         dpp_problem* out) {
     return guarded("dpp_assemble", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(d != nullptr && out != nullptr, "null descriptor or output handle");
         *out = nullptr;
         require(d->dim == 2 || d->dim == 3, "dim must be 2 or 3");
@@ -203,6 +257,7 @@ dpp_status dpp_assemble(const dpp_problem_desc* d, int32_t precision, dpp_stream
 dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t stream,
                         dpp_pc* out) {
     return guarded("dpp_setup_pc", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob != nullptr && out != nullptr, "null problem or output handle");
         *out = nullptr;
         dpp_pc_opts o;
@@ -240,6 +295,7 @@ static dpp_status solve_common(const char* name, dpp_problem prob, dpp_pc pc,
     dpp_solve_info& inf = info ? *info : local;
     std::memset(&inf, 0, sizeof(inf));
     dpp_status st = guarded(name, [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob && pc && x, "null problem, pc or x");
         require(pc->owner == prob, "pc was built for a different problem");
         dpp_solve_opts o;
@@ -305,6 +361,7 @@ dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* 
     dpp_status st;
     {
         dpp_status pre = guarded("dpp_adjoint_solve", [&]() -> dpp_status {
+            StreamScope scope_((cudaStream_t)stream);
             require(prob && x && dJdx && lambda && dJ_dlogk1 && dJ_dlogk2 && dJ_dbeta,
                     "null argument");
             if (opts) require(opts->x_memory == DPP_MEM_DEVICE, "adjoint arrays must be device memory");
@@ -323,6 +380,7 @@ dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* 
     st = solve_common("dpp_adjoint_solve", prob, pc, &o, dJdx, lambda, true, info, stream);
     if (st != DPP_OK) return st;
     return guarded("dpp_adjoint_solve", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         cudaStream_t s = (cudaStream_t)stream;
         adjoint_gradients(prob->impl, x, lambda, dJ_dlogk1, dJ_dlogk2, dJ_dbeta, s);
         DPP_CK(cudaStreamSynchronize(s));
@@ -335,6 +393,7 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
                              double* const* xs, dpp_solve_info* infos, dpp_stream_t stream) {
     std::vector<int> codes;
     dpp_status st = guarded("dpp_solve_batched", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(n_inst >= 1 && descs && xs && infos, "null argument or n_inst < 1");
         for (int i = 0; i < n_inst; ++i) std::memset(&infos[i], 0, sizeof(dpp_solve_info));
         dpp_pc_opts po;
@@ -357,6 +416,7 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
             cudaStream_t s;
             ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
         } guard{s};
+        StreamScope on_private(s);  // declared after guard: restored before s is destroyed
         dpp_problem_s prob;
         dpp_pc_s pc;
         EventTimer ta(s);
@@ -426,8 +486,28 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
     return st;
 }
 
-void dpp_destroy_problem(dpp_problem p) { delete p; }
-void dpp_destroy_pc(dpp_pc p) { delete p; }
+// The library's buffers go back to its stream-ordered pool, so first wait for
+// every stream that may still use them.
+void dpp_destroy_problem(dpp_problem p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    delete p;
+}
+void dpp_destroy_pc(dpp_pc p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    delete p;
+}
+
+dpp_status dpp_release_cached_memory(void) {
+    return guarded("dpp_release_cached_memory", [&]() -> dpp_status {
+        int dev = 0;
+        DPP_CK(cudaGetDevice(&dev));
+        DPP_CK(cudaDeviceSynchronize());
+        DPP_CK(cudaMemPoolTrimTo(device_pool(dev), 0));
+        return DPP_OK;
+    });
+}
 
 dpp_status dpp_problem_sizes(dpp_problem prob, int64_t out[6]) {
     return guarded("dpp_problem_sizes", [&]() -> dpp_status {
@@ -446,6 +526,7 @@ dpp_status dpp_problem_sizes(dpp_problem prob, int64_t out[6]) {
 dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, double* y,
                        dpp_stream_t stream) {
     return guarded("dpp_apply_K", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob && x && y && x != y, "null or aliased argument");
         require_aligned(x, "x");
         require_aligned(y, "y");
@@ -457,6 +538,7 @@ dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, dou
 dpp_status dpp_apply_K32(dpp_problem prob, int32_t transpose, const float* x, double* y,
                          dpp_stream_t stream) {
     return guarded("dpp_apply_K32", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob && x && y, "null argument");
         require_aligned(x, "x");
         require_aligned(y, "y");
@@ -467,6 +549,7 @@ dpp_status dpp_apply_K32(dpp_problem prob, int32_t transpose, const float* x, do
 
 dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream) {
     return guarded("dpp_get_rhs", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob && f, "null argument");
         const ProblemImpl& P = prob->impl;
         DPP_CK(cudaMemcpyAsync(f, P.f.get(), P.n_nodes * P.ns * sizeof(double),
@@ -486,6 +569,7 @@ extern "C" {
 dpp_status dpp_export_pairs(dpp_problem prob, int32_t* row_ptr, int32_t* col, double* vals,
                             dpp_stream_t stream) {
     return guarded("dpp_export_pairs", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob && row_ptr && col && vals, "null argument");
         export_pairs(prob->impl, row_ptr, col, vals, (cudaStream_t)stream);
         return DPP_OK;
@@ -495,6 +579,7 @@ dpp_status dpp_export_pairs(dpp_problem prob, int32_t* row_ptr, int32_t* col, do
 dpp_status dpp_pc_apply(dpp_problem prob, dpp_pc pc, int32_t transpose, const double* r, double* z,
                         dpp_stream_t stream) {
     return guarded("dpp_pc_apply", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(prob && pc && r && z && r != z, "null or aliased argument");
         require(pc->owner == prob, "pc was built for a different problem");
         require_aligned(r, "r");
@@ -522,6 +607,7 @@ dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32
                                double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
                                dpp_stream_t stream) {
     return guarded("dpp_pc_export_level", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
         require(pc && row_ptr && col && val, "null argument");
         const auto& L = pc->impl.levels;
         require(level >= 0 && level < (int)L.size(), "level out of range");

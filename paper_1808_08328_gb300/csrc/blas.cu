@@ -8,11 +8,13 @@
 
 namespace dpp {
 
-void Reducer::ensure(int rows) {
+void Reducer::ensure(int rows, cudaStream_t s) {
     if ((int64_t)partial.n < (int64_t)rows * kRedBlocks) partial.alloc((size_t)rows * kRedBlocks);
     if (!counter.get()) {
         counter.alloc(64);
-        DPP_CK(cudaMemset(counter.get(), 0, 64 * sizeof(unsigned)));
+        // reset on s, the stream that uses it (the legacy stream would not
+        // wait for work on a non-blocking one)
+        DPP_CK(cudaMemsetAsync(counter.get(), 0, 64 * sizeof(unsigned), s));
     }
 }
 
@@ -124,7 +126,7 @@ __global__ void k_axpby(double a, const double* __restrict__ x, double b, double
                         int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        y[i] = a * x[i] + b * y[i];
+        y[i] = (b == 0.0) ? a * x[i] : a * x[i] + b * y[i];  // b = 0: y is not read (may be unset)
 }
 
 __global__ void k_fill(double* __restrict__ x, double v, int64_t n) {
@@ -146,7 +148,7 @@ inline int stream_grid(int64_t n) {
 }  // namespace
 
 void dot(Reducer& R, const double* x, const double* y, int64_t n, double* out, cudaStream_t s) {
-    R.ensure(1);
+    R.ensure(1, s);
     k_dot<<<kRedBlocks, kRedThreads, 0, s>>>(x, y, n, R.partial.get(), R.counter.get(), out);
     DPP_LAUNCH_CK();
 }
@@ -154,7 +156,7 @@ void dot(Reducer& R, const double* x, const double* y, int64_t n, double* out, c
 void multidot(Reducer& R, const double* V, int64_t ld, int k, const double* w, int64_t n,
               double* out, cudaStream_t s) {
     if (k <= 0) return;
-    R.ensure(k);
+    R.ensure(k, s);
     dim3 grid(kRedBlocks, k);
     k_multidot<<<grid, kRedThreads, 0, s>>>(V, ld, w, n, R.partial.get());
     DPP_LAUNCH_CK();

@@ -69,8 +69,28 @@ struct ProfScope {
     }
 };
 
-// Owning device buffer. Freed with cudaFree (a device-wide sync point), which
-// only happens in dpp_destroy_* and on error paths.
+// Device memory comes from a library-owned, stream-ordered CUDA memory pool
+// (one per device, created on first use, which keeps freed memory for reuse):
+// an allocation or a free is an operation on the stream of the API call in
+// progress (stream_scope below), with no device-wide synchronisation. Outside
+// any API call the legacy default stream is used. Allocating on a stream that
+// is being captured into a CUDA graph is an error: graph captures must find
+// their buffers already allocated.
+void* pool_alloc(size_t bytes);
+void pool_free(void* p);
+cudaStream_t& current_stream();  // thread-local
+
+// Makes `s` the stream of pool allocations and frees for the scope's lifetime.
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s) : prev(current_stream()) { current_stream() = s; }
+    ~StreamScope() { current_stream() = prev; }
+    StreamScope(const StreamScope&) = delete;
+    StreamScope& operator=(const StreamScope&) = delete;
+};
+
+// Owning device buffer, allocated from and returned to the pool in stream
+// order (see pool_alloc).
 template <class T>
 struct DBuf {
     T* p = nullptr;
@@ -88,10 +108,10 @@ struct DBuf {
     void alloc(size_t count) {
         release();
         n = count;
-        if (count) DPP_CK(cudaMalloc(&p, count * sizeof(T)));
+        if (count) p = static_cast<T*>(pool_alloc(count * sizeof(T)));
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) pool_free(p);
         p = nullptr;
         n = 0;
     }

@@ -39,7 +39,7 @@ void scatter_p(const ProblemImpl& P, const T* yp, T* z, cudaStream_t s);
 struct Reducer {
     DBuf<double> partial;   // [rows][kRedBlocks]
     DBuf<unsigned> counter;
-    void ensure(int rows);
+    void ensure(int rows, cudaStream_t s);  // allocation and counter reset ordered on s
 };
 constexpr int kRedBlocks = 2 * kSMs;
 // out[0] = x . y (deterministic two-level reduction)

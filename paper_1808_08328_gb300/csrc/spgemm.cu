@@ -7,24 +7,27 @@
 //   * the CSR transpose.
 //
 // Product scheme (deterministic; no floating-point atomics). One warp owns one
-// output row, and its lanes form G groups of 32/G lanes. Group g takes the
-// entries p = g, g+G, ... of A's row i; its lanes take the entries of B's row
-// acol[p]. The group count follows B's mean row length, so short rows of B
-// (aggregation prolongators) still keep every lane busy.
+// output row i of C = A B. The warp takes A's row in chunks of 32 entries, one
+// per lane; a warp prefix sum of the lengths of the B rows they select numbers
+// the chunk's products t = 0, 1, ... in (p, q) order, and the warp then takes
+// 32 consecutive products per round, one per lane, so every lane has a product
+// and its own independent loads whatever the lengths of B's rows. A lane finds
+// the A entry that owns its product by a binary search over the chunk's prefix
+// sums held in the lanes' registers (shuffles).
 //   1. symbolic: the candidate columns go into an open-addressing hash set in
 //      shared memory, and the distinct keys are counted. Tables grow in tiers
 //      (256, 2048, 8192 slots); a row that overflows one tier is retried in
 //      the next;
-//   2. numeric: the warp rebuilds the set, compacts it, and ranks the keys
-//      (they are distinct, so a key's rank is the number of smaller keys) to
-//      get the row's sorted columns. Each group then scatters a_ip * B_p into
-//      its own accumulator, at positions found by binary search in the sorted
-//      columns. Within one round the positions of a group are distinct
-//      (B's row has distinct columns); between rounds the warp synchronises.
-//      At the end the group accumulators are added in group order. The
-//      summation order is therefore fixed, and the result is deterministic. Rows
-//      wider than the largest shared accumulator (1024 columns) use one
-//      warp with the accumulator in C's own storage.
+//   2. numeric: the warp rebuilds the set, compacts it and ranks the keys
+//      (they are distinct, so a key's rank is the number of smaller keys):
+//      the ranks give the row's sorted columns and, stored beside each key in
+//      the table, the accumulator slot of each column. Each round then adds
+//      a_ip * b_pq into the slot of column q. Lanes of one round that hit the
+//      same slot add one after another in lane order (found with a warp
+//      match), and rounds follow each other, so every entry of C is summed in
+//      the sequential (p, q) order and the result is deterministic. Rows
+//      wider than the largest shared accumulator (1024 columns) use one warp
+//      with the accumulator in C's own storage.
 #include <climits>
 
 #include "amg.cuh"
@@ -32,55 +35,145 @@
 namespace dpp {
 
 namespace {
-__device__ __forceinline__ unsigned hash_key(int k) { return (unsigned)k * 2654435761u; }
+constexpr unsigned kFull = 0xffffffffu;
 
+// multiplicative (Fibonacci) hashing: the top log2(HT) bits of k * 2^32/phi
+template <int HT>
+__device__ __forceinline__ unsigned hash_slot(int k) {
+    constexpr int bits = __builtin_ctz(HT);
+    return ((unsigned)k * 2654435761u) >> (32 - bits);
+}
+
+// Most inserts find their key already present, so a plain read comes first and
+// only an empty slot takes the atomic.
 template <int HT>
 __device__ __forceinline__ bool hs_insert(int* keys, int key) {
-    unsigned h = hash_key(key) & (HT - 1);
+    unsigned h = hash_slot<HT>(key);
     for (int probe = 0; probe < HT; ++probe) {
-        int prev = atomicCAS(&keys[h], -1, key);
-        if (prev == -1 || prev == key) return true;
+        const int cur = reinterpret_cast<volatile int*>(keys)[h];
+        if (cur == key) return true;
+        if (cur == -1) {
+            const int prev = atomicCAS(&keys[h], -1, key);
+            if (prev == -1 || prev == key) return true;
+        }
         h = (h + 1) & (HT - 1);
     }
     return false;
 }
 
+// table position of a key known to be in the set (-1 if absent)
+template <int HT>
+__device__ __forceinline__ int hs_find(const int* keys, int key) {
+    unsigned h = hash_slot<HT>(key);
+    for (int probe = 0; probe < HT; ++probe) {
+        const int k = keys[h];
+        if (k == key) return (int)h;
+        if (k < 0) return -1;
+        h = (h + 1) & (HT - 1);
+    }
+    return -1;
+}
+
+// Calls f(active, q, a_ip) for every product of row i of A B, 32 per round,
+// in (p, q) order; every lane of the warp makes every call (f may use warp
+// collectives), inactive lanes with active == false.
+template <bool VALS, class F>
+__device__ __forceinline__ void for_each_product(int i, const int* __restrict__ arp,
+                                                 const int* __restrict__ acol,
+                                                 const double* __restrict__ aval,
+                                                 const int* __restrict__ brp, int lane, F&& f) {
+    const int a0 = arp[i], a1 = arp[i + 1];
+    for (int pc = a0; pc < a1; pc += 32) {
+        const int p = pc + lane;
+        int bs = 0, len = 0;
+        double a = 0.0;
+        if (p < a1) {
+            const int k = acol[p];
+            bs = brp[k];
+            len = brp[k + 1] - bs;
+            if (VALS) a = aval[p];
+        }
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(kFull, inc, 31);
+        const int excl = inc - len;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int j = 0;  // owner: the last lane whose products start at or before t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(kFull, excl, j + step);
+                if (e <= t) j += step;
+            }
+            const int q = __shfl_sync(kFull, bs, j) + (t - __shfl_sync(kFull, excl, j));
+            const double aj = VALS ? __shfl_sync(kFull, a, j) : 0.0;
+            f(t < total, q, aj);
+        }
+    }
+}
+
 // Fill the warp's hash set with the candidate columns of row i of A*B.
-template <int HT, int G>
+template <int HT>
 __device__ bool warp_collect(int i, const int* __restrict__ arp, const int* __restrict__ acol,
                              const int* __restrict__ brp, const int* __restrict__ bcol, int* keys,
                              int lane) {
-    constexpr int GL = 32 / G;
     for (int t = lane; t < HT; t += 32) keys[t] = -1;
     __syncwarp();
-    const int g = lane / GL, gl = lane % GL;
     bool ok = true;
-    for (int p = arp[i] + g; p < arp[i + 1]; p += G) {
-        const int k = acol[p];
-        for (int q = brp[k] + gl; q < brp[k + 1]; q += GL) ok &= hs_insert<HT>(keys, bcol[q]);
-    }
+    for_each_product<false>(i, arp, acol, nullptr, brp, lane, [&](bool act, int q, double) {
+        if (act) ok &= hs_insert<HT>(keys, bcol[q]);
+    });
     __syncwarp();
-    return __all_sync(0xffffffffu, ok);
+    return __all_sync(kFull, ok);
 }
 
-// Compact the set into list[0..u) and write the keys in ascending order to out.
+// Compact the set into list[0..u) (any order); returns u.
 template <int HT>
-__device__ int warp_sorted_keys(const int* keys, int* list, int lane, int* out) {
+__device__ int warp_compact(const int* keys, int* list, int lane) {
     int base = 0;
     for (int t0 = 0; t0 < HT; t0 += 32) {
-        int k = keys[t0 + lane];
-        unsigned m = __ballot_sync(0xffffffffu, k >= 0);
+        const int k = keys[t0 + lane];
+        const unsigned m = __ballot_sync(kFull, k >= 0);
         if (k >= 0) list[base + __popc(m & ((1u << lane) - 1u))] = k;
         base += __popc(m);
     }
     __syncwarp();
-    for (int e = lane; e < base; e += 32) {
-        int k = list[e], r = 0;
-        for (int f = 0; f < base; ++f) r += (list[f] < k);
-        out[r] = k;
+    return base;
+}
+
+// Rank the distinct keys list[0..u): out[rank] = key and, if slot != nullptr,
+// slot[table position of key] = rank. Each lane holds up to 8 keys in
+// registers and reads the list once per batch.
+template <int HT>
+__device__ void warp_rank(const int* list, int u, int lane, int* __restrict__ out,
+                          const int* keys, int* slot) {
+    constexpr int KR = 8;
+    for (int e0 = 0; e0 < u; e0 += 32 * KR) {
+        int k[KR], r[KR];
+#pragma unroll
+        for (int j = 0; j < KR; ++j) {
+            const int e = e0 + j * 32 + lane;
+            k[j] = (e < u) ? list[e] : INT_MAX;
+            r[j] = 0;
+        }
+        for (int f = 0; f < u; ++f) {
+            const int v = list[f];
+#pragma unroll
+            for (int j = 0; j < KR; ++j) r[j] += (v < k[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < KR; ++j) {
+            if (e0 + j * 32 + lane < u) {
+                out[r[j]] = k[j];
+                if (slot) slot[hs_find<HT>(keys, k[j])] = r[j];
+            }
+        }
     }
     __syncwarp();
-    return base;
 }
 
 __device__ __forceinline__ int bsearch_row(const int* __restrict__ col, int lo, int hi, int key) {
@@ -97,7 +190,7 @@ __device__ __forceinline__ int bsearch_row(const int* __restrict__ col, int lo, 
 // Symbolic pass: count[i] = distinct columns of row i (rows[] lists the rows to
 // do, with rows[-1] their number; rows == nullptr means every row). Rows that
 // overflow the table are appended to ovf (ovf[0] = count).
-template <int HT, int G>
+template <int HT>
 __global__ void k_spgemm_count(int64_t n_rows, const int* __restrict__ arp,
                                const int* __restrict__ acol, const int* __restrict__ brp,
                                const int* __restrict__ bcol, int* __restrict__ count,
@@ -111,11 +204,10 @@ __global__ void k_spgemm_count(int64_t n_rows, const int* __restrict__ arp,
     const int i = rows ? rows[w] : (int)w;
     if (is_long && is_long[i]) return;  // done by the block-per-row kernels
     int* keys = smem + warp * HT;
-    const bool ok = warp_collect<HT, G>(i, arp, acol, brp, bcol, keys, lane);
+    const bool ok = warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane);
     int c = 0;
     for (int t = lane; t < HT; t += 32) c += (keys[t] >= 0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    c = __reduce_add_sync(kFull, c);
     if (lane == 0) {
         count[i] = ok ? c : 0;
         if (!ok) ovf[atomicAdd(&ovf[0], 1) + 1] = i;
@@ -123,7 +215,7 @@ __global__ void k_spgemm_count(int64_t n_rows, const int* __restrict__ arp,
 }
 
 // Symbolic fill for pattern-only products: sorted columns of each row.
-template <int HT, int G>
+template <int HT>
 __global__ void k_spgemm_pattern(int64_t n_rows, const int* __restrict__ arp,
                                  const int* __restrict__ acol, const int* __restrict__ brp,
                                  const int* __restrict__ bcol, const int* __restrict__ crp,
@@ -135,21 +227,25 @@ __global__ void k_spgemm_pattern(int64_t n_rows, const int* __restrict__ arp,
     if (w >= n_work) return;
     const int i = rows ? rows[w] : (int)w;
     int* keys = smem + warp * 2 * HT;
-    if (!warp_collect<HT, G>(i, arp, acol, brp, bcol, keys, lane)) return;
-    warp_sorted_keys<HT>(keys, keys + HT, lane, ccol + crp[i]);
+    if (!warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane)) return;
+    int* list = keys + HT;
+    const int u = warp_compact<HT>(keys, list, lane);
+    warp_rank<HT>(list, u, lane, ccol + crp[i], keys, nullptr);
 }
 
 // Numeric pass for rows with at most CAP distinct columns (shared accumulators).
-template <int HT, int G, int CAP>
+// Shared memory per warp: keys[HT], slot[HT], acc[CAP] (the compacted key list
+// lives in acc until the ranks are known).
+template <int HT, int CAP>
 __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
                                  const int* __restrict__ acol, const double* __restrict__ aval,
                                  const int* __restrict__ brp, const int* __restrict__ bcol,
                                  const double* __restrict__ bval, const int* __restrict__ crp,
                                  int* __restrict__ ccol, double* __restrict__ cval,
                                  int* __restrict__ wide, const int* __restrict__ is_long) {
+    static_assert(HT >= 2 * CAP, "table at most half full");
     extern __shared__ int smem[];
     constexpr int WPB = 4;
-    constexpr int GL = 32 / G;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * WPB + warp;
     if (w >= n_rows) return;
@@ -161,46 +257,31 @@ __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
         return;
     }
     int* keys = smem + warp * 2 * HT;
-    int* sorted = keys + HT;  // HT >= 2 CAP slots: the compacted list, then the sorted keys
-    double* acc = reinterpret_cast<double*>(smem + WPB * 2 * HT) + (size_t)warp * G * CAP;
-    warp_collect<HT, G>(i, arp, acol, brp, bcol, keys, lane);  // cannot overflow (HT >= 2 CAP)
-    // compact into sorted[CAP..2CAP), rank-sort into sorted[0..u)
-    int* list = sorted + CAP;
-    int u = 0;
-    for (int t0 = 0; t0 < HT; t0 += 32) {
-        int k = keys[t0 + lane];
-        unsigned m = __ballot_sync(0xffffffffu, k >= 0);
-        if (k >= 0) list[u + __popc(m & ((1u << lane) - 1u))] = k;
-        u += __popc(m);
-    }
+    int* slot = keys + HT;
+    double* acc = reinterpret_cast<double*>(smem + WPB * 2 * HT) + (size_t)warp * CAP;
+    warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane);  // cannot overflow (HT >= 2 CAP)
+    int* list = reinterpret_cast<int*>(acc);
+    const int u = warp_compact<HT>(keys, list, lane);
+    warp_rank<HT>(list, u, lane, ccol + c0, keys, slot);
+    for (int e = lane; e < u; e += 32) acc[e] = 0.0;
     __syncwarp();
-    for (int e = lane; e < u; e += 32) {
-        int k = list[e], r = 0;
-        for (int f = 0; f < u; ++f) r += (list[f] < k);
-        sorted[r] = k;
-    }
-    for (int e = lane; e < G * CAP; e += 32) acc[e] = 0.0;
-    __syncwarp();
-    for (int e = lane; e < u; e += 32) ccol[c0 + e] = sorted[e];
-    const int g = lane / GL, gl = lane % GL;
-    double* my = acc + g * CAP;
-    const int a0 = arp[i], a1 = arp[i + 1];
-    for (int pb = a0; pb < a1; pb += G) {
-        const int p = pb + g;
-        if (p < a1) {
-            const int k = acol[p];
-            const double a = aval[p];
-            for (int q = brp[k] + gl; q < brp[k + 1]; q += GL)
-                my[bsearch_row(sorted, 0, u, bcol[q])] += a * bval[q];
+    for_each_product<true>(i, arp, acol, aval, brp, lane, [&](bool act, int q, double a) {
+        int s = -1 - lane;  // distinct for idle lanes
+        double v = 0.0;
+        if (act) {
+            const int key = bcol[q];
+            v = a * bval[q];
+            s = slot[hs_find<HT>(keys, key)];
         }
-        __syncwarp();
-    }
-    for (int e = lane; e < u; e += 32) {
-        double v = acc[e];
-#pragma unroll
-        for (int h = 1; h < G; ++h) v += acc[h * CAP + e];
-        cval[c0 + e] = v;
-    }
+        const unsigned peers = __match_any_sync(kFull, s);
+        const int order = __popc(peers & ((1u << lane) - 1u));
+        const int n_sub = (int)__reduce_max_sync(kFull, (unsigned)__popc(peers));
+        for (int r = 0; r < n_sub; ++r) {
+            if (act && order == r) acc[s] += v;
+            __syncwarp();
+        }
+    });
+    for (int e = lane; e < u; e += 32) cval[c0 + e] = acc[e];
 }
 
 // Numeric pass for wide rows: one warp per listed row, accumulating in C.
@@ -217,12 +298,13 @@ __global__ void k_spgemm_wide(const int* __restrict__ arp, const int* __restrict
     if (w >= rows[-1]) return;
     const int i = rows[w];
     int* keys = smem + warp * 2 * HT;
-    if (!warp_collect<HT, 1>(i, arp, acol, brp, bcol, keys, lane)) {
+    if (!warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane)) {
         if (lane == 0) atomicOr(status, 1);
         return;
     }
     const int c0 = crp[i];
-    const int u = warp_sorted_keys<HT>(keys, keys + HT, lane, ccol + c0);
+    const int u = warp_compact<HT>(keys, keys + HT, lane);
+    warp_rank<HT>(keys + HT, u, lane, ccol + c0, keys, nullptr);
     for (int e = lane; e < u; e += 32) cval[c0 + e] = 0.0;
     __syncwarp();
     for (int p = arp[i]; p < arp[i + 1]; ++p) {
@@ -443,74 +525,36 @@ void set_smem(K kernel, size_t smem) {
         DPP_CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
 }
 
-int groups_for(double avg_b) {  // lane groups per warp ~ 32 / (mean row length of B)
-    if (avg_b <= 1.5) return 32;
-    if (avg_b <= 3.0) return 16;
-    if (avg_b <= 6.0) return 8;
-    if (avg_b <= 12.0) return 4;
-    if (avg_b <= 24.0) return 2;
-    return 1;
-}
-
-template <int HT, int G>
+template <int HT>
 void count_tier(const CsrView& A, const CsrView& B, int* count, int* ovf, const int* rows,
                 int64_t n_work, int wpb, const int* is_long, cudaStream_t s) {
     const size_t smem = (size_t)wpb * HT * sizeof(int);
-    set_smem(k_spgemm_count<HT, G>, smem);
-    k_spgemm_count<HT, G><<<grid_for(n_work, wpb), wpb * 32, smem, s>>>(
+    set_smem(k_spgemm_count<HT>, smem);
+    k_spgemm_count<HT><<<grid_for(n_work, wpb), wpb * 32, smem, s>>>(
         A.n_rows, A.rp, A.col, B.rp, B.col, count, ovf, rows, is_long);
     DPP_LAUNCH_CK();
 }
 
 template <int HT>
-void count_g(int G, const CsrView& A, const CsrView& B, int* count, int* ovf, const int* rows,
-             int64_t n_work, int wpb, const int* is_long, cudaStream_t s) {
-    switch (G) {
-        case 32: count_tier<HT, 32>(A, B, count, ovf, rows, n_work, wpb, is_long, s); break;
-        case 16: count_tier<HT, 16>(A, B, count, ovf, rows, n_work, wpb, is_long, s); break;
-        case 8: count_tier<HT, 8>(A, B, count, ovf, rows, n_work, wpb, is_long, s); break;
-        case 4: count_tier<HT, 4>(A, B, count, ovf, rows, n_work, wpb, is_long, s); break;
-        case 2: count_tier<HT, 2>(A, B, count, ovf, rows, n_work, wpb, is_long, s); break;
-        default: count_tier<HT, 1>(A, B, count, ovf, rows, n_work, wpb, is_long, s); break;
-    }
-}
-
-template <int HT, int G>
 void pattern_tier(const CsrView& A, const CsrView& B, Csr& C, const int* rows, int64_t n_work,
                   int wpb, cudaStream_t s) {
     const size_t smem = (size_t)wpb * 2 * HT * sizeof(int);
-    set_smem(k_spgemm_pattern<HT, G>, smem);
-    k_spgemm_pattern<HT, G><<<grid_for(n_work, wpb), wpb * 32, smem, s>>>(
+    set_smem(k_spgemm_pattern<HT>, smem);
+    k_spgemm_pattern<HT><<<grid_for(n_work, wpb), wpb * 32, smem, s>>>(
         A.n_rows, A.rp, A.col, B.rp, B.col, C.row_ptr.get(), C.col.get(), rows);
     DPP_LAUNCH_CK();
 }
 
-template <int HT, int G, int CAP>
+template <int CAP>
 void scatter_tier(const CsrView& A, const CsrView& B, Csr& C, int* wide, const int* is_long,
                   cudaStream_t s) {
-    const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * G * CAP * sizeof(double);
-    set_smem(k_spgemm_scatter<HT, G, CAP>, smem);
-    k_spgemm_scatter<HT, G, CAP><<<grid_for(A.n_rows, kWarps), kWarps * 32, smem, s>>>(
+    constexpr int HT = 2 * CAP < 64 ? 64 : 2 * CAP;
+    const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * CAP * sizeof(double);
+    set_smem(k_spgemm_scatter<HT, CAP>, smem);
+    k_spgemm_scatter<HT, CAP><<<grid_for(A.n_rows, kWarps), kWarps * 32, smem, s>>>(
         A.n_rows, A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(),
         C.val.get(), wide, is_long);
     DPP_LAUNCH_CK();
-}
-
-// G is capped so that the accumulators stay at or below 8 KB per warp.
-template <int CAP>
-void scatter_g(int G, const CsrView& A, const CsrView& B, Csr& C, int* wide, const int* is_long,
-               cudaStream_t s) {
-    constexpr int HT = 2 * CAP < 64 ? 64 : 2 * CAP;
-    constexpr int GMAX = 1024 / CAP < 1 ? 1 : 1024 / CAP;
-    G = std::min(G, GMAX);
-    switch (G) {
-        case 32: scatter_tier<HT, (GMAX >= 32 ? 32 : 1), CAP>(A, B, C, wide, is_long, s); break;
-        case 16: scatter_tier<HT, (GMAX >= 16 ? 16 : 1), CAP>(A, B, C, wide, is_long, s); break;
-        case 8: scatter_tier<HT, (GMAX >= 8 ? 8 : 1), CAP>(A, B, C, wide, is_long, s); break;
-        case 4: scatter_tier<HT, (GMAX >= 4 ? 4 : 1), CAP>(A, B, C, wide, is_long, s); break;
-        case 2: scatter_tier<HT, (GMAX >= 2 ? 2 : 1), CAP>(A, B, C, wide, is_long, s); break;
-        default: scatter_tier<HT, 1, CAP>(A, B, C, wide, is_long, s); break;
-    }
 }
 
 constexpr int kHtTiers[3] = {256, 2048, 8192};
@@ -526,7 +570,6 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     C.n_cols = B.n_cols;
     C.row_ptr.alloc(n + 1);
     DPP_CK(cudaMemsetAsync(C.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
-    const int G = groups_for(B.n_rows ? (double)B.nnz / (double)B.n_rows : 1.0);
     // symbolic: tiers of hash tables; rows[t] lists the rows retried in tier t
     DBuf<int> lists(2 * (n + 2));
     int* tier_rows[3] = {nullptr, lists.get() + 1, lists.get() + (n + 2) + 1};
@@ -551,15 +594,15 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     }
     {
         ProfScope pc("spgemm_count", s, 0);
-        count_g<256>(G, A, B, C.row_ptr.get(), tier_rows[1] - 1, nullptr, n, kWarps, long_flag, s);
+        count_tier<256>(A, B, C.row_ptr.get(), tier_rows[1] - 1, nullptr, n, kWarps, long_flag, s);
         tier_n[1] = read_scalar(tier_rows[1] - 1, s, hs);
         if (tier_n[1] > 0) {
-            count_g<2048>(G, A, B, C.row_ptr.get(), tier_rows[2] - 1, tier_rows[1], tier_n[1], kWarps,
+            count_tier<2048>(A, B, C.row_ptr.get(), tier_rows[2] - 1, tier_rows[1], tier_n[1], kWarps,
                           long_flag, s);
             tier_n[2] = read_scalar(tier_rows[2] - 1, s, hs);
         }
         if (tier_n[2] > 0) {
-            count_g<8192>(G, A, B, C.row_ptr.get(), last_ovf.get(), tier_rows[2], tier_n[2], 1,
+            count_tier<8192>(A, B, C.row_ptr.get(), last_ovf.get(), tier_rows[2], tier_n[2], 1,
                           long_flag, s);
             if (read_scalar(last_ovf.get(), s, hs) > 0)
                 fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
@@ -584,9 +627,9 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     }
     ProfScope pf(values ? "spgemm_fill" : "spgemm_fill_pattern", s, 0);
     if (!values) {
-        pattern_tier<256, 1>(A, B, C, nullptr, n, kWarps, s);  // rows that fit the first tier
-        if (tier_n[1] > 0) pattern_tier<2048, 1>(A, B, C, tier_rows[1], tier_n[1], kWarps, s);
-        if (tier_n[2] > 0) pattern_tier<8192, 1>(A, B, C, tier_rows[2], tier_n[2], 1, s);
+        pattern_tier<256>(A, B, C, nullptr, n, kWarps, s);  // rows that fit the first tier
+        if (tier_n[1] > 0) pattern_tier<2048>(A, B, C, tier_rows[1], tier_n[1], kWarps, s);
+        if (tier_n[2] > 0) pattern_tier<8192>(A, B, C, tier_rows[2], tier_n[2], 1, s);
         DPP_CK(cudaStreamSynchronize(s));
         return;
     }
@@ -608,12 +651,12 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
         DPP_LAUNCH_CK();
     }
     if (n_long < n) {
-        if (max_u <= 32) scatter_g<32>(G, A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 64) scatter_g<64>(G, A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 128) scatter_g<128>(G, A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 256) scatter_g<256>(G, A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 512) scatter_g<512>(G, A, B, C, wide.get(), long_flag, s);
-        else scatter_g<1024>(G, A, B, C, wide.get(), long_flag, s);
+        if (max_u <= 32) scatter_tier<32>(A, B, C, wide.get(), long_flag, s);
+        else if (max_u <= 64) scatter_tier<64>(A, B, C, wide.get(), long_flag, s);
+        else if (max_u <= 128) scatter_tier<128>(A, B, C, wide.get(), long_flag, s);
+        else if (max_u <= 256) scatter_tier<256>(A, B, C, wide.get(), long_flag, s);
+        else if (max_u <= 512) scatter_tier<512>(A, B, C, wide.get(), long_flag, s);
+        else scatter_tier<1024>(A, B, C, wide.get(), long_flag, s);
     }
     const int n_wide = read_scalar(wide.get(), s, hs);
     if (n_wide > 0) {

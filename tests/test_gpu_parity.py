@@ -107,6 +107,46 @@ def test_amg_levels_are_galerkin_products(DPPSystem):
     s.close()
 
 
+def test_galerkin_products_3d_are_exact_and_deterministic(DPPSystem):
+    # 3D 20^3 cubes: 18,522 level-0 rows, so every row of A P and P^T (A P)
+    # takes the warp-per-row product kernels (no block-per-row path); two
+    # setups must give bit-identical coarse matrices (fixed summation order).
+    P = inputs.heterogeneous_problem(3, 20, seed=8, beta=1.0)
+    s1 = DPPSystem.from_problem(P).setup_pc()
+    s2 = DPPSystem.from_problem(P).setup_pc()
+    sz, (rp, col, val), (prp, pcol, pval) = s1.level(0)
+    assert sz["rows"] >= 16384
+    A = csr_from_export(rp, col, val, (sz["rows"], sz["rows"]))
+    Pm = csr_from_export(prp, pcol, pval, (sz["rows"], sz["p_cols"]))
+    sz1, (rp1, col1, val1), _ = s1.level(1, with_p=False)
+    Ac = csr_from_export(rp1, col1, val1, (sz1["rows"], sz1["rows"]))
+    ref = (Pm.T @ A @ Pm).tocsr()
+    ref.sort_indices()
+    assert abs(Ac - ref).max() <= 1e-12 * abs(ref).max()
+    for l in range(1, sz["levels"]):
+        a = s1.level(l, with_p=False)[1]
+        b = s2.level(l, with_p=False)[1]
+        for u, v in zip(a, b):
+            assert torch.equal(u, v), f"level {l} differs between two setups"
+    s1.close()
+    s2.close()
+
+
+def test_release_cached_memory_keeps_live_handles(DPPSystem):
+    from paper_1808_08328_gb300 import binding as B
+    P = inputs.heterogeneous_problem(2, 24, seed=3, beta=1.0)
+    s = DPPSystem.from_problem(P).setup_pc()
+    x0, _ = s.solve(rtol=1e-10)
+    tmp = DPPSystem.from_problem(inputs.heterogeneous_problem(2, 30, seed=4)).setup_pc()
+    tmp.close()
+    B.dpp_release_cached_memory()
+    x1, info = s.solve(rtol=1e-10)
+    assert info["status"] == 0
+    assert torch.equal(x0, x1)
+    s.close()
+    B.dpp_release_cached_memory()
+
+
 SOLVES = [("het2d_n32", lambda: inputs.heterogeneous_problem(2, 32, seed=0, beta=1.0)),
           ("mms2d_n32", lambda: inputs.mms_problem(2, 32)),
           ("het3d_n8", lambda: inputs.heterogeneous_problem(3, 8, seed=0, beta=1.0)),
