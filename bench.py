@@ -286,8 +286,11 @@ def bench_gb300(args):
     fam = {k: v for k, v in fam.items() if v["launches"]}
     phases = {f: B.dpp_profile_read(f)["ms"] / args.steps
               for f in ("assemble", "setup_selfp", "setup_amg", "setup_power", "setup_aggregate",
-                        "setup_prolong_rap", "setup_coarse_inverse", "setup_tune", "spgemm_numeric",
-                        "spgemm_pattern", "spgemm_alloc", "spgemm_fill", "spgemm_fill_pattern")}
+                        "setup_strength", "setup_mis", "setup_prolong_rap", "setup_coarse_inverse",
+                        "setup_tune", "spgemm_numeric", "spgemm_pattern", "spgemm_count",
+                        "spgemm_alloc", "spgemm_fill", "spgemm_fill_pattern", "spgemm_AP0_L0",
+                        "spgemm_AP_L0", "spgemm_RAP_L0", "spgemm_AP0_Lc", "spgemm_AP_Lc",
+                        "spgemm_RAP_Lc", "krylov_pc", "krylov_orth")}
     B.dpp_profile_enable(False)
     clk = clocks.stop()
     if dist:

@@ -300,11 +300,17 @@ dpp_status dpp_release_cached_memory(void);
 int64_t dpp_launch_count(void);
 
 /* Enable (on != 0) or disable per-family CUDA-event timing and reset the
- * records. When enabled, the library records a start and a stop event on the
- * launching stream around every launch of the timed families: "apply_K",
- * "apply_K_fp32", "mass_cheb" and "amg_csr_spmv". For each such launch it also
- * accumulates the algorithmic bytes: every matrix value, index and vector
- * entry, counted once. Timing adds a few microseconds of host work per launch. */
+ * records (waits for the device first: the timing events are reused). When
+ * enabled, the library records a start and a stop event on the launching
+ * stream around every launch of the kernel families "apply_K",
+ * "apply_K_fp32", "mass_cheb", "mass_cheb_fp32", "amg_spmv_L0",
+ * "amg_spmv_L0_fp32" (level-0 SpMVs of the V-cycle), "amg_csr_spmv" and
+ * "amg_csr_spmv_fp32" (all other AMG SpMVs), and around the phases
+ * "assemble", "setup_*", "spgemm_*", "krylov_pc" and "krylov_orth". For the
+ * kernel families it also accumulates the algorithmic bytes: every matrix
+ * value, index and vector entry, counted once. Timing adds about a
+ * microsecond of host work per timed range; ranges inside a CUDA graph
+ * capture are not timed. */
 dpp_status dpp_profile_enable(int32_t on);
 
 /* Totals for one family since the last dpp_profile_enable: launches, device

@@ -39,7 +39,23 @@ struct Family {
 };
 std::mutex g_prof_mu;
 std::map<std::string, Family> g_prof;
+std::map<int, std::vector<cudaEvent_t>> g_event_pool;  // per device
+std::map<int, size_t> g_event_next;
 }  // namespace
+
+cudaEvent_t profile_event() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    auto& pool = g_event_pool[dev];
+    size_t& next = g_event_next[dev];
+    if (next == pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pool.push_back(e);
+    }
+    return pool[next++];
+}
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 namespace {
@@ -638,13 +654,10 @@ int64_t dpp_launch_count(void) { return g_launches.load(); }
 
 dpp_status dpp_profile_enable(int32_t on) {
     return guarded("dpp_profile_enable", [&]() -> dpp_status {
+        DPP_CK(cudaDeviceSynchronize());  // recorded events are reused from here on
         std::lock_guard<std::mutex> lk(g_prof_mu);
-        for (auto& kv : g_prof)
-            for (auto& e : kv.second.events) {
-                cudaEventDestroy(e.first);
-                cudaEventDestroy(e.second);
-            }
         g_prof.clear();
+        for (auto& kv : g_event_next) kv.second = 0;
         g_profiling.store(on != 0);
         return DPP_OK;
     });

@@ -185,30 +185,49 @@ __global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
 }
 
 // ------------------------------------------------------------------ aggregation
+// Strength of connection, one warp per row: j != i is a strong neighbour of i
+// when |a_ij| >= theta sqrt(|a_ii| |a_jj|), tested as a_ij^2 >= theta^2 |a_ii| |a_jj|
+// (no FP64 square root, which is slow on this GPU's FP64 pipe). Ballots keep
+// the row's column order, so the fill pass writes exactly the entries the
+// count pass counted.
+__device__ __forceinline__ bool is_strong(int64_t i, int j, double aij, double di,
+                                          const double* __restrict__ dabs, double theta2) {
+    return j != i && aij * aij >= theta2 * (di * dabs[j]);
+}
+
 __global__ void k_strength_count(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
                                  const double* __restrict__ val, const double* __restrict__ dabs,
-                                 double theta, int* __restrict__ cnt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                 double theta2, int* __restrict__ cnt) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    int c = 0;
     const double di = dabs[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        int j = col[p];
-        if (j != i && fabs(val[p]) >= theta * sqrt(di * dabs[j])) ++c;
+    const int p1 = rp[i + 1];
+    int c = 0;
+    for (int p0 = rp[i]; p0 < p1; p0 += 32) {
+        const int p = p0 + lane;
+        const bool st = p < p1 && is_strong(i, col[p], val[p], di, dabs, theta2);
+        c += __popc(__ballot_sync(0xffffffffu, st));
     }
-    cnt[i] = c;
+    if (lane == 0) cnt[i] = c;
 }
 
 __global__ void k_strength_fill(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
                                 const double* __restrict__ val, const double* __restrict__ dabs,
-                                double theta, const int* __restrict__ srp, int* __restrict__ scol) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                double theta2, const int* __restrict__ srp, int* __restrict__ scol) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    int q = srp[i];
     const double di = dabs[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-        int j = col[p];
-        if (j != i && fabs(val[p]) >= theta * sqrt(di * dabs[j])) scol[q++] = j;
+    const int p1 = rp[i + 1];
+    int q = srp[i];
+    for (int p0 = rp[i]; p0 < p1; p0 += 32) {
+        const int p = p0 + lane;
+        const int j = p < p1 ? col[p] : -1;
+        const bool st = p < p1 && is_strong(i, j, val[p], di, dabs, theta2);
+        const unsigned m = __ballot_sync(0xffffffffu, st);
+        if (st) scol[q + __popc(m & ((1u << lane) - 1u))] = j;
+        q += __popc(m);
     }
 }
 
@@ -223,13 +242,25 @@ __global__ void k_mis_t0(int64_t n, const int* __restrict__ state, uint64_t* __r
     if (i < n) t0[i] = mis_key(state[i], i);
 }
 
+// tout[i] = max of tin over i and its strong neighbours; kMisLanes lanes per row
+constexpr int kMisLanes = 8;
 __global__ void k_mis_max(int64_t n, const int* __restrict__ srp, const int* __restrict__ scol,
                           const uint64_t* __restrict__ tin, uint64_t* __restrict__ tout) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint64_t m = tin[i];
-    for (int p = srp[i]; p < srp[i + 1]; ++p) m = max(m, tin[scol[p]]);
-    tout[i] = m;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / kMisLanes;
+    const int sub = (int)(t % kMisLanes);
+    const bool valid = i < n;  // every lane stays for the shuffles below
+    uint64_t m = 0;
+    if (valid) {
+        if (sub == 0) m = tin[i];
+        for (int p = srp[i] + sub; p < srp[i + 1]; p += kMisLanes) m = max(m, tin[scol[p]]);
+    }
+#pragma unroll
+    for (int o = kMisLanes / 2; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, m, o, kMisLanes);
+        m = max(m, y);
+    }
+    if (valid && sub == 0) tout[i] = m;
 }
 
 __global__ void k_mis_update(int64_t n, int* __restrict__ state, const uint64_t* __restrict__ t0,
@@ -432,22 +463,26 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
 
         // strength graph
         ProfScope pr_agg("setup_aggregate", s, 0);
+        ProfScope pr_str("setup_strength", s, 0);
+        const double theta2 = o.strength_theta * o.strength_theta;
         Csr S;
         S.n_rows = S.n_cols = n;
         S.row_ptr.alloc(n + 1);
         DPP_CK(cudaMemsetAsync(S.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
-        k_strength_count<<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
-                                                      L.A.val.get(), dabs.get(), o.strength_theta,
+        k_strength_count<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                      L.A.val.get(), dabs.get(), theta2,
                                                       S.row_ptr.get());
         DPP_LAUNCH_CK();
         S.nnz = exclusive_scan(S.row_ptr.get(), S.row_ptr.get(), n + 1, s, hs);
         S.col.alloc(std::max<int64_t>(S.nnz, 1));
-        k_strength_fill<<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
-                                                     L.A.val.get(), dabs.get(), o.strength_theta,
+        k_strength_fill<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                     L.A.val.get(), dabs.get(), theta2,
                                                      S.row_ptr.get(), S.col.get());
         DPP_LAUNCH_CK();
 
+        pr_str.stop();
         // distance-2 maximal independent set
+        ProfScope pr_mis("setup_mis", s, 0);
         DBuf<int> state(n), undecided(1);
         DBuf<uint64_t> t0(n), t1(n), t2(n);
         k_fill_int<<<grid_for(n, B), B, 0, s>>>(n, kUnd, state.get());
@@ -456,9 +491,9 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
             DPP_CK(cudaMemsetAsync(undecided.get(), 0, sizeof(int), s));
             k_mis_t0<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get());
             DPP_LAUNCH_CK();
-            k_mis_max<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t0.get(), t1.get());
+            k_mis_max<<<grid_for(n * kMisLanes, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t0.get(), t1.get());
             DPP_LAUNCH_CK();
-            k_mis_max<<<grid_for(n, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t1.get(), t2.get());
+            k_mis_max<<<grid_for(n * kMisLanes, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t1.get(), t2.get());
             DPP_LAUNCH_CK();
             k_mis_update<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get(), t2.get(),
                                                       undecided.get());
@@ -466,6 +501,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
             if (read_scalar(undecided.get(), s, hs) == 0) break;
             if (round == 63) fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: MIS-2 did not finish");
         }
+        pr_mis.stop();
         DBuf<int> root_id(n + 1), agg1(n), agg(n);
         k_root_flags<<<grid_for(n + 1, B), B, 0, s>>>(n, state.get(), root_id.get());
         DPP_LAUNCH_CK();

@@ -44,6 +44,10 @@ inline void fail(dpp_status s, const std::string& m) { throw Error(s, m); }
 void count_launch();
 bool profiling_enabled();
 void profile_record(const char* family, cudaEvent_t start, cudaEvent_t stop, double alg_bytes);
+// A timing event from a per-device pool that dpp_profile_enable recycles
+// (nullptr on failure); creating events in the timed path would cost more
+// host time than the launches being timed.
+cudaEvent_t profile_event();
 
 // Times everything issued on `s` inside its scope when profiling is enabled.
 struct ProfScope {
@@ -59,13 +63,17 @@ struct ProfScope {
         fam = family;
         s = st;
         bytes = alg_bytes;
-        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { fam = nullptr; return; }
+        a = profile_event();
+        b = profile_event();
+        if (!a || !b) { fam = nullptr; return; }
         cudaEventRecord(a, s);
     }
-    ~ProfScope() {
+    ~ProfScope() { stop(); }
+    void stop() {  // end the timed range early (idempotent)
         if (!fam) return;
         cudaEventRecord(b, s);
         profile_record(fam, a, b, bytes);
+        fam = nullptr;
     }
 };
 

@@ -435,17 +435,138 @@ __global__ void k_row_len_max(int64_t n, const int* __restrict__ rp, const int* 
 }
 
 // S_p rows for both networks. The pattern is the pair graph squared; it is
-// produced by the product kernels above with A = B = pair graph.
+// produced by the product kernels above with A = B = pair graph. Row a:
+//   S_pi[a][c] = D_i[a][c] - sum_b C[a][b] . B[b][c] / M_i[b]
+// (C the pressure-velocity and B the velocity-pressure pair blocks, M_i the
+// diagonal velocity mass). One warp per node a: the D terms are written into
+// shared accumulators first, then the products (b in N(a), c in N(b)) run
+// 32 per round in (b, c) order as in the general product kernels, and lanes of
+// one round that hit the same column subtract in lane order. Every entry is
+// therefore summed over b in increasing order, as the definition reads. Rows
+// with more than CAP columns are listed in `wide` for k_selfp_values.
+template <int DIM, int CAP>
+__global__ void __launch_bounds__(128, 8)
+k_selfp_scatter(int64_t n_nodes, const int* __restrict__ prp, const int* __restrict__ pcol,
+                const int* __restrict__ slice_ptr, const double* __restrict__ pv,
+                const double* __restrict__ mdiag, const int* __restrict__ srp,
+                const int* __restrict__ scol, double* __restrict__ sval, int64_t nnz_half,
+                int* __restrict__ wide) {
+    constexpr int NV = pair_values(DIM);
+    constexpr int HT = 2 * CAP;
+    constexpr int WPB = 4;
+    __shared__ int sh_keys[WPB][HT];
+    __shared__ int sh_slot[WPB][HT];
+    __shared__ double sh_acc[WPB][2][CAP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * WPB + warp;
+    if (a >= n_nodes) return;
+    const int e0 = srp[a], u = srp[a + 1] - e0;
+    if (u > CAP) {
+        if (lane == 0) wide[atomicAdd(&wide[0], 1) + 1] = (int)a;
+        return;
+    }
+    int* keys = sh_keys[warp];
+    int* slot = sh_slot[warp];
+    double* acc1 = sh_acc[warp][0];
+    double* acc2 = sh_acc[warp][1];
+    auto pval = [&](int row, int p, int k) -> double {
+        const int64_t grp = (int64_t)slice_ptr[row >> 5] + (p - prp[row]);
+        return pv[(grp * NV + k) * kSell + (row & 31)];
+    };
+    for (int t = lane; t < HT; t += 32) keys[t] = -1;
+    for (int e = lane; e < CAP; e += 32) acc1[e] = acc2[e] = 0.0;
+    __syncwarp();
+    for (int e = lane; e < u; e += 32) {  // the row's columns are distinct
+        const int c = scol[e0 + e];
+        hs_insert<HT>(keys, c);
+    }
+    __syncwarp();
+    for (int e = lane; e < u; e += 32) slot[hs_find<HT>(keys, scol[e0 + e])] = e;
+    __syncwarp();
+    const int pa0 = prp[a], pa1 = prp[a + 1];
+    for (int pac = pa0 + lane; pac < pa1; pac += 32) {  // D terms: distinct columns
+        const int e = slot[hs_find<HT>(keys, pcol[pac])];
+        acc1[e] = pval((int)a, pac, 2 + 2 * DIM);
+        acc2[e] = pval((int)a, pac, 3 + 2 * DIM);
+    }
+    __syncwarp();
+    for (int pc0 = pa0; pc0 < pa1; pc0 += 32) {
+        const int pab = pc0 + lane;
+        int b = 0, bs = 0, len = 0;
+        double cab[DIM], m1 = 0.0, m2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cab[k] = 0.0;
+        if (pab < pa1) {
+            b = pcol[pab];
+            bs = prp[b];
+            len = prp[b + 1] - bs;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) cab[k] = pval((int)a, pab, 2 + DIM + k);
+            m1 = mdiag[2 * b];
+            m2 = mdiag[2 * b + 1];
+        }
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(kFull, inc, 31);
+        const int excl = inc - len;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(kFull, excl, j + step);
+                if (ex <= t) j += step;
+            }
+            const int bj = __shfl_sync(kFull, b, j);
+            const int pbc = __shfl_sync(kFull, bs, j) + (t - __shfl_sync(kFull, excl, j));
+            double cj[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) cj[k] = __shfl_sync(kFull, cab[k], j);
+            const double mj1 = __shfl_sync(kFull, m1, j), mj2 = __shfl_sync(kFull, m2, j);
+            const bool act = t < total;
+            int e = -1 - lane;
+            double dot = 0.0;
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) dot += cj[k] * pval(bj, pbc, 2 + k);
+                e = slot[hs_find<HT>(keys, pcol[pbc])];
+            }
+            const unsigned peers = __match_any_sync(kFull, e);
+            const int order = __popc(peers & ((1u << lane) - 1u));
+            const int n_sub = (int)__reduce_max_sync(kFull, (unsigned)__popc(peers));
+            for (int r = 0; r < n_sub; ++r) {
+                if (act && order == r) {
+                    acc1[e] -= dot * mj1;
+                    acc2[e] -= dot * mj2;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < u; e += 32) {
+        sval[e0 + e] = acc1[e];
+        sval[nnz_half + e0 + e] = acc2[e];
+    }
+}
+
+// Entry-per-lane form with a binary search per (a, b, c): used for the rows
+// listed in rows[0..rows[-1]) that are too wide for k_selfp_scatter.
 template <int DIM>
-__global__ void k_selfp_values(int64_t n_nodes, const int* __restrict__ prp,
+__global__ void k_selfp_values(const int* __restrict__ rows, const int* __restrict__ prp,
                                const int* __restrict__ pcol, const int* __restrict__ slice_ptr,
                                const double* __restrict__ pv, const double* __restrict__ mdiag,
                                const int* __restrict__ srp, const int* __restrict__ scol,
                                double* __restrict__ sval, int64_t nnz_half) {
     constexpr int NV = pair_values(DIM);
-    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (a >= n_nodes) return;
+    if (w >= rows[-1]) return;
+    const int64_t a = rows[w];
     auto pval = [&](int row, int p, int k) -> double {
         int64_t grp = (int64_t)slice_ptr[row >> 5] + (p - prp[row]);
         return pv[(grp * NV + k) * kSell + (row & 31)];
@@ -724,15 +845,30 @@ void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t
     k_dup_pattern<<<grid_for(std::max<int64_t>(nnz, n + 1), B), B, 0, s>>>(n, nnz, S.row_ptr.get(),
                                                                            S.col.get());
     DPP_LAUNCH_CK();
+    constexpr int kSelfpCap = 128;
+    DBuf<int> wide(n + 1);
+    DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
     if (P.dim == 2)
-        k_selfp_values<2><<<grid_for(n * 32, B), B, 0, s>>>(
+        k_selfp_scatter<2, kSelfpCap><<<grid_for(n, 4), 128, 0, s>>>(
             n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(), mdiag,
-            Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz);
+            Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz, wide.get());
     else
-        k_selfp_values<3><<<grid_for(n * 32, B), B, 0, s>>>(
+        k_selfp_scatter<3, kSelfpCap><<<grid_for(n, 4), 128, 0, s>>>(
             n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(), mdiag,
-            Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz);
+            Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz, wide.get());
     DPP_LAUNCH_CK();
+    const int n_wide = read_scalar(wide.get(), s, hs);
+    if (n_wide > 0) {
+        if (P.dim == 2)
+            k_selfp_values<2><<<grid_for((int64_t)n_wide * 32, B), B, 0, s>>>(
+                wide.get() + 1, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(),
+                mdiag, Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz);
+        else
+            k_selfp_values<3><<<grid_for((int64_t)n_wide * 32, B), B, 0, s>>>(
+                wide.get() + 1, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(),
+                mdiag, Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz);
+        DPP_LAUNCH_CK();
+    }
     DPP_CK(cudaStreamSynchronize(s));
 }
 
