@@ -118,6 +118,9 @@ typedef struct {
     int32_t check_every;       /* host convergence check period in iterations (default 1) */
     double inner_rtol;         /* mixed precision: inner cycle reduction target (default 1e-4) */
     int64_t wait_budget_cycles;/* bound for device-side waits, 0 = library default */
+    double reorth_eta;         /* second Gram-Schmidt pass when ||w|| drops below reorth_eta
+                                  times its value before the first pass (DGKS test; 0 = never,
+                                  1 = always; default 0.1) */
 } dpp_solve_opts;
 
 typedef struct {
@@ -312,6 +315,11 @@ int64_t dpp_launch_count(void);
  * microsecond of host work per timed range; ranges inside a CUDA graph
  * capture are not timed. */
 dpp_status dpp_profile_enable(int32_t on);
+
+/* Restrict timing to the comma-separated families in `families` (NULL or ""
+ * = every family, the default), so that a long timed run pays for the events
+ * of the families it reads only. Takes effect for ranges opened afterwards. */
+dpp_status dpp_profile_select(const char* families);
 
 /* Totals for one family since the last dpp_profile_enable: launches, device
  * milliseconds (summed event intervals, synchronising on them), algorithmic

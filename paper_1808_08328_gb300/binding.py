@@ -55,6 +55,7 @@ class dpp_solve_opts(C.Structure):
         ("rtol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
         ("x0_zero", C.c_int32), ("x_memory", C.c_int32), ("check_every", C.c_int32),
         ("inner_rtol", C.c_double), ("wait_budget_cycles", C.c_int64),
+        ("reorth_eta", C.c_double),
     ]
 
 
@@ -105,6 +106,7 @@ _SIGS = {
     "dpp_release_cached_memory": (C.c_int, []),
     "dpp_launch_count": (C.c_int64, []),
     "dpp_profile_enable": (C.c_int, [C.c_int32]),
+    "dpp_profile_select": (C.c_int, [C.c_char_p]),
     "dpp_profile_read": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double)]),
 }
@@ -300,6 +302,12 @@ def dpp_launch_count() -> int:
 
 def dpp_profile_enable(on: bool) -> None:
     _check(load().dpp_profile_enable(1 if on else 0))
+
+
+def dpp_profile_select(families=None) -> None:
+    """Time only these families (an iterable of names); None times every family."""
+    arg = ",".join(families).encode() if families else None
+    _check(load().dpp_profile_select(arg))
 
 
 def dpp_profile_read(family: str) -> dict:

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <new>
+#include <set>
 
 #include "amg.cuh"
 
@@ -41,7 +42,15 @@ std::mutex g_prof_mu;
 std::map<std::string, Family> g_prof;
 std::map<int, std::vector<cudaEvent_t>> g_event_pool;  // per device
 std::map<int, size_t> g_event_next;
+std::atomic<bool> g_prof_all{true};
+std::set<std::string> g_prof_select;  // timed families when !g_prof_all
 }  // namespace
+
+bool profiling_selected(const char* family) {
+    if (g_prof_all.load(std::memory_order_relaxed)) return true;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_prof_select.count(family) != 0;
+}
 
 cudaEvent_t profile_event() {
     int dev = 0;
@@ -216,6 +225,7 @@ void dpp_solve_opts_default(dpp_solve_opts* o) {
     o->check_every = 1;
     o->inner_rtol = 1e-4;
     o->wait_budget_cycles = 0;
+    o->reorth_eta = 0.1;
 }
 
 const char* dpp_status_string(int32_t s) {
@@ -659,6 +669,23 @@ dpp_status dpp_profile_enable(int32_t on) {
         g_prof.clear();
         for (auto& kv : g_event_next) kv.second = 0;
         g_profiling.store(on != 0);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_profile_select(const char* families) {
+    return guarded("dpp_profile_select", [&]() -> dpp_status {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_select.clear();
+        const std::string all = families ? families : "";
+        size_t b = 0;
+        while (b <= all.size()) {
+            size_t e = all.find(',', b);
+            if (e == std::string::npos) e = all.size();
+            if (e > b) g_prof_select.insert(all.substr(b, e - b));
+            b = e + 1;
+        }
+        g_prof_all.store(g_prof_select.empty());
         return DPP_OK;
     });
 }

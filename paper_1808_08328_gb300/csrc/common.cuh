@@ -43,6 +43,7 @@ inline void fail(dpp_status s, const std::string& m) { throw Error(s, m); }
 // Launch accounting and optional per-family CUDA-event timing (abi.cu).
 void count_launch();
 bool profiling_enabled();
+bool profiling_selected(const char* family);  // enabled and in the dpp_profile_select list
 void profile_record(const char* family, cudaEvent_t start, cudaEvent_t stop, double alg_bytes);
 // A timing event from a per-device pool that dpp_profile_enable recycles
 // (nullptr on failure); creating events in the timed path would cost more
@@ -56,7 +57,7 @@ struct ProfScope {
     double bytes = 0;
     cudaEvent_t a = nullptr, b = nullptr;
     ProfScope(const char* family, cudaStream_t st, double alg_bytes) {
-        if (!profiling_enabled()) return;
+        if (!profiling_enabled() || !profiling_selected(family)) return;
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
             return;  // no event records inside a graph capture

@@ -7,7 +7,7 @@
 // Each iteration j:
 //   z_j = P^-1 v_j;  w = K z_j;
 //   classical Gram-Schmidt, h = V^T w, w -= V h, repeated once (h += V^T w,
-//   w -= V h') when the first pass cancelled more than 1/sqrt(2) of ||w||;
+//   w -= V h') when the first pass left less than reorth_eta of ||w||;
 //   h_{j+1,j} = ||w||;  v_{j+1} = w / h_{j+1,j};
 //   then a Givens rotation of column j of the Hessenberg matrix gives the
 //   residual estimate |g_{j+1}|.
@@ -121,17 +121,21 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
             }
             double* hd = W.dscal.get();
             ProfScope po("krylov_orth", s, 0);
-            // classical Gram-Schmidt; a second pass only when the first lost more
-            // than a factor 1/sqrt(2) of ||w|| (Daniel, Gragg, Kaufman & Stewart,
-            // Math. Comp. 30, 1976)
+            // classical Gram-Schmidt; a second pass only when the first left less
+            // than reorth_eta of ||w|| (the test of Daniel, Gragg, Kaufman &
+            // Stewart, Math. Comp. 30, 1976, with a threshold chosen by measurement)
+            ProfScope pk("krylov_orth_kernels", s, 0);
             dot(W.R, W.w.get(), W.w.get(), n, hd + 2 * m + 4, s);
             multidot(W.R, V, n, j + 1, W.w.get(), n, hd, s);
             multi_axpy_sub(V, n, j + 1, hd, W.w.get(), n, s);
             dot(W.R, W.w.get(), W.w.get(), n, hd + 2 * m + 2, s);
+            pk.stop();
+            ProfScope pw("krylov_orth_wait", s, 0);
             double* hh = (double*)hs.get((2 * m + 8) * sizeof(double));
             DPP_CK(cudaMemcpyAsync(hh, hd, (2 * m + 5) * sizeof(double), cudaMemcpyDeviceToHost, s));
             DPP_CK(cudaStreamSynchronize(s));
-            const bool reorth = hh[2 * m + 2] < 0.5 * hh[2 * m + 4];
+            const double eta = std::min(std::max(o.reorth_eta, 0.0), 1.0);
+            const bool reorth = hh[2 * m + 2] < eta * eta * hh[2 * m + 4];
             for (int i = 0; i <= j; ++i) h_at(i, j) = hh[i];
             if (reorth) {
                 multidot(W.R, V, n, j + 1, W.w.get(), n, hd + m + 1, s);
@@ -141,6 +145,7 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
                 DPP_CK(cudaStreamSynchronize(s));
                 for (int i = 0; i <= j; ++i) h_at(i, j) += hh[m + 1 + i];
             }
+            pw.stop();
             const double hn = std::sqrt(std::max(hh[2 * m + 2], 0.0));
             h_at(j + 1, j) = hn;
             if (!std::isfinite(hn)) { nonfinite = true; ncol = j; break; }
