@@ -106,6 +106,10 @@ typedef struct {
     double cheb_ratio;         /* AMG smoothing interval [lmax/ratio, 1.1 lmax] (default 10) */
     int32_t use_lumped_diag;   /* 0: diag(K_uu) as written (default); 1: row-sum lumping */
     int32_t precision;         /* dpp_precision of the hierarchy values */
+    int32_t sell_min_rows;     /* level matrices with at least this many rows also get a SELL-32
+                                  copy (0 = library default, 65536) */
+    int32_t spmv_format;       /* AMG SpMV format: 0 = autotuned among SELL-32 (where built) and
+                                  CSR (default), 1 = CSR only, 2 = SELL-32 wherever built */
 } dpp_pc_opts;
 
 /* Krylov options. */

@@ -47,6 +47,7 @@ class dpp_pc_opts(C.Structure):
         ("coarse_max_rows", C.c_int32), ("max_levels", C.c_int32),
         ("strength_theta", C.c_double), ("cheb_ratio", C.c_double),
         ("use_lumped_diag", C.c_int32), ("precision", C.c_int32),
+        ("sell_min_rows", C.c_int32), ("spmv_format", C.c_int32),
     ]
 
 

@@ -213,6 +213,8 @@ void dpp_pc_opts_default(dpp_pc_opts* o) {
     o->cheb_ratio = 10.0;
     o->use_lumped_diag = 0;
     o->precision = DPP_FP64;
+    o->sell_min_rows = 0;
+    o->spmv_format = 0;
 }
 
 void dpp_solve_opts_default(dpp_solve_opts* o) {
@@ -296,6 +298,8 @@ dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t 
         require(o.strength_theta >= 0 && o.strength_theta < 1, "strength_theta in [0,1)");
         require(o.cheb_ratio > 1, "cheb_ratio > 1");
         require(o.precision == DPP_FP64 || o.precision == DPP_MIXED_FP32_FP64, "bad precision");
+        require(o.sell_min_rows >= 0, "sell_min_rows >= 0");
+        require(o.spmv_format >= 0 && o.spmv_format <= 2, "spmv_format in {0,1,2}");
         cudaStream_t s = (cudaStream_t)stream;
         auto* h = new dpp_pc_s();
         try {

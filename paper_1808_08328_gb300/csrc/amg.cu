@@ -75,6 +75,67 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
     }
 }
 
+// ------------------------------------------------------------------ SELL-32 SpMV
+// One thread per row; a warp owns a slice, so every column and value load of
+// the warp is one contiguous 128 B (int, float) or 256 B (double) transaction.
+// Four partial sums keep several gathers in flight. Same MODEs as k_csr_spmv.
+template <int MODE, class T>
+__global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __restrict__ off,
+                                                   const int* __restrict__ col,
+                                                   const T* __restrict__ val,
+                                                   const T* __restrict__ x,
+                                                   const T* __restrict__ b, T* __restrict__ y) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rows) return;
+    const int64_t sl = row >> 5;
+    const int lane = (int)(row & 31);
+    const int e = off[sl + 1];
+    int p = off[sl] + lane;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    for (; p + 96 < e; p += 128) {
+        const int c0 = col[p], c1 = col[p + 32], c2 = col[p + 64], c3 = col[p + 96];
+        const T v0 = val[p], v1 = val[p + 32], v2 = val[p + 64], v3 = val[p + 96];
+        a0 += v0 * __ldg(x + c0);
+        a1 += v1 * __ldg(x + c1);
+        a2 += v2 * __ldg(x + c2);
+        a3 += v3 * __ldg(x + c3);
+    }
+    for (; p < e; p += 32) a0 += val[p] * __ldg(x + col[p]);
+    const T acc = (a0 + a1) + (a2 + a3);
+    if (MODE == 0) y[row] = acc;
+    else if (MODE == 1) y[row] = b[row] - acc;
+    else y[row] += acc;
+}
+
+// slice widths: w[s] = 32 * (longest row of slice s); one warp per slice
+__global__ void k_sell_width(int64_t n_rows, const int* __restrict__ rp, int* __restrict__ w) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t sl = t >> 5;
+    const int64_t row = t;
+    const int64_t n_sl = (n_rows + 31) / 32;
+    int len = (row < n_rows) ? rp[row + 1] - rp[row] : 0;
+    len = __reduce_max_sync(0xffffffffu, len);
+    if ((t & 31) == 0 && sl < n_sl) w[sl] = 32 * len;
+    if (t == 0) w[n_sl] = 0;
+}
+
+template <class T>
+__global__ void k_sell_fill(int64_t n_rows, const int* __restrict__ rp, const int* __restrict__ col,
+                            const T* __restrict__ val, const int* __restrict__ off,
+                            int* __restrict__ scol, T* __restrict__ sval) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rows) return;
+    const int64_t sl = row >> 5;
+    const int lane = (int)(row & 31);
+    const int r0 = rp[row], len = rp[row + 1] - r0;
+    const int width = (off[sl + 1] - off[sl]) / 32;
+    for (int k = 0; k < width; ++k) {
+        const int64_t q = (int64_t)off[sl] + (int64_t)k * 32 + lane;
+        scol[q] = (k < len) ? col[r0 + k] : (int)row;
+        sval[q] = (k < len) ? val[r0 + k] : T(0);
+    }
+}
+
 template <class T> const T* vals(const Csr& A);
 template <> const double* vals<double>(const Csr& A) { return A.val.get(); }
 template <> const float* vals<float>(const Csr& A) { return A.val32.get(); }
@@ -82,10 +143,23 @@ template <> const float* vals<float>(const Csr& A) { return A.val32.get(); }
 template <int MODE, class T>
 void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStream_t s,
                 const char* family = nullptr) {
-    const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (double)(A.n_rows + 1) * 4.0 +
+    const bool sell = lanes == 0 && A.has_sell() &&
+                      (sizeof(T) == 8 ? A.sell_val.get() != nullptr : A.sell_val32.get() != nullptr);
+    // algorithmic bytes: values and column indices of the nonzeros, the row
+    // pointers (CSR only), x once, y (and b) once; SELL padding is not counted
+    const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (sell ? 0.0 : (double)(A.n_rows + 1) * 4.0) +
                        (double)A.n_cols * sizeof(T) + (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : 2);
     ProfScope prof(family ? family : (sizeof(T) == 8 ? "amg_csr_spmv" : "amg_csr_spmv_fp32"), s, alg);
     const int B = 256;
+    if (sell) {
+        const T* sv = (sizeof(T) == 8) ? reinterpret_cast<const T*>(A.sell_val.get())
+                                       : reinterpret_cast<const T*>(A.sell_val32.get());
+        k_sell_spmv<MODE, T><<<grid_for(A.n_rows, B), B, 0, s>>>(A.n_rows, A.sell_off.get(),
+                                                                 A.sell_col.get(), sv, x, b, y);
+        DPP_LAUNCH_CK();
+        return;
+    }
+    if (lanes < 1) lanes = 2;  // SELL requested but not built
     const int64_t thr = A.n_rows * lanes;
     const int g = grid_for(thr, B);
     const int* rp = A.row_ptr.get();
@@ -110,6 +184,26 @@ int pick_lanes(const Csr& A) {
     int l = 2;
     while (l < 32 && l < want) l <<= 1;
     return l;
+}
+
+// SELL-32 copy of a level matrix (FP64 values; amg_make_fp32 adds FP32 ones),
+// built for matrices with at least opts.sell_min_rows rows (default 65536)
+// unless opts.spmv_format asks for CSR only; offsets must fit int32.
+int64_t sell_min_rows(const dpp_pc_opts& o) { return o.sell_min_rows > 0 ? o.sell_min_rows : 65536; }
+
+void build_sell(Csr& A, cudaStream_t s, HostScratch& hs) {
+    const int64_t n = A.n_rows, n_sl = (n + 31) / 32;
+    DBuf<int> off(n_sl + 1);
+    k_sell_width<<<grid_for(n_sl * 32, 256), 256, 0, s>>>(n, A.row_ptr.get(), off.get());
+    DPP_LAUNCH_CK();
+    const int64_t tot = exclusive_scan(off.get(), off.get(), n_sl + 1, s, hs);
+    if (tot <= 0 || tot >= INT32_MAX) return;  // keep CSR only
+    A.sell_col.alloc(tot);
+    A.sell_val.alloc(tot);
+    k_sell_fill<double><<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
+                                                        off.get(), A.sell_col.get(), A.sell_val.get());
+    DPP_LAUNCH_CK();
+    A.sell_off = std::move(off);
 }
 
 // ------------------------------------------------------------------ vectors
@@ -443,6 +537,10 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         Level& L = pc.levels[l];
         const int64_t n = L.A.n_rows;
         L.lanes = pick_lanes(L.A);
+        if (o.spmv_format != 1 && n >= sell_min_rows(o)) {
+            build_sell(L.A, s, hs);
+            if (L.A.has_sell()) L.lanes = 0;  // SELL-32 (the autotuner may still pick CSR)
+        }
         L.dinv.alloc(n);
         DBuf<double> dabs(n);
         DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
@@ -635,9 +733,10 @@ void to_f32(const DBuf<double>& in, DBuf<float>& out, cudaStream_t s) {
 // DPP_TUNE_CACHE names a file, the cache is read from it and new choices are
 // appended to it as JSON lines.
 struct TuneKey {
-    int fp32, kind, log2_rows, avg_nnz;
+    int fp32, kind, log2_rows, avg_nnz, sell;
     bool operator<(const TuneKey& o) const {
-        return std::tie(fp32, kind, log2_rows, avg_nnz) < std::tie(o.fp32, o.kind, o.log2_rows, o.avg_nnz);
+        return std::tie(fp32, kind, log2_rows, avg_nnz, sell) <
+               std::tie(o.fp32, o.kind, o.log2_rows, o.avg_nnz, o.sell);
     }
 };
 std::mutex g_tune_mu;
@@ -655,9 +754,12 @@ void tune_load_locked() {
     while (std::fgets(line, sizeof line, f)) {
         TuneKey k;
         int lanes = 0;
-        if (std::sscanf(line, "{\"fp32\": %d, \"kind\": %d, \"log2_rows\": %d, \"avg_nnz\": %d, \"lanes\": %d}",
-                        &k.fp32, &k.kind, &k.log2_rows, &k.avg_nnz, &lanes) == 5 &&
-            (lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+        if (std::sscanf(line,
+                        "{\"fp32\": %d, \"kind\": %d, \"log2_rows\": %d, \"avg_nnz\": %d, "
+                        "\"sell\": %d, \"lanes\": %d}",
+                        &k.fp32, &k.kind, &k.log2_rows, &k.avg_nnz, &k.sell, &lanes) == 6 &&
+            ((lanes == 0 && k.sell == 1) || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
+             lanes == 32))
             g_tune[k] = lanes;
     }
     std::fclose(f);
@@ -669,8 +771,10 @@ void tune_store_locked(const TuneKey& k, int lanes) {
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"fp32\": %d, \"kind\": %d, \"log2_rows\": %d, \"avg_nnz\": %d, \"lanes\": %d}\n",
-                 k.fp32, k.kind, k.log2_rows, k.avg_nnz, lanes);
+    std::fprintf(f,
+                 "{\"fp32\": %d, \"kind\": %d, \"log2_rows\": %d, \"avg_nnz\": %d, \"sell\": %d, "
+                 "\"lanes\": %d}\n",
+                 k.fp32, k.kind, k.log2_rows, k.avg_nnz, k.sell, lanes);
     std::fclose(f);
 }
 
@@ -682,19 +786,23 @@ int tune_lanes(const Csr& A, const T* x, const T* b, T* y, int kind, cudaStream_
     key.log2_rows = 0;
     for (int64_t r = A.n_rows; r > 1; r >>= 1) ++key.log2_rows;
     key.avg_nnz = (int)std::lround(A.n_rows ? (double)A.nnz / (double)A.n_rows : 0.0);
+    key.sell = A.has_sell() ? 1 : 0;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load_locked();
         auto it = g_tune.find(key);
         if (it != g_tune.end()) return it->second;
     }
-    // candidates: the heuristic choice and its neighbours
+    // candidates: SELL-32 when built (first, so that it wins ties), then the
+    // heuristic CSR choice and its neighbours
     const int h = pick_lanes(A);
-    int cands[3] = {std::max(2, h / 2), h, std::min(32, h * 2)};
+    std::vector<int> cands;
+    if (A.has_sell()) cands.push_back(0);
+    for (int c : {std::max(2, h / 2), h, std::min(32, h * 2)}) cands.push_back(c);
     cudaEvent_t e0, e1;
     DPP_CK(cudaEventCreate(&e0));
     DPP_CK(cudaEventCreate(&e1));
-    int best = h;
+    int best = cands[0];
     float best_ms = 1e30f;
     for (int c : cands) {
         spmv_lanes<MODE, T>(c, A, x, b, y, s);  // warm
@@ -724,7 +832,8 @@ void tune_levels(PcImpl& pc, cudaStream_t s) {
         T* r = lv<T>(L.r, L.r32);
         DPP_CK(cudaMemsetAsync(x, 0, L.A.n_rows * sizeof(T), s));
         DPP_CK(cudaMemsetAsync(b, 0, L.A.n_rows * sizeof(T), s));
-        L.lanes = tune_lanes<1, T>(L.A, x, b, r, 0, s);
+        if (pc.opts.spmv_format == 2 && L.A.has_sell()) L.lanes = 0;  // SELL-32 as asked
+        else L.lanes = tune_lanes<1, T>(L.A, x, b, r, 0, s);
         if (l + 1 < pc.levels.size()) {
             Level& C = pc.levels[l + 1];
             T* cx = lv<T>(C.x, C.x32);
@@ -749,6 +858,7 @@ void amg_make_fp32(PcImpl& pc, cudaStream_t s) {
     for (size_t l = 0; l < pc.levels.size(); ++l) {
         Level& L = pc.levels[l];
         to_f32(L.A.val, L.A.val32, s);
+        if (L.A.has_sell()) to_f32(L.A.sell_val, L.A.sell_val32, s);
         to_f32(L.dinv, L.dinv32, s);
         if (l + 1 < pc.levels.size()) {
             to_f32(L.P.val, L.P.val32, s);

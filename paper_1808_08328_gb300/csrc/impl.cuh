@@ -23,6 +23,14 @@ struct Csr {
     DBuf<int> row_ptr, col;
     DBuf<double> val;
     DBuf<float> val32;
+    // Optional SELL-32 copy (slices of 32 rows, column-major within a slice,
+    // each slice as wide as its longest row; padding = (own row, 0.0)). Built
+    // for level matrices with many rows, where one thread per row fills the GPU.
+    DBuf<int> sell_off;      // [n_slices + 1] entry offsets
+    DBuf<int> sell_col;
+    DBuf<double> sell_val;
+    DBuf<float> sell_val32;
+    bool has_sell() const { return sell_off.get() != nullptr; }
 };
 
 struct ProblemImpl {
