@@ -258,8 +258,9 @@ def bench_gb300(args):
 
     # one untimed step with every family and phase timed: the per-step breakdown,
     # and the dominant kernel family
-    families = ("apply_K", "amg_spmv_L0", "amg_csr_spmv", "mass_cheb", "apply_K_fp32",
-                "amg_spmv_L0_fp32", "amg_csr_spmv_fp32", "mass_cheb_fp32")
+    families = ("apply_K", "amg_spmv_L0", "amg_spmv_Lc", "amg_spmv_PR", "mass_cheb",
+                "apply_K_fp32", "amg_spmv_L0_fp32", "amg_spmv_Lc_fp32", "amg_spmv_PR_fp32",
+                "mass_cheb_fp32", "amg_spmv_setup", "amg_spmv_setup_fp32")
     phase_names = ("assemble", "setup_selfp", "setup_amg", "setup_power", "setup_aggregate",
                    "setup_strength", "setup_mis", "setup_prolong_rap", "setup_coarse_inverse",
                    "setup_tune", "spgemm_numeric", "spgemm_pattern", "spgemm_count",

@@ -310,9 +310,11 @@ int64_t dpp_launch_count(void);
  * records (waits for the device first: the timing events are reused). When
  * enabled, the library records a start and a stop event on the launching
  * stream around every launch of the kernel families "apply_K",
- * "apply_K_fp32", "mass_cheb", "mass_cheb_fp32", "amg_spmv_L0",
- * "amg_spmv_L0_fp32" (level-0 SpMVs of the V-cycle), "amg_csr_spmv" and
- * "amg_csr_spmv_fp32" (all other AMG SpMVs), and around the phases
+ * "apply_K_fp32", "mass_cheb", "mass_cheb_fp32", the V-cycle SpMVs
+ * "amg_spmv_L0" (level-0 matrix), "amg_spmv_Lc" (coarser matrices) and
+ * "amg_spmv_PR" (prolongation and restriction), each also with an "_fp32"
+ * twin, "amg_spmv_setup" and "amg_spmv_setup_fp32" (SpMVs of the setup: power
+ * iterations and the autotuner), and around the phases
  * "assemble", "setup_*", "spgemm_*", "krylov_pc" and "krylov_orth". For the
  * kernel families it also accumulates the algorithmic bytes: every matrix
  * value, index and vector entry, counted once. Timing adds about a

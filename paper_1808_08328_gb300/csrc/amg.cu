@@ -78,30 +78,41 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
 // ------------------------------------------------------------------ SELL-32 SpMV
 // One thread per row; a warp owns a slice, so every column and value load of
 // the warp is one contiguous 128 B (int, float) or 256 B (double) transaction.
-// Four partial sums keep several gathers in flight. Same MODEs as k_csr_spmv.
+// U partial sums keep U gathers in flight: 4 in FP64 (the FP64 pipe is the
+// other limit there), 8 in FP32. Same MODEs as k_csr_spmv.
 template <int MODE, class T>
 __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __restrict__ off,
                                                    const int* __restrict__ col,
                                                    const T* __restrict__ val,
                                                    const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y) {
+    constexpr int U = sizeof(T) == 4 ? 8 : 4;
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= n_rows) return;
     const int64_t sl = row >> 5;
     const int lane = (int)(row & 31);
     const int e = off[sl + 1];
     int p = off[sl] + lane;
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    for (; p + 96 < e; p += 128) {
-        const int c0 = col[p], c1 = col[p + 32], c2 = col[p + 64], c3 = col[p + 96];
-        const T v0 = val[p], v1 = val[p + 32], v2 = val[p + 64], v3 = val[p + 96];
-        a0 += v0 * __ldg(x + c0);
-        a1 += v1 * __ldg(x + c1);
-        a2 += v2 * __ldg(x + c2);
-        a3 += v3 * __ldg(x + c3);
+    T a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = T(0);
+    for (; p + 32 * (U - 1) < e; p += 32 * U) {
+        int c[U];
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            c[u] = col[p + 32 * u];
+            v[u] = val[p + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] += v[u] * __ldg(x + c[u]);
     }
-    for (; p < e; p += 32) a0 += val[p] * __ldg(x + col[p]);
-    const T acc = (a0 + a1) + (a2 + a3);
+    for (; p < e; p += 32) a[0] += val[p] * __ldg(x + col[p]);
+#pragma unroll
+    for (int w = U / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int u = 0; u < w; ++u) a[u] += a[u + w];
+    const T acc = a[0];
     if (MODE == 0) y[row] = acc;
     else if (MODE == 1) y[row] = b[row] - acc;
     else y[row] += acc;
@@ -149,7 +160,7 @@ void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStrea
     // pointers (CSR only), x once, y (and b) once; SELL padding is not counted
     const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (sell ? 0.0 : (double)(A.n_rows + 1) * 4.0) +
                        (double)A.n_cols * sizeof(T) + (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : 2);
-    ProfScope prof(family ? family : (sizeof(T) == 8 ? "amg_csr_spmv" : "amg_csr_spmv_fp32"), s, alg);
+    ProfScope prof(family ? family : (sizeof(T) == 8 ? "amg_spmv_setup" : "amg_spmv_setup_fp32"), s, alg);
     const int B = 256;
     if (sell) {
         const T* sv = (sizeof(T) == 8) ? reinterpret_cast<const T*>(A.sell_val.get())
@@ -533,6 +544,11 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
     pc.levels[0].A = std::move(A0);
     DBuf<int> st(1);
     const int B = 256;
+    // Galerkin products of a symmetric A (S_p is, up to rounding in its
+    // assembly) may be computed as an upper triangle and mirrored
+    constexpr int64_t kMirrorMinRows = 16384;
+    const bool symmetric = is_symmetric(pc.levels[0].A, 1e-10, s, hs);
+    pc.symmetric = symmetric;
     for (int l = 0;; ++l) {
         Level& L = pc.levels[l];
         const int64_t n = L.A.n_rows;
@@ -645,7 +661,15 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         Csr Ac;
         {
             ProfScope q(l == 0 ? "spgemm_RAP_L0" : "spgemm_RAP_Lc", s, 0);
-            spgemm(view(L.R), view(AP), Ac, true, s, hs);
+            // P^T A P is symmetric too: its upper triangle, mirrored, where the
+            // product is large enough (many coarse rows) to repay the mirroring
+            if (symmetric && L.R.n_rows >= kMirrorMinRows) {
+                Csr U;
+                spgemm(view(L.R), view(AP), U, true, s, hs, /*upper_only=*/true);
+                symmetrize_upper(U, Ac, s, hs);
+            } else {
+                spgemm(view(L.R), view(AP), Ac, true, s, hs);
+            }
         }
         pc.levels.emplace_back();
         pc.levels.back().A = std::move(Ac);
@@ -709,12 +733,16 @@ void vcycle_level(PcImpl& pc, size_t l, const T* b, T* x, cudaStream_t s) {
     T* r = lv<T>(L.r, L.r32);
     T* cb = lv<T>(C.b, C.b32);
     T* cx = lv<T>(C.x, C.x32);
-    const char* fam = (l == 0) ? (sizeof(T) == 8 ? "amg_spmv_L0" : "amg_spmv_L0_fp32") : nullptr;
+    // timing families: level-0 A, coarser A, and the transfers P and R
+    const bool f64 = sizeof(T) == 8;
+    const char* fam = (l == 0) ? (f64 ? "amg_spmv_L0" : "amg_spmv_L0_fp32")
+                               : (f64 ? "amg_spmv_Lc" : "amg_spmv_Lc_fp32");
+    const char* fam_pr = f64 ? "amg_spmv_PR" : "amg_spmv_PR_fp32";
     cheb_smooth<T>(pc, L, b, x, true, s, fam);
     spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
-    spmv_lanes<0, T>(L.lanes_R, L.R, r, nullptr, cb, s);
+    spmv_lanes<0, T>(L.lanes_R, L.R, r, nullptr, cb, s, fam_pr);
     vcycle_level<T>(pc, l + 1, cb, cx, s);
-    spmv_lanes<2, T>(L.lanes_P, L.P, cx, nullptr, x, s);
+    spmv_lanes<2, T>(L.lanes_P, L.P, cx, nullptr, x, s, fam_pr);
     cheb_smooth<T>(pc, L, b, x, false, s, fam);
 }
 

@@ -24,8 +24,15 @@ inline CsrView view(const Csr& A) {
 }
 
 // C = A B (sorted columns in every row of B are required and produced in C).
+// upper_only: only the entries C[i][j] with j >= i (the upper triangle of a
+// product known to be symmetric; see symmetrize_upper).
 void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
-            HostScratch& hs);
+            HostScratch& hs, bool upper_only = false);
+// C = U + strict_upper(U)^T for an upper-triangular U (the full symmetric matrix).
+void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs);
+// True when A is square, structurally symmetric and |a_ij - a_ji| <= tol (|a_ij| + |a_ji|)
+// for every entry.
+bool is_symmetric(const Csr& A, double tol, cudaStream_t s, HostScratch& hs);
 void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs);
 // blockdiag(S_p1, S_p2) from the pair values and mdiag = 1/diag(K_uu) per network.
 void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,

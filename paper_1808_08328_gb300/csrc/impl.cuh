@@ -92,6 +92,7 @@ struct PcImpl {
     DBuf<double> coarse_inv;  // dense inverse of the coarsest matrix, row-major
     DBuf<float> coarse_inv32;
     int64_t coarse_n = 0;
+    bool symmetric = false;   // level-0 matrix found symmetric: Galerkin products mirrored
     // preconditioner work vectors (node-interleaved, n_nodes * ns)
     DBuf<double> yu, su, tmp, dcheb;
     DBuf<double> tp, yp;      // split pressures [2][n_nodes]

@@ -74,14 +74,35 @@ __device__ __forceinline__ int hs_find(const int* keys, int key) {
     return -1;
 }
 
+// first position in the sorted col[lo, hi) with col >= key
+__device__ __forceinline__ int lower_bound_col(const int* __restrict__ col, int lo, int hi, int key) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (col[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Start of the part of B's row k that the product row needs: all of it, or,
+// for the upper triangle of a symmetric product (col_lo = the row index), the
+// columns >= col_lo (B's rows are sorted).
+__device__ __forceinline__ int b_row_start(const int* __restrict__ brp, const int* __restrict__ bcol,
+                                           int k, int col_lo) {
+    return (col_lo == INT_MIN) ? brp[k] : lower_bound_col(bcol, brp[k], brp[k + 1], col_lo);
+}
+
 // Calls f(active, q, a_ip) for every product of row i of A B, 32 per round,
 // in (p, q) order; every lane of the warp makes every call (f may use warp
-// collectives), inactive lanes with active == false.
+// collectives), inactive lanes with active == false. Only columns >= col_lo
+// are produced (INT_MIN: all).
 template <bool VALS, class F>
 __device__ __forceinline__ void for_each_product(int i, const int* __restrict__ arp,
                                                  const int* __restrict__ acol,
                                                  const double* __restrict__ aval,
-                                                 const int* __restrict__ brp, int lane, F&& f) {
+                                                 const int* __restrict__ brp,
+                                                 const int* __restrict__ bcol, int col_lo, int lane,
+                                                 F&& f) {
     const int a0 = arp[i], a1 = arp[i + 1];
     for (int pc = a0; pc < a1; pc += 32) {
         const int p = pc + lane;
@@ -89,7 +110,7 @@ __device__ __forceinline__ void for_each_product(int i, const int* __restrict__ 
         double a = 0.0;
         if (p < a1) {
             const int k = acol[p];
-            bs = brp[k];
+            bs = b_row_start(brp, bcol, k, col_lo);
             len = brp[k + 1] - bs;
             if (VALS) a = aval[p];
         }
@@ -120,11 +141,11 @@ __device__ __forceinline__ void for_each_product(int i, const int* __restrict__ 
 template <int HT>
 __device__ bool warp_collect(int i, const int* __restrict__ arp, const int* __restrict__ acol,
                              const int* __restrict__ brp, const int* __restrict__ bcol, int* keys,
-                             int lane) {
+                             int lane, int col_lo) {
     for (int t = lane; t < HT; t += 32) keys[t] = -1;
     __syncwarp();
     bool ok = true;
-    for_each_product<false>(i, arp, acol, nullptr, brp, lane, [&](bool act, int q, double) {
+    for_each_product<false>(i, arp, acol, nullptr, brp, bcol, col_lo, lane, [&](bool act, int q, double) {
         if (act) ok &= hs_insert<HT>(keys, bcol[q]);
     });
     __syncwarp();
@@ -195,7 +216,7 @@ __global__ void k_spgemm_count(int64_t n_rows, const int* __restrict__ arp,
                                const int* __restrict__ acol, const int* __restrict__ brp,
                                const int* __restrict__ bcol, int* __restrict__ count,
                                int* __restrict__ ovf, const int* __restrict__ rows,
-                               const int* __restrict__ is_long) {
+                               const int* __restrict__ is_long, int upper) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -204,7 +225,7 @@ __global__ void k_spgemm_count(int64_t n_rows, const int* __restrict__ arp,
     const int i = rows ? rows[w] : (int)w;
     if (is_long && is_long[i]) return;  // done by the block-per-row kernels
     int* keys = smem + warp * HT;
-    const bool ok = warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane);
+    const bool ok = warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, upper ? i : INT_MIN);
     int c = 0;
     for (int t = lane; t < HT; t += 32) c += (keys[t] >= 0);
     c = __reduce_add_sync(kFull, c);
@@ -219,7 +240,7 @@ template <int HT>
 __global__ void k_spgemm_pattern(int64_t n_rows, const int* __restrict__ arp,
                                  const int* __restrict__ acol, const int* __restrict__ brp,
                                  const int* __restrict__ bcol, const int* __restrict__ crp,
-                                 int* __restrict__ ccol, const int* __restrict__ rows) {
+                                 int* __restrict__ ccol, const int* __restrict__ rows, int upper) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -227,7 +248,7 @@ __global__ void k_spgemm_pattern(int64_t n_rows, const int* __restrict__ arp,
     if (w >= n_work) return;
     const int i = rows ? rows[w] : (int)w;
     int* keys = smem + warp * 2 * HT;
-    if (!warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane)) return;
+    if (!warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, upper ? i : INT_MIN)) return;
     int* list = keys + HT;
     const int u = warp_compact<HT>(keys, list, lane);
     warp_rank<HT>(list, u, lane, ccol + crp[i], keys, nullptr);
@@ -242,7 +263,8 @@ __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
                                  const int* __restrict__ brp, const int* __restrict__ bcol,
                                  const double* __restrict__ bval, const int* __restrict__ crp,
                                  int* __restrict__ ccol, double* __restrict__ cval,
-                                 int* __restrict__ wide, const int* __restrict__ is_long) {
+                                 int* __restrict__ wide, const int* __restrict__ is_long,
+                                 int upper) {
     static_assert(HT >= 2 * CAP, "table at most half full");
     extern __shared__ int smem[];
     constexpr int WPB = 4;
@@ -259,13 +281,14 @@ __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
     int* keys = smem + warp * 2 * HT;
     int* slot = keys + HT;
     double* acc = reinterpret_cast<double*>(smem + WPB * 2 * HT) + (size_t)warp * CAP;
-    warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane);  // cannot overflow (HT >= 2 CAP)
+    const int col_lo = upper ? i : INT_MIN;
+    warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, col_lo);  // cannot overflow (HT >= 2 CAP)
     int* list = reinterpret_cast<int*>(acc);
     const int u = warp_compact<HT>(keys, list, lane);
     warp_rank<HT>(list, u, lane, ccol + c0, keys, slot);
     for (int e = lane; e < u; e += 32) acc[e] = 0.0;
     __syncwarp();
-    for_each_product<true>(i, arp, acol, aval, brp, lane, [&](bool act, int q, double a) {
+    for_each_product<true>(i, arp, acol, aval, brp, bcol, col_lo, lane, [&](bool act, int q, double a) {
         int s = -1 - lane;  // distinct for idle lanes
         double v = 0.0;
         if (act) {
@@ -291,14 +314,15 @@ __global__ void k_spgemm_wide(const int* __restrict__ arp, const int* __restrict
                               const int* __restrict__ bcol, const double* __restrict__ bval,
                               const int* __restrict__ crp, int* __restrict__ ccol,
                               double* __restrict__ cval, const int* __restrict__ rows,
-                              int* __restrict__ status) {
+                              int* __restrict__ status, int upper) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (w >= rows[-1]) return;
     const int i = rows[w];
+    const int col_lo = upper ? i : INT_MIN;
     int* keys = smem + warp * 2 * HT;
-    if (!warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane)) {
+    if (!warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, col_lo)) {
         if (lane == 0) atomicOr(status, 1);
         return;
     }
@@ -310,7 +334,7 @@ __global__ void k_spgemm_wide(const int* __restrict__ arp, const int* __restrict
     for (int p = arp[i]; p < arp[i + 1]; ++p) {
         const int k = acol[p];
         const double a = aval[p];
-        for (int q = brp[k] + lane; q < brp[k + 1]; q += 32)
+        for (int q = b_row_start(brp, bcol, k, col_lo) + lane; q < brp[k + 1]; q += 32)
             cval[bsearch_row(ccol, c0, c0 + u, bcol[q])] += a * bval[q];
         __syncwarp();
     }
@@ -329,7 +353,7 @@ constexpr int kLongCap = 1024;
 __global__ void __launch_bounds__(kLongWarps * 32)
 k_long_count(const int* __restrict__ arp, const int* __restrict__ acol,
              const int* __restrict__ brp, const int* __restrict__ bcol, int* __restrict__ count,
-             const int* __restrict__ rows, int* __restrict__ status) {
+             const int* __restrict__ rows, int* __restrict__ status, int upper) {
     extern __shared__ int keys[];
     __shared__ int part[kLongWarps];
     const int i = rows[blockIdx.x];
@@ -339,7 +363,8 @@ k_long_count(const int* __restrict__ arp, const int* __restrict__ acol,
     bool ok = true;
     for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
         const int k = acol[p];
-        for (int q = brp[k] + lane; q < brp[k + 1]; q += 32) ok &= hs_insert<kLongHT>(keys, bcol[q]);
+        for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32)
+            ok &= hs_insert<kLongHT>(keys, bcol[q]);
     }
     __syncthreads();
     int c = 0;
@@ -360,7 +385,7 @@ k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
                const double* __restrict__ aval, const int* __restrict__ brp,
                const int* __restrict__ bcol, const double* __restrict__ bval,
                const int* __restrict__ crp, int* __restrict__ ccol, double* __restrict__ cval,
-               const int* __restrict__ rows, int* __restrict__ wide) {
+               const int* __restrict__ rows, int* __restrict__ wide, int upper) {
     extern __shared__ int smem[];
     int* keys = smem;                                  // kLongHT
     int* list = keys + kLongHT;                        // kLongCap
@@ -380,7 +405,8 @@ k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
     __syncthreads();
     for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
         const int k = acol[p];
-        for (int q = brp[k] + lane; q < brp[k + 1]; q += 32) hs_insert<kLongHT>(keys, bcol[q]);
+        for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32)
+            hs_insert<kLongHT>(keys, bcol[q]);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < kLongHT; t += blockDim.x)  // compact (order irrelevant)
@@ -397,7 +423,7 @@ k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
     for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
         const int k = acol[p];
         const double a = aval[p];
-        for (int q = brp[k] + lane; q < brp[k + 1]; q += 32)
+        for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32)
             my[bsearch_row(sorted, 0, u, bcol[q])] += a * bval[q];
         __syncwarp();
     }
@@ -648,33 +674,33 @@ void set_smem(K kernel, size_t smem) {
 
 template <int HT>
 void count_tier(const CsrView& A, const CsrView& B, int* count, int* ovf, const int* rows,
-                int64_t n_work, int wpb, const int* is_long, cudaStream_t s) {
+                int64_t n_work, int wpb, const int* is_long, int upper, cudaStream_t s) {
     const size_t smem = (size_t)wpb * HT * sizeof(int);
     set_smem(k_spgemm_count<HT>, smem);
     k_spgemm_count<HT><<<grid_for(n_work, wpb), wpb * 32, smem, s>>>(
-        A.n_rows, A.rp, A.col, B.rp, B.col, count, ovf, rows, is_long);
+        A.n_rows, A.rp, A.col, B.rp, B.col, count, ovf, rows, is_long, upper);
     DPP_LAUNCH_CK();
 }
 
 template <int HT>
 void pattern_tier(const CsrView& A, const CsrView& B, Csr& C, const int* rows, int64_t n_work,
-                  int wpb, cudaStream_t s) {
+                  int wpb, int upper, cudaStream_t s) {
     const size_t smem = (size_t)wpb * 2 * HT * sizeof(int);
     set_smem(k_spgemm_pattern<HT>, smem);
     k_spgemm_pattern<HT><<<grid_for(n_work, wpb), wpb * 32, smem, s>>>(
-        A.n_rows, A.rp, A.col, B.rp, B.col, C.row_ptr.get(), C.col.get(), rows);
+        A.n_rows, A.rp, A.col, B.rp, B.col, C.row_ptr.get(), C.col.get(), rows, upper);
     DPP_LAUNCH_CK();
 }
 
 template <int CAP>
 void scatter_tier(const CsrView& A, const CsrView& B, Csr& C, int* wide, const int* is_long,
-                  cudaStream_t s) {
+                  int upper, cudaStream_t s) {
     constexpr int HT = 2 * CAP < 64 ? 64 : 2 * CAP;
     const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * CAP * sizeof(double);
     set_smem(k_spgemm_scatter<HT, CAP>, smem);
     k_spgemm_scatter<HT, CAP><<<grid_for(A.n_rows, kWarps), kWarps * 32, smem, s>>>(
         A.n_rows, A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(),
-        C.val.get(), wide, is_long);
+        C.val.get(), wide, is_long, upper);
     DPP_LAUNCH_CK();
 }
 
@@ -683,7 +709,8 @@ constexpr int kHtTiers[3] = {256, 2048, 8192};
 }  // namespace
 
 void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
-            HostScratch& hs) {
+            HostScratch& hs, bool upper_only) {
+    const int up = upper_only ? 1 : 0;
     ProfScope prof(values ? "spgemm_numeric" : "spgemm_pattern", s, 0);
     if (A.n_cols != B.n_rows) fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: shape mismatch");
     const int64_t n = A.n_rows;
@@ -715,16 +742,16 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     }
     {
         ProfScope pc("spgemm_count", s, 0);
-        count_tier<256>(A, B, C.row_ptr.get(), tier_rows[1] - 1, nullptr, n, kWarps, long_flag, s);
+        count_tier<256>(A, B, C.row_ptr.get(), tier_rows[1] - 1, nullptr, n, kWarps, long_flag, up, s);
         tier_n[1] = read_scalar(tier_rows[1] - 1, s, hs);
         if (tier_n[1] > 0) {
             count_tier<2048>(A, B, C.row_ptr.get(), tier_rows[2] - 1, tier_rows[1], tier_n[1], kWarps,
-                          long_flag, s);
+                             long_flag, up, s);
             tier_n[2] = read_scalar(tier_rows[2] - 1, s, hs);
         }
         if (tier_n[2] > 0) {
             count_tier<8192>(A, B, C.row_ptr.get(), last_ovf.get(), tier_rows[2], tier_n[2], 1,
-                          long_flag, s);
+                             long_flag, up, s);
             if (read_scalar(last_ovf.get(), s, hs) > 0)
                 fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
         }
@@ -734,7 +761,7 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
             const size_t smem = (size_t)kLongHT * sizeof(int);
             set_smem(k_long_count, smem);
             k_long_count<<<(unsigned)n_long, kLongWarps * 32, smem, s>>>(
-                A.rp, A.col, B.rp, B.col, C.row_ptr.get(), long_rows.get() + 1, st.get());
+                A.rp, A.col, B.rp, B.col, C.row_ptr.get(), long_rows.get() + 1, st.get(), up);
             DPP_LAUNCH_CK();
             if (read_scalar(st.get(), s, hs))
                 fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
@@ -748,9 +775,9 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     }
     ProfScope pf(values ? "spgemm_fill" : "spgemm_fill_pattern", s, 0);
     if (!values) {
-        pattern_tier<256>(A, B, C, nullptr, n, kWarps, s);  // rows that fit the first tier
-        if (tier_n[1] > 0) pattern_tier<2048>(A, B, C, tier_rows[1], tier_n[1], kWarps, s);
-        if (tier_n[2] > 0) pattern_tier<8192>(A, B, C, tier_rows[2], tier_n[2], 1, s);
+        pattern_tier<256>(A, B, C, nullptr, n, kWarps, up, s);  // rows that fit the first tier
+        if (tier_n[1] > 0) pattern_tier<2048>(A, B, C, tier_rows[1], tier_n[1], kWarps, up, s);
+        if (tier_n[2] > 0) pattern_tier<8192>(A, B, C, tier_rows[2], tier_n[2], 1, up, s);
         DPP_CK(cudaStreamSynchronize(s));
         return;
     }
@@ -768,16 +795,16 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
         set_smem(k_long_numeric, smem);
         k_long_numeric<<<(unsigned)n_long, kLongWarps * 32, smem, s>>>(
             A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(), C.val.get(),
-            long_rows.get() + 1, wide.get());
+            long_rows.get() + 1, wide.get(), up);
         DPP_LAUNCH_CK();
     }
     if (n_long < n) {
-        if (max_u <= 32) scatter_tier<32>(A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 64) scatter_tier<64>(A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 128) scatter_tier<128>(A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 256) scatter_tier<256>(A, B, C, wide.get(), long_flag, s);
-        else if (max_u <= 512) scatter_tier<512>(A, B, C, wide.get(), long_flag, s);
-        else scatter_tier<1024>(A, B, C, wide.get(), long_flag, s);
+        if (max_u <= 32) scatter_tier<32>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 64) scatter_tier<64>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 128) scatter_tier<128>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 256) scatter_tier<256>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 512) scatter_tier<512>(A, B, C, wide.get(), long_flag, up, s);
+        else scatter_tier<1024>(A, B, C, wide.get(), long_flag, up, s);
     }
     const int n_wide = read_scalar(wide.get(), s, hs);
     if (n_wide > 0) {
@@ -785,7 +812,7 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
         set_smem(k_spgemm_wide<8192>, smem);
         k_spgemm_wide<8192><<<n_wide, 32, smem, s>>>(A.rp, A.col, A.val, B.rp, B.col, B.val,
                                                      C.row_ptr.get(), C.col.get(), C.val.get(),
-                                                     wide.get() + 1, st.get());
+                                                     wide.get() + 1, st.get(), up);
         DPP_LAUNCH_CK();
         if (read_scalar(st.get(), s, hs))
             fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
@@ -820,6 +847,87 @@ void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs) {
                                                          T.val.get(), tc.get(), tv.get());
     DPP_LAUNCH_CK();
     DPP_CK(cudaStreamSynchronize(s));
+}
+
+namespace {
+// rows of C = U + strict_upper(U)^T: T = U^T (sorted rows, column <= row),
+// count[i] = |T row i without the diagonal| + |U row i|
+__global__ void k_sym_count(int64_t n, const int* __restrict__ urp, const int* __restrict__ trp,
+                            const int* __restrict__ tcol, int* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lt = trp[i + 1] - trp[i];
+    if (lt > 0 && tcol[trp[i + 1] - 1] == (int)i) --lt;  // the diagonal comes from U
+    count[i] = lt + (urp[i + 1] - urp[i]);
+}
+
+// one warp per row: the strictly lower part from T, then U's row (both sorted)
+__global__ void k_sym_fill(int64_t n, const int* __restrict__ urp, const int* __restrict__ ucol,
+                           const double* __restrict__ uval, const int* __restrict__ trp,
+                           const int* __restrict__ tcol, const double* __restrict__ tval,
+                           const int* __restrict__ crp, int* __restrict__ ccol,
+                           double* __restrict__ cval) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int c0 = crp[i];
+    const int nl = crp[i + 1] - c0 - (urp[i + 1] - urp[i]);
+    for (int e = lane; e < nl; e += 32) {
+        ccol[c0 + e] = tcol[trp[i] + e];
+        cval[c0 + e] = tval[trp[i] + e];
+    }
+    for (int e = lane; e < urp[i + 1] - urp[i]; e += 32) {
+        ccol[c0 + nl + e] = ucol[urp[i] + e];
+        cval[c0 + nl + e] = uval[urp[i] + e];
+    }
+}
+
+// one warp per row: flag entries whose mirror is missing or differs
+__global__ void k_sym_check(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, double tol, int* __restrict__ bad) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    bool ok = true;
+    for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+        const int j = col[p];
+        const int q = bsearch_row(col, rp[j], rp[j + 1], (int)i);
+        if (q < 0) { ok = false; continue; }
+        const double a = val[p], b = val[q];
+        if (!(fabs(a - b) <= tol * (fabs(a) + fabs(b)))) ok = false;
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(bad, 1);
+}
+}  // namespace
+
+void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs) {
+    Csr T;
+    transpose(U, T, s, hs);
+    const int64_t n = U.n_rows;
+    C.n_rows = C.n_cols = n;
+    C.row_ptr.alloc(n + 1);
+    DPP_CK(cudaMemsetAsync(C.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
+    k_sym_count<<<grid_for(n, 256), 256, 0, s>>>(n, U.row_ptr.get(), T.row_ptr.get(), T.col.get(),
+                                                 C.row_ptr.get());
+    DPP_LAUNCH_CK();
+    C.nnz = exclusive_scan(C.row_ptr.get(), C.row_ptr.get(), n + 1, s, hs);
+    C.col.alloc(std::max<int64_t>(C.nnz, 1));
+    C.val.alloc(std::max<int64_t>(C.nnz, 1));
+    k_sym_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(n, U.row_ptr.get(), U.col.get(), U.val.get(),
+                                                     T.row_ptr.get(), T.col.get(), T.val.get(),
+                                                     C.row_ptr.get(), C.col.get(), C.val.get());
+    DPP_LAUNCH_CK();
+    DPP_CK(cudaStreamSynchronize(s));
+}
+
+bool is_symmetric(const Csr& A, double tol, cudaStream_t s, HostScratch& hs) {
+    if (A.n_rows != A.n_cols) return false;
+    DBuf<int> bad(1);
+    DPP_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
+    k_sym_check<<<grid_for(A.n_rows * 32, 256), 256, 0, s>>>(A.n_rows, A.row_ptr.get(), A.col.get(),
+                                                             A.val.get(), tol, bad.get());
+    DPP_LAUNCH_CK();
+    return read_scalar(bad.get(), s, hs) == 0;
 }
 
 void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,

@@ -7,7 +7,11 @@ those nodes are needed. Against those rows:
     at full size, in the benchmark's launch configuration);
   * the GPU solution of each mode satisfies every sampled residual row to
     within the global bound ||f - K x||_2 <= 1e-10 ||f||_2. Any single entry
-    of the residual is bounded by its 2-norm.
+    of the residual is bounded by its 2-norm;
+  * the first Galerkin product, which at this size is computed as an upper
+    triangle and mirrored, matches P^T A P (scipy, from the exported level-0
+    matrix and prolongator) on sampled coarse rows to 1e-12 of the largest
+    entry, and is symmetric bit for bit.
 """
 import numpy as np
 import pytest
@@ -54,3 +58,21 @@ def test_fullsize_solution_rows(workload, precision):
     r = fr - Kr @ oracle.from_nodal(x.cpu().numpy())
     assert np.abs(r).max() <= 1e-10 * fnorm
     s.close()
+
+
+def test_fullsize_galerkin_rows(workload):
+    import scipy.sparse as sp
+    from gpu_helpers import csr_from_export
+    P = workload[0]
+    s = system_cls().from_problem(P).setup_pc()
+    sz, (rp, col, val), (prp, pcol, pval) = s.level(0)
+    A = csr_from_export(rp, col, val, (sz["rows"], sz["rows"]))
+    Pm = csr_from_export(prp, pcol, pval, (sz["rows"], sz["p_cols"]))
+    sz1, (rp1, col1, val1), _ = s.level(1, with_p=False)
+    Ac = csr_from_export(rp1, col1, val1, (sz1["rows"], sz1["rows"]))
+    s.close()
+    assert (Ac != Ac.T).nnz == 0
+    Icoarse = np.sort(inputs.rng(23).choice(sz1["rows"], size=50, replace=False))
+    ref = ((Pm[:, Icoarse].T.tocsr() @ A) @ Pm).toarray()
+    got = Ac[Icoarse].toarray()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()

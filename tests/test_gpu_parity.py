@@ -123,6 +123,8 @@ def test_galerkin_products_3d_are_exact_and_deterministic(DPPSystem):
     ref = (Pm.T @ A @ Pm).tocsr()
     ref.sort_indices()
     assert abs(Ac - ref).max() <= 1e-12 * abs(ref).max()
+    # S_p is symmetric, and so is the coarse operator (to rounding)
+    assert abs(Ac - Ac.T).max() <= 1e-13 * abs(Ac).max()
     for l in range(1, sz["levels"]):
         a = s1.level(l, with_p=False)[1]
         b = s2.level(l, with_p=False)[1]
