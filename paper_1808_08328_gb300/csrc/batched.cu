@@ -14,12 +14,16 @@
 // Reductions are segmented by a chunk table whose chunks never straddle two
 // instances: each block reduces one chunk, then one pass adds an instance's
 // chunk partials in chunk order. The result is deterministic. The small
-// per-instance algebra runs as one device thread per instance. A restart cycle
-// (m Arnoldi steps, the update of x, the FP64 true residual and the
-// convergence flags) has no host synchronisation, so it is captured once as a
-// CUDA graph and replayed; the host reads one counter (instances still active)
-// per cycle. An instance stops contributing once its residual estimate meets
-// its target; its later basis vectors are zero.
+// per-instance algebra runs as one device thread per instance, including the
+// test for a second Gram-Schmidt pass, which then runs only over that
+// instance's chunks. A restart cycle (m Arnoldi steps, the update of x, the
+// FP64 true residual and the convergence flags) needs no host
+// synchronisation; its Arnoldi steps are captured as CUDA graphs of a few
+// steps each, and the end of the cycle as one more. Between step graphs the
+// host reads one counter (instances still iterating) and ends the cycle when
+// it is zero; after a cycle it reads the number of instances still active.
+// An instance stops contributing once its residual estimate meets its target;
+// its later basis vectors are zero.
 #include <cmath>
 #include <cstring>
 
@@ -107,9 +111,10 @@ template <class VT>
 __global__ void __launch_bounds__(kSegThreads)
 k_seg_dots(const int64_t* __restrict__ beg, const int64_t* __restrict__ end, const VT* __restrict__ V,
            int64_t ld, int nvec, const double* __restrict__ w, double* __restrict__ partial,
-           int pld) {
+           int pld, const int* __restrict__ inst, const int* __restrict__ run) {
     __shared__ double sh[kSegThreads / 32];
     const int c = blockIdx.x;
+    if (run && !run[inst[c]]) return;  // this instance skips the pass (its partials are unused)
     const int64_t b0 = beg[c], b1 = end[c];
     for (int j = 0; j < nvec; ++j) {
         const VT* v = V + (int64_t)j * ld;
@@ -122,9 +127,11 @@ k_seg_dots(const int64_t* __restrict__ beg, const int64_t* __restrict__ end, con
 
 // out[b][j] = sum over b's chunks (in order) of partial[chunk][j]
 __global__ void k_seg_finish(int nb, const int* __restrict__ inst_ch, const double* __restrict__ partial,
-                             int pld, int nvec, double* __restrict__ out, int old) {
+                             int pld, int nvec, double* __restrict__ out, int old,
+                             const int* __restrict__ run) {
     const int b = blockIdx.x;
     if (b >= nb) return;
+    if (run && !run[b]) return;  // out keeps what k_batch_reorth_flags wrote
     for (int j = threadIdx.x; j < nvec; j += blockDim.x) {
         double s = 0.0;
         for (int c = inst_ch[b]; c < inst_ch[b + 1]; ++c) s += partial[(int64_t)c * pld + j];
@@ -137,10 +144,12 @@ template <class VT>
 __global__ void __launch_bounds__(kSegThreads)
 k_seg_axpy(const int* __restrict__ inst, const int64_t* __restrict__ beg,
            const int64_t* __restrict__ end, const VT* __restrict__ V, int64_t ld, int nvec,
-           const double* __restrict__ coef, int cld, double sign, double* __restrict__ w) {
+           const double* __restrict__ coef, int cld, double sign, double* __restrict__ w,
+           const int* __restrict__ run) {
     __shared__ double cs[64];
     const int c = blockIdx.x;
     const int b = inst[c];
+    if (run && !run[b]) return;
     if (threadIdx.x < nvec) cs[threadIdx.x] = sign * coef[(int64_t)b * cld + threadIdx.x];
     __syncthreads();
     for (int64_t i = beg[c] + threadIdx.x; i < end[c]; i += blockDim.x) {
@@ -164,6 +173,9 @@ k_seg_scale(const int* __restrict__ inst, const int64_t* __restrict__ beg,
 struct BatchDev {
     double *H, *cs, *sn, *g, *y, *hcol, *hcol2, *nrm2, *hn, *beta, *bnorm, *target, *relres;
     int *ncol, *active, *status, *iters, *n_active;
+    double* nrm0;  // ||w||^2 before the first Gram-Schmidt pass
+    int* reo;      // per instance: 1 = run the second Gram-Schmidt pass in this iteration
+    int* n_iter;   // instances still iterating after the last column (reset every iteration)
 };
 
 // Column j of every instance's Hessenberg matrix: rotations, residual estimate,
@@ -210,7 +222,20 @@ __global__ void k_batch_givens(int nb, int j, int m, BatchDev d) {
         d.hn[b] = 0.0;  // later basis vectors of this instance are zero
     } else {
         d.hn[b] = hn;
+        atomicAdd(d.n_iter, 1);
     }
+}
+
+// Second Gram-Schmidt pass needed? (DGKS test per instance, against the norm
+// before the first pass). hcol2 is zeroed for the instances that skip it.
+__global__ void k_batch_reorth_flags(int nb, int j, int pld, double eta2, BatchDev d) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const bool live = d.active[b] && d.ncol[b] > j;
+    const int r = (live && d.nrm2[b] < eta2 * d.nrm0[b]) ? 1 : 0;
+    d.reo[b] = r;
+    if (!r)
+        for (int i = 0; i <= j; ++i) d.hcol2[(int64_t)b * pld + i] = 0.0;
 }
 
 // y = H^-1 g over the instance's ncol columns (zero for instances that are done)
@@ -449,22 +474,29 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
     const int pld = m + 2;
     DBuf<double> V((size_t)(m + 1) * n), Z(mixed ? 1 : (size_t)m * n), w(n), r(n), partial((size_t)nch * pld);
     DBuf<float> Z32(mixed ? (size_t)m * n : 1);
+    // A cycle that ends early leaves later columns of Z from an earlier cycle
+    // (zero coefficients in x += Z y); they start at zero so that they are finite.
+    if (mixed) DPP_CK(cudaMemsetAsync(Z32.get(), 0, Z32.bytes(), s));
+    else DPP_CK(cudaMemsetAsync(Z.get(), 0, Z.bytes(), s));
     DBuf<double> H((size_t)nb * (m + 1) * m), cs((size_t)nb * m), sn((size_t)nb * m), g((size_t)nb * (m + 1)),
         y((size_t)nb * m), hcol((size_t)nb * pld), hcol2((size_t)nb * pld), nrm2(nb), hn(nb), beta(nb),
         bnorm(nb), target(nb), rel(nb);
-    DBuf<int> ncol(nb), active(nb), st(nb), it(nb), n_active(1);
+    DBuf<int> ncol(nb), active(nb), st(nb), it(nb), n_active(1), reo(nb), n_iter(1);
+    DBuf<double> nrm0(nb);
     BatchDev d{H.get(), cs.get(), sn.get(), g.get(), y.get(), hcol.get(), hcol2.get(), nrm2.get(),
                hn.get(), beta.get(), bnorm.get(), target.get(), rel.get(), ncol.get(), active.get(),
-               st.get(), it.get(), n_active.get()};
+               st.get(), it.get(), n_active.get(), nrm0.get(), reo.get(), n_iter.get()};
     const double* f = P.f.get();
-    auto seg_dot = [&](const double* Vv, int64_t ld, int nvec, const double* wv, double* out, int old) {
-        k_seg_dots<double><<<nch, kSegThreads, 0, s>>>(d_cb.get(), d_ce.get(), Vv, ld, nvec, wv, partial.get(), pld);
+    auto seg_dot = [&](const double* Vv, int64_t ld, int nvec, const double* wv, double* out, int old,
+                       const int* run) {
+        k_seg_dots<double><<<nch, kSegThreads, 0, s>>>(d_cb.get(), d_ce.get(), Vv, ld, nvec, wv,
+                                                       partial.get(), pld, d_ci.get(), run);
         DPP_LAUNCH_CK();
-        k_seg_finish<<<nb, 64, 0, s>>>(nb, d_ich.get(), partial.get(), pld, nvec, out, old);
+        k_seg_finish<<<nb, 64, 0, s>>>(nb, d_ich.get(), partial.get(), pld, nvec, out, old, run);
         DPP_LAUNCH_CK();
     };
     // ||f_b||, initial x, residual and flags
-    seg_dot(f, 0, 1, f, nrm2.get(), 1);
+    seg_dot(f, 0, 1, f, nrm2.get(), 1, nullptr);
     k_sqrt_copy<<<g1(nb), 128, 0, s>>>(nb, nrm2.get(), bnorm.get());
     DPP_LAUNCH_CK();
     if (o.x0_zero) DPP_CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
@@ -472,7 +504,7 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
     DPP_LAUNCH_CK();
     auto tail = [&]() {  // true residual, convergence test, v_0 of the next cycle
         apply_K(P, x, r.get(), f, false, false, s);
-        seg_dot(r.get(), 0, 1, r.get(), nrm2.get(), 1);
+        seg_dot(r.get(), 0, 1, r.get(), nrm2.get(), 1, nullptr);
         DPP_CK(cudaMemsetAsync(n_active.get(), 0, sizeof(int), s));
         k_batch_check<<<g1(nb), 128, 0, s>>>(nb, m, o.rtol, o.inner_rtol, mixed ? 1 : 0, o.max_iters, d);
         DPP_LAUNCH_CK();
@@ -480,76 +512,113 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
         DPP_LAUNCH_CK();
     };
     tail();
-    // one restart cycle, captured once and replayed
-    auto cycle = [&]() {
-        for (int j = 0; j < m; ++j) {
-            double* vj = V.get() + (size_t)j * n;
-            if (mixed) {
-                float* zj = Z32.get() + (size_t)j * n;
-                pc_apply32(P, pc, vj, zj, false, s);
-                apply_K32(P, zj, w.get(), false, s);
-            } else {
-                double* zj = Z.get() + (size_t)j * n;
-                pc_apply(P, pc, vj, zj, false, s);
-                apply_K(P, zj, w.get(), nullptr, false, false, s);
-            }
-            seg_dot(V.get(), n, j + 1, w.get(), hcol.get(), pld);
-            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1, hcol.get(), pld, -1.0, w.get());
-            DPP_LAUNCH_CK();
-            seg_dot(V.get(), n, j + 1, w.get(), hcol2.get(), pld);
-            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1, hcol2.get(), pld, -1.0, w.get());
-            DPP_LAUNCH_CK();
-            seg_dot(w.get(), 0, 1, w.get(), nrm2.get(), 1);
-            k_batch_givens<<<g1(nb), 128, 0, s>>>(nb, j, m, d);
-            DPP_LAUNCH_CK();
-            if (j + 1 < m) {
-                k_seg_scale<<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), w.get(), hn.get(),
-                                                        V.get() + (size_t)(j + 1) * n);
-                DPP_LAUNCH_CK();
-            }
+    const double eta = std::min(std::max(o.reorth_eta, 0.0), 1.0);
+    // Arnoldi step j for every instance: classical Gram-Schmidt, and a second
+    // pass for the instances whose first pass left less than eta of ||w||
+    auto iteration = [&](int j) {
+        double* vj = V.get() + (size_t)j * n;
+        if (mixed) {
+            float* zj = Z32.get() + (size_t)j * n;
+            pc_apply32(P, pc, vj, zj, false, s);
+            apply_K32(P, zj, w.get(), false, s);
+        } else {
+            double* zj = Z.get() + (size_t)j * n;
+            pc_apply(P, pc, vj, zj, false, s);
+            apply_K(P, zj, w.get(), nullptr, false, false, s);
         }
+        seg_dot(w.get(), 0, 1, w.get(), nrm0.get(), 1, nullptr);
+        seg_dot(V.get(), n, j + 1, w.get(), hcol.get(), pld, nullptr);
+        k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1,
+                                                       hcol.get(), pld, -1.0, w.get(), nullptr);
+        DPP_LAUNCH_CK();
+        seg_dot(w.get(), 0, 1, w.get(), nrm2.get(), 1, nullptr);
+        k_batch_reorth_flags<<<g1(nb), 128, 0, s>>>(nb, j, pld, eta * eta, d);
+        DPP_LAUNCH_CK();
+        seg_dot(V.get(), n, j + 1, w.get(), hcol2.get(), pld, reo.get());
+        k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1,
+                                                       hcol2.get(), pld, -1.0, w.get(), reo.get());
+        DPP_LAUNCH_CK();
+        seg_dot(w.get(), 0, 1, w.get(), nrm2.get(), 1, reo.get());
+        DPP_CK(cudaMemsetAsync(n_iter.get(), 0, sizeof(int), s));
+        k_batch_givens<<<g1(nb), 128, 0, s>>>(nb, j, m, d);
+        DPP_LAUNCH_CK();
+        if (j + 1 < m) {
+            k_seg_scale<<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), w.get(), hn.get(),
+                                                    V.get() + (size_t)(j + 1) * n);
+            DPP_LAUNCH_CK();
+        }
+    };
+    auto finish = [&]() {  // least squares, x += Z y, true residual and test
         k_batch_lsq<<<g1(nb), 128, 0, s>>>(nb, m, d);
         DPP_LAUNCH_CK();
         if (mixed)
-            k_seg_axpy<float><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z32.get(), n, m, y.get(), m, 1.0, x);
+            k_seg_axpy<float><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z32.get(), n, m,
+                                                          y.get(), m, 1.0, x, nullptr);
         else
-            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z.get(), n, m, y.get(), m, 1.0, x);
+            k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z.get(), n, m,
+                                                           y.get(), m, 1.0, x, nullptr);
         DPP_LAUNCH_CK();
         tail();
     };
+    // A restart cycle runs as chunks of kChunkIters Arnoldi steps, each chunk
+    // captured once as a CUDA graph. After a chunk the host reads how many
+    // instances are still iterating and ends the cycle early when none is;
+    // the end of the cycle is one more graph.
+    constexpr int kChunkIters = 5;
+    const int n_chunks = (m + kChunkIters - 1) / kChunkIters;
+    struct Graph {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        size_t nodes = 0;
+    };
+    std::vector<Graph> graphs(n_chunks + 1);
+    auto destroy_graphs = [&]() {
+        for (auto& gr : graphs) {
+            if (gr.e) cudaGraphExecDestroy(gr.e);
+            if (gr.g) cudaGraphDestroy(gr.g);
+            gr.e = nullptr;
+            gr.g = nullptr;
+        }
+    };
+    auto capture = [&](Graph& gr, auto&& body) {
+        DPP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        try {
+            body();
+        } catch (...) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(s, &tmp);
+            if (tmp) cudaGraphDestroy(tmp);
+            throw;
+        }
+        DPP_CK(cudaStreamEndCapture(s, &gr.g));
+        DPP_CK(cudaGraphInstantiate(&gr.e, gr.g, 0));
+        DPP_CK(cudaGraphGetNodes(gr.g, nullptr, &gr.nodes));
+    };
     int active_now = read_scalar(n_active.get(), s, hs);
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    size_t graph_kernels = 0;
     const int max_cycles = (o.max_iters + m - 1) / m + 1;
     try {
         if (active_now > 0) {
-            DPP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            try {
-                cycle();
-            } catch (...) {
-                cudaStreamEndCapture(s, &graph);
-                if (graph) cudaGraphDestroy(graph);
-                throw;
-            }
-            DPP_CK(cudaStreamEndCapture(s, &graph));
-            DPP_CK(cudaGraphInstantiate(&exec, graph, 0));
-            size_t nn = 0;
-            DPP_CK(cudaGraphGetNodes(graph, nullptr, &nn));
-            graph_kernels = nn;
+            for (int k = 0; k < n_chunks; ++k)
+                capture(graphs[k], [&]() {
+                    for (int j = k * kChunkIters; j < std::min(m, (k + 1) * kChunkIters); ++j) iteration(j);
+                });
+            capture(graphs[n_chunks], finish);
         }
         for (int cyc = 0; cyc < max_cycles && active_now > 0; ++cyc) {
-            DPP_CK(cudaGraphLaunch(exec, s));
-            graph_launches += (int64_t)graph_kernels;
+            for (int k = 0; k < n_chunks; ++k) {
+                DPP_CK(cudaGraphLaunch(graphs[k].e, s));
+                graph_launches += (int64_t)graphs[k].nodes;
+                if (k + 1 < n_chunks && read_scalar(n_iter.get(), s, hs) == 0) break;
+            }
+            DPP_CK(cudaGraphLaunch(graphs[n_chunks].e, s));
+            graph_launches += (int64_t)graphs[n_chunks].nodes;
             active_now = read_scalar(n_active.get(), s, hs);
         }
     } catch (...) {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
+        destroy_graphs();
         throw;
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
+    destroy_graphs();
     status.resize(nb);
     iters.resize(nb);
     relres.resize(nb);
