@@ -448,27 +448,60 @@ __global__ void k_csr_to_dense(int64_t n, const int* __restrict__ rp, const int*
 }
 
 // Gauss-Jordan step k, part 1 (one block): scale pivot row, save and clear column k.
-__global__ void k_gj_pivot(int n, int k, double* __restrict__ M, double* __restrict__ f) {
+// Gauss-Jordan on the diagonal block [b0, b0 + nb) of the row-major n x n
+// matrix M (pivot k of the block; part 1: scale row k, keep column k in f)
+__global__ void k_gj_pivot(int n, int b0, int nb, int k, double* __restrict__ M, double* __restrict__ f) {
     __shared__ double piv;
-    if (threadIdx.x == 0) piv = M[(int64_t)k * n + k];
+    const int kk = b0 + k;
+    if (threadIdx.x == 0) piv = M[(int64_t)kk * n + kk];
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(int64_t)i * n + k];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(int64_t)(b0 + i) * n + kk];
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double v = (j == k) ? 1.0 : M[(int64_t)k * n + j];
-        M[(int64_t)k * n + j] = v / piv;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const double v = (j == k) ? 1.0 : M[(int64_t)kk * n + b0 + j];
+        M[(int64_t)kk * n + b0 + j] = v / piv;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        if (i != k) M[(int64_t)i * n + k] = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (i != k) M[(int64_t)(b0 + i) * n + kk] = 0.0;
 }
 
-// part 2: row_i -= f_i * row_k for every i != k
-__global__ void k_gj_elim(int n, int k, double* __restrict__ M, const double* __restrict__ f) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * n) return;
-    int i = (int)(t / n), j = (int)(t % n);
+// part 2: row_i -= f_i * row_k for every i != k of the block
+__global__ void k_gj_elim(int n, int b0, int nb, int k, double* __restrict__ M, const double* __restrict__ f) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nb * nb) return;
+    const int i = (int)(t / nb), j = (int)(t % nb);
     if (i == k) return;
-    M[t] -= f[i] * M[(int64_t)k * n + j];
+    M[(int64_t)(b0 + i) * n + b0 + j] -= f[i] * M[(int64_t)(b0 + k) * n + b0 + j];
+}
+
+// Gauss-Jordan of many small diagonal blocks at once: one CTA per block of at
+// most kGjSmall rows, the block held in shared memory. blk[2c], blk[2c+1] =
+// first row and size of block c.
+constexpr int kGjSmall = 96;
+constexpr size_t kGjSmem = (size_t)(kGjSmall * kGjSmall + kGjSmall) * sizeof(double);  // dynamic
+__global__ void __launch_bounds__(256) k_gj_blocks(int n, const int* __restrict__ blk, double* __restrict__ M) {
+    extern __shared__ double gj_smem[];
+    double* a = gj_smem;                    // [nb][nb]
+    double* f = gj_smem + kGjSmall * kGjSmall;
+    const int b0 = blk[2 * blockIdx.x], nb = blk[2 * blockIdx.x + 1];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
+        a[t] = M[(int64_t)(b0 + t / nb) * n + b0 + t % nb];
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        const double piv = a[k * nb + k];
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) f[i] = (i == k) ? 0.0 : a[i * nb + k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) a[k * nb + j] = ((j == k) ? 1.0 : a[k * nb + j]) / piv;
+        __syncthreads();
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+            const int i = t / nb, j = t % nb;
+            if (i == k) continue;
+            a[t] = ((j == k) ? 0.0 : a[t]) - f[i] * a[k * nb + j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
+        M[(int64_t)(b0 + t / nb) * n + b0 + t % nb] = a[t];
 }
 
 // x = Minv b, one warp per row; Minv and the accumulation stay FP64 in both modes
@@ -516,19 +549,65 @@ double power_lmax(const Csr& A, const double* dinv, int lanes, cudaStream_t s, H
     return std::sqrt(l2);
 }
 
-void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s) {
+// Inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting) as a
+// dense row-major matrix. The matrix is split into its contiguous diagonal
+// blocks (a union of instances, or the two S_p blocks, coarsens into such
+// blocks), found from the sparsity pattern: block boundaries are where no row
+// above reaches below and no row below reaches above. Blocks of at most
+// kGjSmall rows are inverted one CTA each in shared memory, in one launch;
+// larger blocks pivot by pivot.
+void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s, HostScratch& hs) {
     const int64_t n = A.n_rows;
     inv.alloc(n * n);
     DPP_CK(cudaMemsetAsync(inv.get(), 0, n * n * sizeof(double), s));
     k_csr_to_dense<<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
                                                     inv.get());
     DPP_LAUNCH_CK();
+    // pattern to the host (n <= 4096 rows)
+    std::vector<int> rp(n + 1), col(A.nnz);
+    DPP_CK(cudaMemcpyAsync(rp.data(), A.row_ptr.get(), (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaMemcpyAsync(col.data(), A.col.get(), A.nnz * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaStreamSynchronize(s));
+    std::vector<int> lo(n), hi(n);
+    for (int64_t i = 0; i < n; ++i) {
+        lo[i] = (int)i;
+        hi[i] = (int)i;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            lo[i] = std::min(lo[i], col[p]);
+            hi[i] = std::max(hi[i], col[p]);
+        }
+    }
+    std::vector<int> suffix_lo(n + 1, INT32_MAX);
+    for (int64_t i = n - 1; i >= 0; --i) suffix_lo[i] = std::min(suffix_lo[i + 1], lo[i]);
+    std::vector<int> small, big;  // (first row, size) pairs
+    int start = 0, reach = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        reach = std::max(reach, hi[i]);
+        if (reach <= i && suffix_lo[i + 1] > i) {  // boundary after row i
+            const int sz = (int)i + 1 - start;
+            auto& lst = (sz <= kGjSmall) ? small : big;
+            lst.push_back(start);
+            lst.push_back(sz);
+            start = (int)i + 1;
+        }
+    }
+    if (!small.empty()) {
+        DBuf<int> d_blk(small.size());
+        DPP_CK(cudaMemcpyAsync(d_blk.get(), small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaFuncSetAttribute(k_gj_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem));
+        k_gj_blocks<<<(unsigned)(small.size() / 2), 256, kGjSmem, s>>>((int)n, d_blk.get(), inv.get());
+        DPP_LAUNCH_CK();
+        DPP_CK(cudaStreamSynchronize(s));  // d_blk's host source goes out of scope
+    }
     DBuf<double> f(n);
-    for (int k = 0; k < n; ++k) {
-        k_gj_pivot<<<1, 256, 0, s>>>((int)n, k, inv.get(), f.get());
-        DPP_LAUNCH_CK();
-        k_gj_elim<<<grid_for(n * n, 256), 256, 0, s>>>((int)n, k, inv.get(), f.get());
-        DPP_LAUNCH_CK();
+    for (size_t c = 0; c < big.size(); c += 2) {
+        const int b0 = big[c], nb = big[c + 1];
+        for (int k = 0; k < nb; ++k) {
+            k_gj_pivot<<<1, 256, 0, s>>>((int)n, b0, nb, k, inv.get(), f.get());
+            DPP_LAUNCH_CK();
+            k_gj_elim<<<grid_for((int64_t)nb * nb, 256), 256, 0, s>>>((int)n, b0, nb, k, inv.get(), f.get());
+            DPP_LAUNCH_CK();
+        }
     }
     DPP_CK(cudaStreamSynchronize(s));
 }
@@ -681,7 +760,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
                                        "raise max_levels or lower strength_theta");
     pc.coarse_n = C.A.n_rows;
     ProfScope pr("setup_coarse_inverse", s, 0);
-    dense_inverse(C.A, pc.coarse_inv, s);
+    dense_inverse(C.A, pc.coarse_inv, s, hs);
 }
 
 namespace {

@@ -91,17 +91,44 @@ __global__ void k_offset_ids(int* __restrict__ ids, int64_t n, int per,
     if (i < n * per) ids[i] += (int)off[owner[i / per]];
 }
 
-__global__ void k_fill_owner(int* __restrict__ owner, int64_t begin, int64_t end, int value) {
-    int64_t i = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < end) owner[i] = value;
+// instance owning union element e: the last i with off[i] <= e (off[0] = 0)
+__device__ __forceinline__ int owner_of(const int64_t* __restrict__ off, int nl, int64_t e) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-__global__ void k_fill_mub(double* __restrict__ mub, int64_t begin, int64_t end, double mu,
-                           double beta) {
-    int64_t c = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < end) {
-        mub[2 * c] = mu;
-        mub[2 * c + 1] = beta;
+// Union gather of one input array: element e (comp values each) comes from
+// instance i = owner_of(e) at src[i][(e - off[i]) * comp ...]. Instances with
+// src[i] == nullptr were copied from host memory by the caller. owner[e] = i
+// when owner != nullptr.
+template <class T>
+__global__ void k_union_gather(int nl, const int64_t* __restrict__ off, int comp,
+                               const T* const* __restrict__ src, T* __restrict__ dst,
+                               int* __restrict__ owner) {
+    const int64_t total = off[nl];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int i = owner_of(off, nl, e);
+        if (owner) owner[e] = i;
+        const T* sp = src[i];
+        if (!sp) continue;
+        const int64_t k = e - off[i];
+        for (int c = 0; c < comp; ++c) dst[e * comp + c] = sp[k * comp + c];
+    }
+}
+
+__global__ void k_fill_mub(int64_t n_cells, const int* __restrict__ cell_inst,
+                           const double* __restrict__ mu, const double* __restrict__ beta,
+                           double* __restrict__ mub) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n_cells) {
+        mub[2 * c] = mu[cell_inst[c]];
+        mub[2 * c + 1] = beta[cell_inst[c]];
     }
 }
 
@@ -371,27 +398,65 @@ void assemble_union(ProblemImpl& P, int n, const dpp_problem_desc* descs, std::v
         DBuf<int64_t> d_nnodes(nl), d_noff(nl);
         DPP_CK(cudaMemcpyAsync(d_nnodes.get(), nnodes.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         DPP_CK(cudaMemcpyAsync(d_noff.get(), noff.data(), nl * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        // Host-memory instances are copied one by one; device-memory instances
+        // are gathered by one kernel per array through a table of their
+        // pointers, which also writes the owner of every node, cell and facet.
+        std::vector<const void*> tab(7 * (size_t)nl, nullptr);  // [array][instance]
+        std::vector<double> mu_b(2 * (size_t)nl);
         for (int i = 0; i < nl; ++i) {
             const auto& d = descs[live[i]];
-            const bool host = d.memory == DPP_MEM_HOST;
-            upload_at(P.coords.get() + noff[i] * dim, d.coords, (size_t)d.n_nodes * dim, host, s);
-            upload_at(P.cells.get() + coff[i] * nv, d.cells, (size_t)d.n_cells * nv, host, s);
-            upload_at(P.bfacets.get() + foff[i] * dim, d.bfacets, (size_t)d.n_bfacets * dim, host, s);
-            upload_at(P.logk1.get() + coff[i], d.log_k1, (size_t)d.n_cells, host, s);
-            upload_at(P.logk2.get() + coff[i], d.log_k2, (size_t)d.n_cells, host, s);
-            upload_at(P.p01.get() + noff[i], d.p01, (size_t)d.n_nodes, host, s);
-            upload_at(P.p02.get() + noff[i], d.p02, (size_t)d.n_nodes, host, s);
-            k_fill_owner<<<grid_for(d.n_cells, 256), 256, 0, s>>>(cell_inst.get(), coff[i], coff[i + 1], i);
-            DPP_LAUNCH_CK();
-            k_fill_owner<<<grid_for(d.n_nodes, 256), 256, 0, s>>>(node_inst.get(), noff[i], noff[i + 1], i);
-            DPP_LAUNCH_CK();
-            if (d.n_bfacets) {
-                k_fill_owner<<<grid_for(d.n_bfacets, 256), 256, 0, s>>>(facet_inst.get(), foff[i], foff[i + 1], i);
-                DPP_LAUNCH_CK();
+            mu_b[i] = d.mu;
+            mu_b[nl + i] = d.beta;
+            if (d.memory == DPP_MEM_HOST) {
+                upload_at(P.coords.get() + noff[i] * dim, d.coords, (size_t)d.n_nodes * dim, true, s);
+                upload_at(P.cells.get() + coff[i] * nv, d.cells, (size_t)d.n_cells * nv, true, s);
+                upload_at(P.bfacets.get() + foff[i] * dim, d.bfacets, (size_t)d.n_bfacets * dim, true, s);
+                upload_at(P.logk1.get() + coff[i], d.log_k1, (size_t)d.n_cells, true, s);
+                upload_at(P.logk2.get() + coff[i], d.log_k2, (size_t)d.n_cells, true, s);
+                upload_at(P.p01.get() + noff[i], d.p01, (size_t)d.n_nodes, true, s);
+                upload_at(P.p02.get() + noff[i], d.p02, (size_t)d.n_nodes, true, s);
+            } else {
+                const void* ptrs[7] = {d.coords, d.cells, d.n_bfacets ? d.bfacets : nullptr, d.log_k1,
+                                       d.log_k2, d.p01, d.p02};
+                for (int a = 0; a < 7; ++a) tab[(size_t)a * nl + i] = ptrs[a];
             }
-            k_fill_mub<<<grid_for(d.n_cells, 256), 256, 0, s>>>(P.cell_mu_beta.get(), coff[i], coff[i + 1], d.mu, d.beta);
+        }
+        DBuf<int64_t> d_off(3 * ((size_t)nl + 1));  // node, cell, facet offsets
+        DBuf<const void*> d_tab(tab.size());
+        DBuf<double> d_mub(mu_b.size());
+        DPP_CK(cudaMemcpyAsync(d_off.get(), noff.data(), (nl + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemcpyAsync(d_off.get() + (nl + 1), coff.data(), (nl + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemcpyAsync(d_off.get() + 2 * (nl + 1), foff.data(), (nl + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemcpyAsync(d_tab.get(), tab.data(), tab.size() * sizeof(void*), cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemcpyAsync(d_mub.get(), mu_b.data(), mu_b.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+        const int64_t* o_node = d_off.get();
+        const int64_t* o_cell = d_off.get() + (nl + 1);
+        const int64_t* o_facet = d_off.get() + 2 * (nl + 1);
+        auto dtab = [&](int a) { return reinterpret_cast<const double* const*>(d_tab.get() + (size_t)a * nl); };
+        auto itab = [&](int a) { return reinterpret_cast<const int* const*>(d_tab.get() + (size_t)a * nl); };
+        const int gb = 8 * kSMs;
+        k_union_gather<double><<<gb, 256, 0, s>>>(nl, o_node, dim, dtab(0), P.coords.get(), node_inst.get());
+        DPP_LAUNCH_CK();
+        k_union_gather<int><<<gb, 256, 0, s>>>(nl, o_cell, nv, itab(1), P.cells.get(), cell_inst.get());
+        DPP_LAUNCH_CK();
+        if (P.n_bfacets) {
+            k_union_gather<int><<<gb, 256, 0, s>>>(nl, o_facet, dim, itab(2), P.bfacets.get(), facet_inst.get());
             DPP_LAUNCH_CK();
         }
+        k_union_gather<double><<<gb, 256, 0, s>>>(nl, o_cell, 1, dtab(3), P.logk1.get(), nullptr);
+        DPP_LAUNCH_CK();
+        k_union_gather<double><<<gb, 256, 0, s>>>(nl, o_cell, 1, dtab(4), P.logk2.get(), nullptr);
+        DPP_LAUNCH_CK();
+        k_union_gather<double><<<gb, 256, 0, s>>>(nl, o_node, 1, dtab(5), P.p01.get(), nullptr);
+        DPP_LAUNCH_CK();
+        k_union_gather<double><<<gb, 256, 0, s>>>(nl, o_node, 1, dtab(6), P.p02.get(), nullptr);
+        DPP_LAUNCH_CK();
+        k_fill_mub<<<grid_for(P.n_cells, 256), 256, 0, s>>>(P.n_cells, cell_inst.get(), d_mub.get(),
+                                                            d_mub.get() + nl, P.cell_mu_beta.get());
+        DPP_LAUNCH_CK();
         // per-instance validation before the ids are shifted
         DBuf<int> flags(nl);
         DPP_CK(cudaMemsetAsync(flags.get(), 0, nl * sizeof(int), s));
