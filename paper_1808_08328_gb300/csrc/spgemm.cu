@@ -307,6 +307,85 @@ __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
     for (int e = lane; e < u; e += 32) cval[c0 + e] = acc[e];
 }
 
+// One-pass product for rows of at most CAP distinct columns: the warp
+// collects, ranks and accumulates its row exactly as k_spgemm_scatter does,
+// but writes it to a fixed-capacity staging row (tcol/tval + i * CAP) and
+// records its length, so no separate counting pass is needed. Rows that do
+// not fit get uone[i] = -1 and are listed in ovf (ovf[0] = count) for the
+// counting tiers and k_spgemm_wide.
+template <int HT, int CAP>
+__global__ void k_spgemm_onepass(int64_t n_rows, const int* __restrict__ arp,
+                                 const int* __restrict__ acol, const double* __restrict__ aval,
+                                 const int* __restrict__ brp, const int* __restrict__ bcol,
+                                 const double* __restrict__ bval, int* __restrict__ count,
+                                 int* __restrict__ uone, int* __restrict__ tcol,
+                                 double* __restrict__ tval, int* __restrict__ ovf, int upper) {
+    static_assert(HT == 2 * CAP, "the compacted key list lives in the CAP accumulators");
+    extern __shared__ int smem[];
+    constexpr int WPB = 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * WPB + warp;
+    if (w >= n_rows) return;
+    const int i = (int)w;
+    int* keys = smem + warp * 2 * HT;
+    int* slot = keys + HT;
+    double* acc = reinterpret_cast<double*>(smem + WPB * 2 * HT) + (size_t)warp * CAP;
+    const int col_lo = upper ? i : INT_MIN;
+    const bool ok = warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, col_lo);
+    int* list = reinterpret_cast<int*>(acc);  // HT ints
+    const int u = ok ? warp_compact<HT>(keys, list, lane) : HT + 1;
+    if (u > CAP) {
+        if (lane == 0) {
+            count[i] = 0;
+            uone[i] = -1;
+            ovf[atomicAdd(&ovf[0], 1) + 1] = i;
+        }
+        return;
+    }
+    int* orow = tcol + (int64_t)i * CAP;
+    warp_rank<HT>(list, u, lane, orow, keys, slot);
+    for (int e = lane; e < u; e += 32) acc[e] = 0.0;
+    __syncwarp();
+    for_each_product<true>(i, arp, acol, aval, brp, bcol, col_lo, lane, [&](bool act, int q, double a) {
+        int sl = -1 - lane;
+        double v = 0.0;
+        if (act) {
+            v = a * bval[q];
+            sl = slot[hs_find<HT>(keys, bcol[q])];
+        }
+        const unsigned peers = __match_any_sync(kFull, sl);
+        const int order = __popc(peers & ((1u << lane) - 1u));
+        const int n_sub = (int)__reduce_max_sync(kFull, (unsigned)__popc(peers));
+        for (int r = 0; r < n_sub; ++r) {
+            if (act && order == r) acc[sl] += v;
+            __syncwarp();
+        }
+    });
+    double* vrow = tval + (int64_t)i * CAP;
+    for (int e = lane; e < u; e += 32) vrow[e] = acc[e];
+    if (lane == 0) {
+        count[i] = u;
+        uone[i] = u;
+    }
+}
+
+// staged rows into C (one warp per row; rows with uone < 0 are done elsewhere)
+template <int CAP>
+__global__ void k_onepass_compact(int64_t n_rows, const int* __restrict__ uone,
+                                  const int* __restrict__ crp, const int* __restrict__ tcol,
+                                  const double* __restrict__ tval, int* __restrict__ ccol,
+                                  double* __restrict__ cval) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n_rows) return;
+    const int u = uone[i];
+    const int c0 = crp[i];
+    for (int e = lane; e < u; e += 32) {
+        ccol[c0 + e] = tcol[i * CAP + e];
+        cval[c0 + e] = tval[i * CAP + e];
+    }
+}
+
 // Numeric pass for wide rows: one warp per listed row, accumulating in C.
 template <int HT>
 __global__ void k_spgemm_wide(const int* __restrict__ arp, const int* __restrict__ acol,
@@ -708,12 +787,82 @@ constexpr int kHtTiers[3] = {256, 2048, 8192};
 
 }  // namespace
 
+namespace {
+// Numeric product in one pass for rows of at most kOneCap columns (see
+// k_spgemm_onepass); returns false when the staging rows would not fit the
+// memory budget, and the caller takes the counting path.
+constexpr int kOneCap = 128;
+
+bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStream_t s,
+                    HostScratch& hs) {
+    const int64_t n = A.n_rows;
+    const int64_t stage = n * (int64_t)kOneCap;
+    if (stage * (int64_t)(sizeof(int) + sizeof(double)) > (int64_t(4) << 30)) return false;
+    C.n_rows = n;
+    C.n_cols = B.n_cols;
+    C.row_ptr.alloc(n + 1);
+    DPP_CK(cudaMemsetAsync(C.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
+    DBuf<int> tcol(stage), uone(n), ovf(n + 2), ovf2(n + 2), last(2);
+    DBuf<double> tval(stage);
+    DPP_CK(cudaMemsetAsync(ovf.get(), 0, sizeof(int), s));
+    DPP_CK(cudaMemsetAsync(ovf2.get(), 0, sizeof(int), s));
+    DPP_CK(cudaMemsetAsync(last.get(), 0, sizeof(int), s));
+    {
+        ProfScope pf("spgemm_fill", s, 0);
+        constexpr int HT = 2 * kOneCap;
+        const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * kOneCap * sizeof(double);
+        set_smem(k_spgemm_onepass<HT, kOneCap>, smem);
+        k_spgemm_onepass<HT, kOneCap><<<grid_for(n, kWarps), kWarps * 32, smem, s>>>(
+            n, A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), uone.get(), tcol.get(),
+            tval.get(), ovf.get(), up);
+        DPP_LAUNCH_CK();
+    }
+    const int64_t n_ovf = read_scalar(ovf.get(), s, hs);
+    if (n_ovf > 0) {  // wider rows: counted in the larger tiers
+        ProfScope pc("spgemm_count", s, 0);
+        count_tier<2048>(A, B, C.row_ptr.get(), ovf2.get(), ovf.get() + 1, n_ovf, kWarps, nullptr, up, s);
+        const int64_t n_ovf2 = read_scalar(ovf2.get(), s, hs);
+        if (n_ovf2 > 0) {
+            count_tier<8192>(A, B, C.row_ptr.get(), last.get(), ovf2.get() + 1, n_ovf2, 1, nullptr, up, s);
+            if (read_scalar(last.get(), s, hs) > 0)
+                fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
+        }
+    }
+    C.nnz = exclusive_scan(C.row_ptr.get(), C.row_ptr.get(), n + 1, s, hs);
+    {
+        ProfScope pa("spgemm_alloc", s, 0);
+        C.col.alloc(std::max<int64_t>(C.nnz, 1));
+        C.val.alloc(std::max<int64_t>(C.nnz, 1));
+    }
+    ProfScope pf("spgemm_fill", s, 0);
+    k_onepass_compact<kOneCap><<<grid_for(n * 32, 256), 256, 0, s>>>(n, uone.get(), C.row_ptr.get(), tcol.get(),
+                                                                    tval.get(), C.col.get(), C.val.get());
+    DPP_LAUNCH_CK();
+    if (n_ovf > 0) {
+        DBuf<int> st(1);
+        DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
+        const size_t smem = (size_t)2 * 8192 * sizeof(int);
+        set_smem(k_spgemm_wide<8192>, smem);
+        k_spgemm_wide<8192><<<(unsigned)n_ovf, 32, smem, s>>>(A.rp, A.col, A.val, B.rp, B.col, B.val,
+                                                              C.row_ptr.get(), C.col.get(), C.val.get(),
+                                                              ovf.get() + 1, st.get(), up);
+        DPP_LAUNCH_CK();
+        if (read_scalar(st.get(), s, hs))
+            fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
+    }
+    DPP_CK(cudaStreamSynchronize(s));
+    return true;
+}
+}  // namespace
+
 void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
             HostScratch& hs, bool upper_only) {
     const int up = upper_only ? 1 : 0;
     ProfScope prof(values ? "spgemm_numeric" : "spgemm_pattern", s, 0);
     if (A.n_cols != B.n_rows) fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: shape mismatch");
     const int64_t n = A.n_rows;
+    // many rows: one numeric pass, counting only the rows that overflow it
+    if (values && n >= 16384 && spgemm_onepass(A, B, C, up, s, hs)) return;
     C.n_rows = n;
     C.n_cols = B.n_cols;
     C.row_ptr.alloc(n + 1);
