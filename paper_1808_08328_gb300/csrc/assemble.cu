@@ -226,14 +226,18 @@ __global__ void k_cell_geometry(const double* __restrict__ X, const int* __restr
     kk[2 * c] = k1;
     kk[2 * c + 1] = k2;
     const double muc = mub ? mub[2 * c] : mu, bc = mub ? mub[2 * c + 1] : beta;
+    // per-cell factors of the pair values, with the P1 mass integral
+    // (phi_a; phi_b)_K = vol / ((d+1)(d+2)) (times 2 for a = b, applied per
+    // pair) folded in, so the pair loop adds them without multiplying
     double* cf = coef + c * kCellCoef;
-    cf[0] = vol / (DIM + 1);
-    cf[1] = vol / ((DIM + 1) * (DIM + 2));
-    cf[2] = 0.5 * muc / k1;
-    cf[3] = 0.5 * muc / k2;
-    cf[4] = 0.5 * k1 / muc * vol;
+    const double mass = vol / ((DIM + 1) * (DIM + 2));
+    cf[0] = vol / (DIM + 1);           // (grad phi_a; phi_b)_K = g_a vol / (d+1)
+    cf[1] = mass * (0.5 * muc / k1);   // 1/2 mu/k1 (phi_a; phi_b)
+    cf[2] = mass * (0.5 * muc / k2);
+    cf[3] = mass * (bc / muc);         // beta/mu (phi_a; phi_b)
+    cf[4] = 0.5 * k1 / muc * vol;      // 1/2 k1/mu |K|, times g_a.g_b
     cf[5] = 0.5 * k2 / muc * vol;
-    cf[6] = bc / muc;
+    cf[6] = 0.0;
     cf[7] = 0.0;
 }
 
@@ -254,9 +258,11 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
     const int a = pair_row[p], b = col[p];
     const int j = (int)(p - row_ptr[a]);
     const double self = (a == b) ? 2.0 : 1.0;
-    double m1 = 0, m2 = 0, d1 = 0, d2 = 0, bm = 0, bu[DIM], cu[DIM];
+    // sums over the cells of the pair: mass factors, d terms and the
+    // gradient moments sa = sum vol/(d+1) g_a, sb = sum vol/(d+1) g_b
+    double m1 = 0, m2 = 0, d1 = 0, d2 = 0, bm = 0, sa[DIM], sb[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) bu[k] = cu[k] = 0;
+    for (int k = 0; k < DIM; ++k) sa[k] = sb[k] = 0;
     for (int q = nc_ptr[a]; q < nc_ptr[a + 1]; ++q) {
         const int c = nc_list[q];
         int la = -1, lb = -1;
@@ -277,20 +283,28 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
         const double* ga = g + 1 + la * DIM;
         const double* gb = g + 1 + lb * DIM;
         const double* cf = coef + (int64_t)c * kCellCoef;
-        const double mab = cf[1] * self;           // (phi_a; phi_b)_K
         double dot = 0;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) dot += ga[k] * gb[k];
-        m1 += cf[2] * mab;                          // 1/2 mu/k1 (phi_a; phi_b)
-        m2 += cf[3] * mab;
-        d1 += cf[4] * dot;                          // 1/2 k1/mu |K| g_a.g_b
+        m1 += cf[1];
+        m2 += cf[2];
+        bm += cf[3];
+        d1 += cf[4] * dot;
         d2 += cf[5] * dot;
-        bm += cf[6] * mab;                          // beta/mu (phi_a; phi_b)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            bu[k] -= cf[0] * (ga[k] + 0.5 * gb[k]);  // cf[0] = |K|/(d+1)
-            cu[k] += cf[0] * (gb[k] + 0.5 * ga[k]);
+            sa[k] += cf[0] * ga[k];
+            sb[k] += cf[0] * gb[k];
         }
+    }
+    m1 *= self;
+    m2 *= self;
+    bm *= self;
+    double bu[DIM], cu[DIM];  // B: -(sum vol/(d+1) (g_a + g_b/2)), C: sum vol/(d+1) (g_b + g_a/2)
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        bu[k] = -(sa[k] + 0.5 * sb[k]);
+        cu[k] = sb[k] + 0.5 * sa[k];
     }
     const int64_t grp = (int64_t)slice_ptr[a >> 5] + j;
     double* o = sell_val + grp * NV * kSell + (a & 31);
