@@ -99,7 +99,11 @@ __device__ __forceinline__ void store_node(float* __restrict__ y, int64_t a, con
 }
 
 // y = K x (or b - K x). Arithmetic in FP32 when both values and x are FP32.
-template <int DIM, class VT, class XT, class YT, bool TRANS, bool RESID>
+// H warps share a slice (H = 1 or 2): warp h takes the column groups
+// g0 + h, g0 + h + H, ..., and warp 1's partial sums are added to warp 0's
+// through shared memory (fixed order). H = 2 doubles the loads in flight when
+// one thread per node row leaves most of the GPU idle.
+template <int DIM, class VT, class XT, class YT, bool TRANS, bool RESID, int H>
 __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slices,
                                                  const int* __restrict__ slice_ptr,
                                                  const int* __restrict__ sell_col,
@@ -111,15 +115,18 @@ __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slice
                                          float, double>::type;
     constexpr int NS = 2 * DIM + 2;
     constexpr int NV = pair_values(DIM);
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t s = a >> 5;
-    if (s >= n_slices) return;
-    const int lane = (int)(a & 31);
-    const int g0 = slice_ptr[s], g1 = slice_ptr[s + 1];
+    constexpr int SPB = 4 / H;  // slices per 128-thread block
+    static_assert(H == 1 || H == 2, "one or two warps per slice");
+    __shared__ AT part[H > 1 ? SPB : 1][NS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = warp % H;
+    const int64_t s = (int64_t)blockIdx.x * SPB + warp / H;
+    const bool live = s < n_slices;
+    const int64_t a = s * 32 + lane;
     AT acc[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) acc[k] = AT(0);
-    for (int g = g0; g < g1; ++g) {
+    const int g0 = live ? slice_ptr[s] + h : 0, g1 = live ? slice_ptr[s + 1] : 0;
+    for (int g = g0; g < g1; g += H) {
         const int cb = sell_col[(int64_t)g * kSell + lane];
         if (cb < 0) continue;
         const VT* v = val + (int64_t)g * NV * kSell + lane;
@@ -148,7 +155,16 @@ __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slice
         acc[DIM] += cp1;
         acc[2 * DIM + 1] += cp2;
     }
-    if (a >= n_rows) return;
+    if (H > 1) {
+        if (h == 1)
+#pragma unroll
+            for (int k = 0; k < NS; ++k) part[warp / H][k][lane] = acc[k];
+        __syncthreads();
+        if (h == 1) return;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc[k] += part[warp / H][k][lane];
+    }
+    if (!live || a >= n_rows) return;
     if (RESID) {
         double out[NS], bb[NS];
         load_node_as<NS, YT>(b, a, bb);
@@ -163,7 +179,7 @@ __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slice
 // Chebyshev step on A = blockdiag(K1_uu, K2_uu); each velocity component of
 // network i sees the same scalar matrix with entries m_i. T: vector and
 // arithmetic type; the values have the same type.
-template <int DIM, class T>
+template <int DIM, class T, int H>
 __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_slices,
                                                    const int* __restrict__ slice_ptr,
                                                    const int* __restrict__ sell_col,
@@ -175,16 +191,19 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
                                                    T c1, T c2, int first) {
     constexpr int NS = 2 * DIM + 2;
     constexpr int NV = pair_values(DIM);
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t s = a >> 5;
-    if (s >= n_slices) return;
-    const int lane = (int)(a & 31);
+    constexpr int SPB = 4 / H;  // slices per 128-thread block (H warps per slice, as in k_apply_K)
+    static_assert(H == 1 || H == 2, "one or two warps per slice");
+    __shared__ T part[H > 1 ? SPB : 1][NS][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = warp % H;
+    const int64_t s = (int64_t)blockIdx.x * SPB + warp / H;
+    const bool live = s < n_slices;
+    const int64_t a = s * 32 + lane;
     T acc[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) acc[k] = T(0);
-    if (!first) {
-        const int g0 = slice_ptr[s], g1 = slice_ptr[s + 1];
-        for (int g = g0; g < g1; ++g) {
+    if (!first && live) {
+        const int g0 = slice_ptr[s] + h, g1 = slice_ptr[s + 1];
+        for (int g = g0; g < g1; g += H) {
             const int cb = sell_col[(int64_t)g * kSell + lane];
             if (cb < 0) continue;
             const T* v = val + (int64_t)g * NV * kSell + lane;
@@ -198,7 +217,16 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
             }
         }
     }
-    if (a >= n_rows) return;
+    if (H > 1) {
+        if (h == 1)
+#pragma unroll
+            for (int k = 0; k < NS; ++k) part[warp / H][k][lane] = acc[k];
+        __syncthreads();
+        if (h == 1) return;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) acc[k] += part[warp / H][k][lane];
+    }
+    if (!live || a >= n_rows) return;
     T rr[NS], dd[NS], xx[NS];
     load_node<NS>(r, a, rr);
     const T i1 = mdiag[2 * a], i2 = mdiag[2 * a + 1];
@@ -340,12 +368,15 @@ void apply_K_dim(const ProblemImpl& P, const XT* x, YT* y, const YT* b, bool tr,
                        vecn * (double)(sizeof(XT) + sizeof(YT) + (b ? sizeof(YT) : 0));
     ProfScope prof(sizeof(VT) == 8 ? "apply_K" : "apply_K_fp32", s, alg);
     const int B = 128;
-    const int grid = grid_for(P.n_slices * kSell, B);
+    // two warps per slice in FP32 (HBM-bound, latency-limited at one thread per
+    // row); one in FP64, where the FP64 pipe is the limit
+    constexpr int H = (sizeof(VT) == 4) ? 2 : 1;
+    const int grid = grid_for(P.n_slices, 4 / H);
     const VT* val = vals_of<VT>(P);
 #define DPP_LAUNCH_APPLY(TR, RS)                                                          \
-    k_apply_K<DIM, VT, XT, YT, TR, RS><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices,          \
-                                                          P.slice_ptr.get(),              \
-                                                          P.sell_col.get(), val, x, b, y)
+    k_apply_K<DIM, VT, XT, YT, TR, RS, H><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices,       \
+                                                             P.slice_ptr.get(),           \
+                                                             P.sell_col.get(), val, x, b, y)
     if (tr) {
         if (b) DPP_LAUNCH_APPLY(true, true);
         else DPP_LAUNCH_APPLY(true, false);
@@ -387,16 +418,19 @@ void mass_cheb_step(const ProblemImpl& P, const T* mdiag, const T* r, const T* x
     const double alg = first ? 3 * vecb : (double)P.n_pairs * (2.0 * sizeof(T) + 4.0) + 5 * vecb;
     ProfScope prof(sizeof(T) == 8 ? "mass_cheb" : "mass_cheb_fp32", s, alg);
     const int B = 128;
-    const int grid = grid_for(P.n_slices * kSell, B);
+    // two warps per slice in FP64 (see k_apply_K); in FP32 the per-row epilogue
+    // outweighs the short pair loop, and one warp per slice measured faster
+    constexpr int H = (sizeof(T) == 8) ? 2 : 1;
+    const int grid = grid_for(P.n_slices, 4 / H);
     const T* val = vals_of<T>(P);
     if (P.dim == 2)
-        k_mass_cheb<2, T><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
-                                             P.sell_col.get(), val, mdiag, r, xin, xout, d, (T)c1,
-                                             (T)c2, first ? 1 : 0);
+        k_mass_cheb<2, T, H><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                                P.sell_col.get(), val, mdiag, r, xin, xout, d, (T)c1,
+                                                (T)c2, first ? 1 : 0);
     else
-        k_mass_cheb<3, T><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
-                                             P.sell_col.get(), val, mdiag, r, xin, xout, d, (T)c1,
-                                             (T)c2, first ? 1 : 0);
+        k_mass_cheb<3, T, H><<<grid, B, 0, s>>>(P.n_nodes, P.n_slices, P.slice_ptr.get(),
+                                                P.sell_col.get(), val, mdiag, r, xin, xout, d, (T)c1,
+                                                (T)c2, first ? 1 : 0);
     DPP_LAUNCH_CK();
 }
 
