@@ -113,40 +113,57 @@ def cpu_baseline_block(out, spec):
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 100 ms, stamped on arrival.
+
+    The sampler starts before the warm-up and waits for its first sample, so
+    that the monitoring tool's own start-up is over before anything is timed;
+    summary(t0, t1) keeps the samples taken inside the timed window.
+    """
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, uuid: str | None):
+        import threading
         self.proc = None
-        self.path = None
+        self.lines = []
         try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                   "-lms", "200"]
+                   "-lms", "100"]
             if uuid:
                 cmd += ["-i", uuid]
-            self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
         except Exception:
             self.proc = None
+            return
 
-    def stop(self) -> dict | None:
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append((time.time(), line))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        t_end = time.time() + 10.0
+        while not self.lines and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.05)
+
+    def stop(self) -> None:
         if not self.proc:
-            return None
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.fh.close()
+        time.sleep(0.5)  # let the monitoring process exit before any further timing
+
+    def summary(self, t0: float, t1: float) -> dict | None:
         rows = []
-        for line in open(self.path):
+        for t, line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
+            if t0 <= t <= t1 + 0.1 and len(parts) >= 9:
                 rows.append(parts)
-        os.unlink(self.path)
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -252,6 +269,12 @@ def bench_gb300(args):
         B.dpp_destroy_problem(prob)
         return info
 
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)  # started (and settled) before anything is timed
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize(dev)
@@ -278,13 +301,6 @@ def bench_gb300(args):
     B.dpp_profile_enable(False)
     dom = max(fam, key=lambda f: fam[f]["ms"])
 
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
-    clocks = ClockSampler(uuid)
-    time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -294,12 +310,14 @@ def bench_gb300(args):
     l0 = B.dpp_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_begin = time.time()
     e0.record(torch.cuda.current_stream(dev))
     infos = []
     for _ in range(args.steps):
         infos.append(step())
     e1.record(torch.cuda.current_stream(dev))
     torch.cuda.synchronize(dev)
+    t_end = time.time()
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
@@ -307,7 +325,8 @@ def bench_gb300(args):
     dom_live = B.dpp_profile_read(dom)
     B.dpp_profile_enable(False)
     B.dpp_profile_select(None)
-    clk = clocks.stop()
+    clocks.stop()
+    clk = clocks.summary(t_begin, t_end)
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -643,16 +643,16 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
                                                 L.dinv.get(), dabs.get(), st.get());
         DPP_LAUNCH_CK();
         check_dev(st, s, hs, "a level matrix has a non-positive diagonal entry");
-        {
-            ProfScope pr("setup_power", s, 0);
-            L.lmax = power_lmax(L.A, L.dinv.get(), L.lanes, s, hs);
-        }
         L.x.alloc(n);
         L.b.alloc(n);
         L.r.alloc(n);
         L.d.alloc(n);
         const bool last = (n <= o.coarse_max_rows) || (l + 1 >= o.max_levels);
-        if (last) break;
+        if (last) break;  // the coarsest level is solved directly: no smoother, no lambda_max
+        {
+            ProfScope pr("setup_power", s, 0);
+            L.lmax = power_lmax(L.A, L.dinv.get(), L.lanes, s, hs);
+        }
 
         // strength graph
         ProfScope pr_agg("setup_aggregate", s, 0);
@@ -691,7 +691,9 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
             k_mis_update<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get(), t2.get(),
                                                       undecided.get());
             DPP_LAUNCH_CK();
-            if (read_scalar(undecided.get(), s, hs) == 0) break;
+            // the count is read every other round (a round after the last
+            // decision changes nothing), which halves the host round trips
+            if ((round & 1) && read_scalar(undecided.get(), s, hs) == 0) break;
             if (round == 63) fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: MIS-2 did not finish");
         }
         pr_mis.stop();
