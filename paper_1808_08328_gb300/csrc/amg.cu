@@ -17,9 +17,11 @@
 //   3. tentative prolongator P0 = aggregate indicator; smoothed prolongator
 //      P = (I - omega D^-1 A) P0 with omega = 4 / (3 lambda_max(D^-1 A));
 //   4. Galerkin coarse matrix A_c = P^T (A P).
-// lambda_max comes from 12 power iterations on D^-1 A. The coarsest matrix is
-// inverted densely (Gauss-Jordan without pivoting, valid for SPD) and applied
-// as a dense matrix-vector product.
+// lambda_max comes from 12 power iterations on D^-1 A. Coarsening stops at
+// coarse_max_rows rows, or earlier when a level consists of small diagonal
+// blocks only (a batched union of instances). The coarsest matrix is inverted
+// block by block (its contiguous diagonal blocks, Gauss-Jordan without
+// pivoting, valid for SPD) and applied as block matrix-vector products.
 //
 // Smoother: Chebyshev polynomial in D^-1 A on [lambda_max / ratio,
 // 1.1 lambda_max] (Adams, Brezina, Hu & Tuminaro, J. Comput. Phys. 188,
@@ -439,15 +441,7 @@ __global__ void k_smooth_p(int64_t n, const int* __restrict__ rp, const int* __r
     for (int p = rp[i]; p < rp[i + 1]; ++p) val[p] = (col[p] == agg[i] ? 1.0 : 0.0) - w * val[p];
 }
 
-// ------------------------------------------------------------------ coarse dense inverse
-__global__ void k_csr_to_dense(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
-                               const double* __restrict__ val, double* __restrict__ M) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int p = rp[i]; p < rp[i + 1]; ++p) M[i * n + col[p]] = val[p];
-}
-
-// Gauss-Jordan step k, part 1 (one block): scale pivot row, save and clear column k.
+// ------------------------------------------------------------------ coarse block inverse
 // Gauss-Jordan on the diagonal block [b0, b0 + nb) of the row-major n x n
 // matrix M (pivot k of the block; part 1: scale row k, keep column k in f)
 __global__ void k_gj_pivot(int n, int b0, int nb, int k, double* __restrict__ M, double* __restrict__ f) {
@@ -474,18 +468,49 @@ __global__ void k_gj_elim(int n, int b0, int nb, int k, double* __restrict__ M, 
     M[(int64_t)(b0 + i) * n + b0 + j] -= f[i] * M[(int64_t)(b0 + k) * n + b0 + j];
 }
 
-// Gauss-Jordan of many small diagonal blocks at once: one CTA per block of at
-// most kGjSmall rows, the block held in shared memory. blk[2c], blk[2c+1] =
-// first row and size of block c.
+// The coarsest matrix is inverted block by block: its contiguous diagonal
+// blocks (one per instance and network in a batched union, the two S_p blocks
+// of a single problem) are stored compactly, row-major, block c at coff[c].
+// blk[3c .. 3c+2] = first row, size, offset of block c; rowblk[i] = block of row i.
+
+// row extents: lo[i] / hi[i] = smallest / largest column of row i (and i itself)
+__global__ void k_row_extents(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                              int* __restrict__ lo, int* __restrict__ hi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = (int)i, b = (int)i;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        a = min(a, col[p]);
+        b = max(b, col[p]);
+    }
+    lo[i] = a;
+    hi[i] = b;
+}
+
+__global__ void k_csr_to_blocks(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ val, const int* __restrict__ blk,
+                                const int* __restrict__ rowblk, double* __restrict__ inv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = rowblk[i];
+    const int b0 = blk[3 * c], nb = blk[3 * c + 1], off = blk[3 * c + 2];
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        inv[(int64_t)off + (int64_t)(i - b0) * nb + (col[p] - b0)] = val[p];
+}
+
+// Gauss-Jordan of many small blocks at once: one CTA per listed block (list
+// entries are block ids), the block held in shared memory.
 constexpr int kGjSmall = 96;
 constexpr size_t kGjSmem = (size_t)(kGjSmall * kGjSmall + kGjSmall) * sizeof(double);  // dynamic
-__global__ void __launch_bounds__(256) k_gj_blocks(int n, const int* __restrict__ blk, double* __restrict__ M) {
+__global__ void __launch_bounds__(256) k_gj_blocks(const int* __restrict__ list, const int* __restrict__ blk,
+                                                   double* __restrict__ inv) {
     extern __shared__ double gj_smem[];
     double* a = gj_smem;                    // [nb][nb]
     double* f = gj_smem + kGjSmall * kGjSmall;
-    const int b0 = blk[2 * blockIdx.x], nb = blk[2 * blockIdx.x + 1];
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
-        a[t] = M[(int64_t)(b0 + t / nb) * n + b0 + t % nb];
+    const int c = list[blockIdx.x];
+    const int nb = blk[3 * c + 1];
+    double* M = inv + blk[3 * c + 2];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) a[t] = M[t];
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
         const double piv = a[k * nb + k];
@@ -500,19 +525,22 @@ __global__ void __launch_bounds__(256) k_gj_blocks(int n, const int* __restrict_
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x)
-        M[(int64_t)(b0 + t / nb) * n + b0 + t % nb] = a[t];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) M[t] = a[t];
 }
 
-// x = Minv b, one warp per row; Minv and the accumulation stay FP64 in both modes
+// x = Minv b for the block-diagonal inverse: one warp per row; the inverse and
+// the accumulation stay FP64 in both modes
 template <class T>
-__global__ void k_dense_mv(int n, const double* __restrict__ M, const T* __restrict__ b,
-                           T* __restrict__ x) {
-    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+__global__ void k_block_mv(int64_t n, const double* __restrict__ inv, const int* __restrict__ blk,
+                           const int* __restrict__ rowblk, const T* __restrict__ b, T* __restrict__ x) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (row >= n) return;
+    const int c = rowblk[row];
+    const int b0 = blk[3 * c], nb = blk[3 * c + 1];
+    const double* M = inv + blk[3 * c + 2] + (int64_t)(row - b0) * nb;
     double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += M[row * n + j] * (double)b[j];
+    for (int j = lane; j < nb; j += 32) acc += M[j] * (double)b[b0 + j];
     acc = warp_sum(acc);
     if (lane == 0) x[row] = (T)acc;
 }
@@ -549,67 +577,83 @@ double power_lmax(const Csr& A, const double* dinv, int lanes, cudaStream_t s, H
     return std::sqrt(l2);
 }
 
-// Inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting) as a
-// dense row-major matrix. The matrix is split into its contiguous diagonal
-// blocks (a union of instances, or the two S_p blocks, coarsens into such
-// blocks), found from the sparsity pattern: block boundaries are where no row
-// above reaches below and no row below reaches above. Blocks of at most
-// kGjSmall rows are inverted one CTA each in shared memory, in one launch;
-// larger blocks pivot by pivot.
-void dense_inverse(const Csr& A, DBuf<double>& inv, cudaStream_t s, HostScratch& hs) {
+// Contiguous diagonal blocks of A from its row extents: a boundary falls after
+// row i when no row up to i reaches beyond i and no row after i reaches back
+// to i or before. Returns (first row, size) pairs.
+std::vector<std::pair<int, int>> diag_blocks(const Csr& A, cudaStream_t s) {
     const int64_t n = A.n_rows;
-    inv.alloc(n * n);
-    DPP_CK(cudaMemsetAsync(inv.get(), 0, n * n * sizeof(double), s));
-    k_csr_to_dense<<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
-                                                    inv.get());
+    DBuf<int> d_lo(n), d_hi(n);
+    k_row_extents<<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), d_lo.get(), d_hi.get());
     DPP_LAUNCH_CK();
-    // pattern to the host (n <= 4096 rows)
-    std::vector<int> rp(n + 1), col(A.nnz);
-    DPP_CK(cudaMemcpyAsync(rp.data(), A.row_ptr.get(), (n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
-    DPP_CK(cudaMemcpyAsync(col.data(), A.col.get(), A.nnz * sizeof(int), cudaMemcpyDeviceToHost, s));
-    DPP_CK(cudaStreamSynchronize(s));
     std::vector<int> lo(n), hi(n);
-    for (int64_t i = 0; i < n; ++i) {
-        lo[i] = (int)i;
-        hi[i] = (int)i;
-        for (int p = rp[i]; p < rp[i + 1]; ++p) {
-            lo[i] = std::min(lo[i], col[p]);
-            hi[i] = std::max(hi[i], col[p]);
-        }
-    }
+    DPP_CK(cudaMemcpyAsync(lo.data(), d_lo.get(), n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaMemcpyAsync(hi.data(), d_hi.get(), n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    DPP_CK(cudaStreamSynchronize(s));
     std::vector<int> suffix_lo(n + 1, INT32_MAX);
     for (int64_t i = n - 1; i >= 0; --i) suffix_lo[i] = std::min(suffix_lo[i + 1], lo[i]);
-    std::vector<int> small, big;  // (first row, size) pairs
+    std::vector<std::pair<int, int>> blocks;
     int start = 0, reach = -1;
     for (int64_t i = 0; i < n; ++i) {
         reach = std::max(reach, hi[i]);
-        if (reach <= i && suffix_lo[i + 1] > i) {  // boundary after row i
-            const int sz = (int)i + 1 - start;
-            auto& lst = (sz <= kGjSmall) ? small : big;
-            lst.push_back(start);
-            lst.push_back(sz);
+        if (reach <= i && suffix_lo[i + 1] > i) {
+            blocks.emplace_back(start, (int)i + 1 - start);
             start = (int)i + 1;
         }
     }
+    return blocks;
+}
+
+// Inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), block
+// by block in compact storage. Blocks of at most kGjSmall rows are inverted
+// one CTA each in shared memory, in one launch; larger ones pivot by pivot.
+void block_inverse(PcImpl& pc, const Csr& A, cudaStream_t s) {
+    const int64_t n = A.n_rows;
+    const auto blocks = diag_blocks(A, s);
+    std::vector<int> blk(3 * blocks.size()), rowblk(n), small;
+    int64_t off = 0;
+    for (size_t c = 0; c < blocks.size(); ++c) {
+        const int b0 = blocks[c].first, nb = blocks[c].second;
+        if (nb > 4096) fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: a coarsest diagonal block has more than "
+                                                      "4096 rows; raise max_levels or lower strength_theta");
+        blk[3 * c] = b0;
+        blk[3 * c + 1] = nb;
+        blk[3 * c + 2] = (int)off;
+        for (int r = 0; r < nb; ++r) rowblk[b0 + r] = (int)c;
+        if (nb <= kGjSmall) small.push_back((int)c);
+        off += (int64_t)nb * nb;
+        if (off >= INT32_MAX) fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: coarsest blocks too large");
+    }
+    pc.coarse_blk.alloc(blk.size());
+    pc.coarse_rowblk.alloc(n);
+    pc.coarse_inv.alloc(std::max<int64_t>(off, 1));
+    DPP_CK(cudaMemcpyAsync(pc.coarse_blk.get(), blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    DPP_CK(cudaMemcpyAsync(pc.coarse_rowblk.get(), rowblk.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    DPP_CK(cudaMemsetAsync(pc.coarse_inv.get(), 0, off * sizeof(double), s));
+    k_csr_to_blocks<<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
+                                                     pc.coarse_blk.get(), pc.coarse_rowblk.get(),
+                                                     pc.coarse_inv.get());
+    DPP_LAUNCH_CK();
     if (!small.empty()) {
-        DBuf<int> d_blk(small.size());
-        DPP_CK(cudaMemcpyAsync(d_blk.get(), small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        DBuf<int> d_small(small.size());
+        DPP_CK(cudaMemcpyAsync(d_small.get(), small.data(), small.size() * sizeof(int), cudaMemcpyHostToDevice, s));
         DPP_CK(cudaFuncSetAttribute(k_gj_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGjSmem));
-        k_gj_blocks<<<(unsigned)(small.size() / 2), 256, kGjSmem, s>>>((int)n, d_blk.get(), inv.get());
+        k_gj_blocks<<<(unsigned)small.size(), 256, kGjSmem, s>>>(d_small.get(), pc.coarse_blk.get(),
+                                                                 pc.coarse_inv.get());
         DPP_LAUNCH_CK();
-        DPP_CK(cudaStreamSynchronize(s));  // d_blk's host source goes out of scope
     }
     DBuf<double> f(n);
-    for (size_t c = 0; c < big.size(); c += 2) {
-        const int b0 = big[c], nb = big[c + 1];
+    for (size_t c = 0; c < blocks.size(); ++c) {
+        const int nb = blocks[c].second;
+        if (nb <= kGjSmall) continue;
+        double* M = pc.coarse_inv.get() + blk[3 * c + 2];
         for (int k = 0; k < nb; ++k) {
-            k_gj_pivot<<<1, 256, 0, s>>>((int)n, b0, nb, k, inv.get(), f.get());
+            k_gj_pivot<<<1, 256, 0, s>>>(nb, 0, nb, k, M, f.get());
             DPP_LAUNCH_CK();
-            k_gj_elim<<<grid_for((int64_t)nb * nb, 256), 256, 0, s>>>((int)n, b0, nb, k, inv.get(), f.get());
+            k_gj_elim<<<grid_for((int64_t)nb * nb, 256), 256, 0, s>>>(nb, 0, nb, k, M, f.get());
             DPP_LAUNCH_CK();
         }
     }
-    DPP_CK(cudaStreamSynchronize(s));
+    DPP_CK(cudaStreamSynchronize(s));  // host tables go out of scope
 }
 
 }  // namespace
@@ -626,6 +670,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
     // Galerkin products of a symmetric A (S_p is, up to rounding in its
     // assembly) may be computed as an upper triangle and mirrored
     constexpr int64_t kMirrorMinRows = 16384;
+    constexpr int64_t kBlockCoarseRows = 65536;
     const bool symmetric = is_symmetric(pc.levels[0].A, 1e-10, s, hs);
     pc.symmetric = symmetric;
     for (int l = 0;; ++l) {
@@ -647,7 +692,14 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         L.b.alloc(n);
         L.r.alloc(n);
         L.d.alloc(n);
-        const bool last = (n <= o.coarse_max_rows) || (l + 1 >= o.max_levels);
+        bool last = (n <= o.coarse_max_rows) || (l + 1 >= o.max_levels);
+        if (!last && n <= kBlockCoarseRows) {
+            // a level made of small diagonal blocks only (a batched union that
+            // has coarsened to a few rows per instance) is solved directly
+            int max_block = 0;
+            for (const auto& bl : diag_blocks(L.A, s)) max_block = std::max(max_block, bl.second);
+            last = max_block <= kGjSmall;
+        }
         if (last) break;  // the coarsest level is solved directly: no smoother, no lambda_max
         {
             ProfScope pr("setup_power", s, 0);
@@ -757,12 +809,9 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
     }
     // coarse solve
     Level& C = pc.levels.back();
-    if (C.A.n_rows > 4096)
-        fail(DPP_ERR_INVALID_ARGUMENT, "AMG setup: coarsest level has more than 4096 rows; "
-                                       "raise max_levels or lower strength_theta");
     pc.coarse_n = C.A.n_rows;
     ProfScope pr("setup_coarse_inverse", s, 0);
-    dense_inverse(C.A, pc.coarse_inv, s, hs);
+    block_inverse(pc, C.A, s);
 }
 
 namespace {
@@ -805,8 +854,9 @@ template <class T>
 void vcycle_level(PcImpl& pc, size_t l, const T* b, T* x, cudaStream_t s) {
     Level& L = pc.levels[l];
     if (l + 1 == pc.levels.size()) {
-        const int n = (int)pc.coarse_n;
-        k_dense_mv<T><<<grid_for((int64_t)n * 32, 256), 256, 0, s>>>(n, pc.coarse_inv.get(), b, x);
+        const int64_t n = pc.coarse_n;
+        k_block_mv<T><<<grid_for(n * 32, 256), 256, 0, s>>>(n, pc.coarse_inv.get(), pc.coarse_blk.get(),
+                                                            pc.coarse_rowblk.get(), b, x);
         DPP_LAUNCH_CK();
         return;
     }

@@ -89,8 +89,9 @@ struct PcImpl {
     dpp_pc_opts opts{};
     double mass_lmin = 0.5, mass_lmax = 2.0;  // Wathen bounds of D^-1 M (TRI: [1/2, 2], TET: [1/2, 5/2])
     std::vector<Level> levels;
-    DBuf<double> coarse_inv;  // dense inverse of the coarsest matrix, row-major
-    DBuf<float> coarse_inv32;
+    DBuf<double> coarse_inv;  // inverse of the coarsest matrix: its diagonal blocks, row-major
+    DBuf<int> coarse_blk;     // per block: first row, size, offset into coarse_inv
+    DBuf<int> coarse_rowblk;  // block of each coarsest row
     int64_t coarse_n = 0;
     bool symmetric = false;   // level-0 matrix found symmetric: Galerkin products mirrored
     // preconditioner work vectors (node-interleaved, n_nodes * ns)
