@@ -82,39 +82,55 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
 // the warp is one contiguous 128 B (int, float) or 256 B (double) transaction.
 // U partial sums keep U gathers in flight: 4 in FP64 (the FP64 pipe is the
 // other limit there), 8 in FP32. Same MODEs as k_csr_spmv.
-template <int MODE, class T>
+//
+// H warps may share a slice (H = 2 in FP32): warp h takes the slots
+// h, h + H, ... of every row, and the partial sums meet in shared memory.
+template <int MODE, class T, int H>
 __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __restrict__ off,
                                                    const int* __restrict__ col,
                                                    const T* __restrict__ val,
                                                    const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y) {
     constexpr int U = sizeof(T) == 4 ? 8 : 4;
-    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= n_rows) return;
-    const int64_t sl = row >> 5;
-    const int lane = (int)(row & 31);
-    const int e = off[sl + 1];
-    int p = off[sl] + lane;
+    constexpr int SPB = 8 / H;  // slices per 256-thread block
+    static_assert(H == 1 || H == 2, "one or two warps per slice");
+    __shared__ T part[H > 1 ? SPB : 1][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = warp % H;
+    const int64_t sl = (int64_t)blockIdx.x * SPB + warp / H;
+    const int64_t row = sl * 32 + lane;
+    const bool live = row < n_rows;
     T a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) a[u] = T(0);
-    for (; p + 32 * (U - 1) < e; p += 32 * U) {
-        int c[U];
-        T v[U];
+    if (live) {
+        const int e = off[sl + 1];
+        int p = off[sl] + 32 * h + lane;
+        constexpr int S = 32 * H;  // stride between this warp's slots
+        for (; p + S * (U - 1) < e; p += S * U) {
+            int c[U];
+            T v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            c[u] = col[p + 32 * u];
-            v[u] = val[p + 32 * u];
+            for (int u = 0; u < U; ++u) {
+                c[u] = col[p + S * u];
+                v[u] = val[p + S * u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] += v[u] * __ldg(x + c[u]);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] += v[u] * __ldg(x + c[u]);
+        for (; p < e; p += S) a[0] += val[p] * __ldg(x + col[p]);
     }
-    for (; p < e; p += 32) a[0] += val[p] * __ldg(x + col[p]);
 #pragma unroll
     for (int w = U / 2; w > 0; w >>= 1)
 #pragma unroll
         for (int u = 0; u < w; ++u) a[u] += a[u + w];
-    const T acc = a[0];
+    T acc = a[0];
+    if (H > 1) {
+        if (h == 1) part[warp / H][lane] = acc;
+        __syncthreads();
+        if (h == 1) return;
+        acc += part[warp / H][lane];
+    }
+    if (!live) return;
     if (MODE == 0) y[row] = acc;
     else if (MODE == 1) y[row] = b[row] - acc;
     else y[row] += acc;
@@ -142,9 +158,12 @@ __global__ void k_sell_fill(int64_t n_rows, const int* __restrict__ rp, const in
     const int lane = (int)(row & 31);
     const int r0 = rp[row], len = rp[row + 1] - r0;
     const int width = (off[sl + 1] - off[sl]) / 32;
+    // padding: (the row's last column, 0.0), a valid column also for a
+    // rectangular matrix (P), already loaded for this row
+    const int pad = (len > 0) ? col[r0 + len - 1] : 0;
     for (int k = 0; k < width; ++k) {
         const int64_t q = (int64_t)off[sl] + (int64_t)k * 32 + lane;
-        scol[q] = (k < len) ? col[r0 + k] : (int)row;
+        scol[q] = (k < len) ? col[r0 + k] : pad;
         sval[q] = (k < len) ? val[r0 + k] : T(0);
     }
 }
@@ -167,8 +186,12 @@ void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStrea
     if (sell) {
         const T* sv = (sizeof(T) == 8) ? reinterpret_cast<const T*>(A.sell_val.get())
                                        : reinterpret_cast<const T*>(A.sell_val32.get());
-        k_sell_spmv<MODE, T><<<grid_for(A.n_rows, B), B, 0, s>>>(A.n_rows, A.sell_off.get(),
-                                                                 A.sell_col.get(), sv, x, b, y);
+        // two warps per slice in FP32 (latency-limited at one thread per row),
+        // one in FP64 (the FP64 pipe is the limit there)
+        constexpr int H = sizeof(T) == 4 ? 2 : 1;
+        const int64_t n_sl = (A.n_rows + 31) / 32;
+        k_sell_spmv<MODE, T, H><<<grid_for(n_sl, 8 / H), B, 0, s>>>(A.n_rows, A.sell_off.get(),
+                                                                   A.sell_col.get(), sv, x, b, y);
         DPP_LAUNCH_CK();
         return;
     }
@@ -785,6 +808,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
                                                 agg.get(), L.dinv.get(), omega);
         DPP_LAUNCH_CK();
         L.P = std::move(Pm);
+        if (o.spmv_format != 1 && n >= sell_min_rows(o)) build_sell(L.P, s, hs);  // autotuner may pick it
         transpose(L.P, L.R, s, hs);
         Csr AP;
         {
@@ -999,7 +1023,8 @@ void tune_levels(PcImpl& pc, cudaStream_t s) {
             T* cb = lv<T>(C.b, C.b32);
             DPP_CK(cudaMemsetAsync(cx, 0, C.A.n_rows * sizeof(T), s));
             L.lanes_R = tune_lanes<0, T>(L.R, r, nullptr, cb, 1, s);
-            L.lanes_P = tune_lanes<2, T>(L.P, cx, nullptr, x, 2, s);
+            if (pc.opts.spmv_format == 2 && L.P.has_sell()) L.lanes_P = 0;
+            else L.lanes_P = tune_lanes<2, T>(L.P, cx, nullptr, x, 2, s);
         }
     }
     DPP_CK(cudaStreamSynchronize(s));
@@ -1021,6 +1046,7 @@ void amg_make_fp32(PcImpl& pc, cudaStream_t s) {
         to_f32(L.dinv, L.dinv32, s);
         if (l + 1 < pc.levels.size()) {
             to_f32(L.P.val, L.P.val32, s);
+            if (L.P.has_sell()) to_f32(L.P.sell_val, L.P.sell_val32, s);
             to_f32(L.R.val, L.R.val32, s);
         }
         const int64_t n = L.A.n_rows;

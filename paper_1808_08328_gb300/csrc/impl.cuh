@@ -24,8 +24,9 @@ struct Csr {
     DBuf<double> val;
     DBuf<float> val32;
     // Optional SELL-32 copy (slices of 32 rows, column-major within a slice,
-    // each slice as wide as its longest row; padding = (own row, 0.0)). Built
-    // for level matrices with many rows, where one thread per row fills the GPU.
+    // each slice as wide as its longest row; padding = (the row's last column,
+    // 0.0)). Built for level matrices and prolongators with many rows, where
+    // one thread per row fills the GPU.
     DBuf<int> sell_off;      // [n_slices + 1] entry offsets
     DBuf<int> sell_col;
     DBuf<double> sell_val;
