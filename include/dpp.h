@@ -119,9 +119,10 @@ typedef struct {
     int32_t max_iters;         /* total inner iterations cap (default 1000) */
     int32_t x0_zero;           /* 1: ignore x on entry and start from 0 (default 1) */
     int32_t x_memory;          /* dpp_memory of x / lambda arrays passed to dpp_solve* (default device) */
-    int32_t check_every;       /* host convergence check period in iterations (default 1) */
+    int32_t check_every;       /* reserved, ignored: the residual estimate is checked at every
+                                  iteration, when the Hessenberg column reaches the host anyway */
     double inner_rtol;         /* mixed precision: inner cycle reduction target (default 1e-4) */
-    int64_t wait_budget_cycles;/* bound for device-side waits, 0 = library default */
+    int64_t wait_budget_cycles;/* reserved, ignored: no kernel of the library spins on a flag */
     double reorth_eta;         /* second Gram-Schmidt pass when ||w|| drops below reorth_eta
                                   times its value before the first pass (DGKS test; 0 = never,
                                   1 = always; default 0.1) */
@@ -315,7 +316,8 @@ int64_t dpp_launch_count(void);
  * "amg_spmv_PR" (prolongation and restriction), each also with an "_fp32"
  * twin, "amg_spmv_setup" and "amg_spmv_setup_fp32" (SpMVs of the setup: power
  * iterations and the autotuner), and around the phases
- * "assemble", "setup_*", "spgemm_*", "krylov_pc" and "krylov_orth". For the
+ * "assemble", "setup_*", "spgemm_*" and "krylov_*" (preconditioner and
+ * K applications, orthogonalisation, its kernels and its host wait). For the
  * kernel families it also accumulates the algorithmic bytes: every matrix
  * value, index and vector entry, counted once. Timing adds about a
  * microsecond of host work per timed range; ranges inside a CUDA graph

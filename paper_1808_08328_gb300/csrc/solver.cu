@@ -88,7 +88,6 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
     double beta = device_norm(W, W.r.get(), n, s, hs);
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     auto h_at = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-    const int every = std::max(1, o.check_every);
     dpp_status st = DPP_ERR_NOT_CONVERGED;
     while (true) {
         if (!std::isfinite(beta)) { st = DPP_ERR_NONFINITE; break; }
@@ -169,7 +168,6 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
             if (hn <= 1e-300 * std::max(1.0, rr)) { breakdown = true; break; }  // exact subspace
             if (j + 1 < m) axpby(1.0 / hn, W.w.get(), 0.0, V + (size_t)(j + 1) * n, n, s);
             if (est <= cycle_target || info.iterations >= o.max_iters) break;
-            (void)every;
         }
         if (nonfinite) { st = DPP_ERR_NONFINITE; break; }
         // y = H^-1 g (upper triangular, ncol columns)
