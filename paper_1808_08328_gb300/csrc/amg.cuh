@@ -30,9 +30,9 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
             HostScratch& hs, bool upper_only = false);
 // C = U + strict_upper(U)^T for an upper-triangular U (the full symmetric matrix).
 void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs);
-// True when A is square, structurally symmetric and |a_ij - a_ji| <= tol (|a_ij| + |a_ji|)
-// for every entry.
-bool is_symmetric(const Csr& A, double tol, cudaStream_t s, HostScratch& hs);
+// True when A is square and, in every stride-th row, each entry has its mirror
+// with |a_ij - a_ji| <= tol (|a_ij| + |a_ji|).
+bool is_symmetric(const Csr& A, double tol, int stride, cudaStream_t s, HostScratch& hs);
 void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs);
 // blockdiag(S_p1, S_p2) from the pair values and mdiag = 1/diag(K_uu) per network.
 void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,

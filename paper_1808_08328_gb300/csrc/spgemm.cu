@@ -838,17 +838,28 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
     k_onepass_compact<kOneCap><<<grid_for(n * 32, 256), 256, 0, s>>>(n, uone.get(), C.row_ptr.get(), tcol.get(),
                                                                     tval.get(), C.col.get(), C.val.get());
     DPP_LAUNCH_CK();
-    if (n_ovf > 0) {
-        DBuf<int> st(1);
+    if (n_ovf > 0) {  // one block per overflow row; rows wider than kLongCap: one warp each
+        DBuf<int> wide(n_ovf + 2), st(1);
+        DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
         DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
-        const size_t smem = (size_t)2 * 8192 * sizeof(int);
-        set_smem(k_spgemm_wide<8192>, smem);
-        k_spgemm_wide<8192><<<(unsigned)n_ovf, 32, smem, s>>>(A.rp, A.col, A.val, B.rp, B.col, B.val,
-                                                              C.row_ptr.get(), C.col.get(), C.val.get(),
-                                                              ovf.get() + 1, st.get(), up);
+        const size_t smem_l = (size_t)(kLongHT + 2 * kLongCap) * sizeof(int) +
+                              (size_t)kLongWarps * kLongCap * sizeof(double);
+        set_smem(k_long_numeric, smem_l);
+        k_long_numeric<<<(unsigned)n_ovf, kLongWarps * 32, smem_l, s>>>(
+            A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(), C.val.get(),
+            ovf.get() + 1, wide.get(), up);
         DPP_LAUNCH_CK();
-        if (read_scalar(st.get(), s, hs))
-            fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
+        const int n_wide = read_scalar(wide.get(), s, hs);
+        if (n_wide > 0) {
+            const size_t smem = (size_t)2 * 8192 * sizeof(int);
+            set_smem(k_spgemm_wide<8192>, smem);
+            k_spgemm_wide<8192><<<(unsigned)n_wide, 32, smem, s>>>(A.rp, A.col, A.val, B.rp, B.col, B.val,
+                                                                   C.row_ptr.get(), C.col.get(), C.val.get(),
+                                                                   wide.get() + 1, st.get(), up);
+            DPP_LAUNCH_CK();
+            if (read_scalar(st.get(), s, hs))
+                fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
+        }
     }
     DPP_CK(cudaStreamSynchronize(s));
     return true;
@@ -1031,10 +1042,11 @@ __global__ void k_sym_fill(int64_t n, const int* __restrict__ urp, const int* __
     }
 }
 
-// one warp per row: flag entries whose mirror is missing or differs
-__global__ void k_sym_check(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+// one warp per checked row (every stride-th row): flag entries whose mirror
+// is missing or differs
+__global__ void k_sym_check(int64_t n, int stride, const int* __restrict__ rp, const int* __restrict__ col,
                             const double* __restrict__ val, double tol, int* __restrict__ bad) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * stride;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
     bool ok = true;
@@ -1069,12 +1081,13 @@ void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs) {
     DPP_CK(cudaStreamSynchronize(s));
 }
 
-bool is_symmetric(const Csr& A, double tol, cudaStream_t s, HostScratch& hs) {
+bool is_symmetric(const Csr& A, double tol, int stride, cudaStream_t s, HostScratch& hs) {
     if (A.n_rows != A.n_cols) return false;
     DBuf<int> bad(1);
     DPP_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
-    k_sym_check<<<grid_for(A.n_rows * 32, 256), 256, 0, s>>>(A.n_rows, A.row_ptr.get(), A.col.get(),
-                                                             A.val.get(), tol, bad.get());
+    const int64_t rows = (A.n_rows + stride - 1) / stride;
+    k_sym_check<<<grid_for(rows * 32, 256), 256, 0, s>>>(A.n_rows, stride, A.row_ptr.get(), A.col.get(),
+                                                         A.val.get(), tol, bad.get());
     DPP_LAUNCH_CK();
     return read_scalar(bad.get(), s, hs) == 0;
 }
