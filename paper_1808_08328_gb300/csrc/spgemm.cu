@@ -699,6 +699,144 @@ __global__ void k_selfp_values(const int* __restrict__ rows, const int* __restri
     }
 }
 
+// One pass for S_p: the warp of node a collects the columns c of its row
+// (c in N(b), b in N(a): the products of G G with G the pair graph), ranks
+// them, and accumulates the D and Schur terms into slots exactly as
+// k_selfp_scatter does; the sorted columns and both networks' values go to
+// fixed-capacity staging rows. A row wider than CAP sets *ovf, and the
+// caller then builds S_p the two-pass way.
+template <int DIM, int CAP>
+__global__ void __launch_bounds__(128, 8)
+k_selfp_onepass(int64_t n_nodes, const int* __restrict__ prp, const int* __restrict__ pcol,
+                const int* __restrict__ slice_ptr, const double* __restrict__ pv,
+                const double* __restrict__ mdiag, int* __restrict__ count, int* __restrict__ tcol,
+                double* __restrict__ tv1, double* __restrict__ tv2, int* __restrict__ ovf) {
+    constexpr int NV = pair_values(DIM);
+    constexpr int HT = 2 * CAP;
+    constexpr int WPB = 4;
+    __shared__ int sh_keys[WPB][HT];
+    __shared__ int sh_slot[WPB][HT];
+    __shared__ double sh_acc[WPB][2][CAP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * WPB + warp;
+    if (a >= n_nodes) return;
+    int* keys = sh_keys[warp];
+    int* slot = sh_slot[warp];
+    double* acc1 = sh_acc[warp][0];
+    double* acc2 = sh_acc[warp][1];
+    auto pval = [&](int row, int p, int k) -> double {
+        const int64_t grp = (int64_t)slice_ptr[row >> 5] + (p - prp[row]);
+        return pv[(grp * NV + k) * kSell + (row & 31)];
+    };
+    const bool ok = warp_collect<HT>((int)a, prp, pcol, prp, pcol, keys, lane, INT_MIN);
+    int* list = reinterpret_cast<int*>(sh_acc[warp]);  // 4 CAP ints >= HT
+    const int u = ok ? warp_compact<HT>(keys, list, lane) : HT + 1;
+    if (u > CAP) {
+        if (lane == 0) {
+            count[a] = 0;
+            atomicOr(ovf, 1);
+        }
+        return;
+    }
+    warp_rank<HT>(list, u, lane, tcol + a * CAP, keys, slot);
+    for (int e = lane; e < CAP; e += 32) acc1[e] = acc2[e] = 0.0;
+    __syncwarp();
+    const int pa0 = prp[a], pa1 = prp[a + 1];
+    for (int pac = pa0 + lane; pac < pa1; pac += 32) {  // D terms: distinct columns
+        const int e = slot[hs_find<HT>(keys, pcol[pac])];
+        acc1[e] = pval((int)a, pac, 2 + 2 * DIM);
+        acc2[e] = pval((int)a, pac, 3 + 2 * DIM);
+    }
+    __syncwarp();
+    for (int pc0 = pa0; pc0 < pa1; pc0 += 32) {
+        const int pab = pc0 + lane;
+        int b = 0, bs = 0, len = 0;
+        double cab[DIM], m1 = 0.0, m2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cab[k] = 0.0;
+        if (pab < pa1) {
+            b = pcol[pab];
+            bs = prp[b];
+            len = prp[b + 1] - bs;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) cab[k] = pval((int)a, pab, 2 + DIM + k);
+            m1 = mdiag[2 * b];
+            m2 = mdiag[2 * b + 1];
+        }
+        int inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int total = __shfl_sync(kFull, inc, 31);
+        const int excl = inc - len;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(kFull, excl, j + step);
+                if (ex <= t) j += step;
+            }
+            const int bj = __shfl_sync(kFull, b, j);
+            const int pbc = __shfl_sync(kFull, bs, j) + (t - __shfl_sync(kFull, excl, j));
+            double cj[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) cj[k] = __shfl_sync(kFull, cab[k], j);
+            const double mj1 = __shfl_sync(kFull, m1, j), mj2 = __shfl_sync(kFull, m2, j);
+            const bool act = t < total;
+            int e = -1 - lane;
+            double dot = 0.0;
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) dot += cj[k] * pval(bj, pbc, 2 + k);
+                e = slot[hs_find<HT>(keys, pcol[pbc])];
+            }
+            const unsigned peers = __match_any_sync(kFull, e);
+            const int order = __popc(peers & ((1u << lane) - 1u));
+            const int n_sub = (int)__reduce_max_sync(kFull, (unsigned)__popc(peers));
+            for (int r = 0; r < n_sub; ++r) {
+                if (act && order == r) {
+                    acc1[e] -= dot * mj1;
+                    acc2[e] -= dot * mj2;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < u; e += 32) {
+        tv1[a * CAP + e] = acc1[e];
+        tv2[a * CAP + e] = acc2[e];
+    }
+    if (lane == 0) count[a] = u;
+}
+
+// staging rows into blockdiag(S_p1, S_p2): rows a and n + a (columns + n)
+template <int CAP>
+__global__ void k_selfp_compact(int64_t n, int64_t nnz_half, const int* __restrict__ rp,
+                                const int* __restrict__ tcol, const double* __restrict__ tv1,
+                                const double* __restrict__ tv2, int* __restrict__ srp,
+                                int* __restrict__ scol, double* __restrict__ sval) {
+    const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (a > n) return;
+    if (lane == 0) {
+        srp[a] = rp[a];
+        srp[n + a] = rp[a] + (int)nnz_half;
+    }
+    if (a == n) return;
+    const int c0 = rp[a], u = rp[a + 1] - c0;
+    for (int e = lane; e < u; e += 32) {
+        const int c = tcol[a * CAP + e];
+        scol[c0 + e] = c;
+        scol[nnz_half + c0 + e] = c + (int)n;
+        sval[c0 + e] = tv1[a * CAP + e];
+        sval[nnz_half + c0 + e] = tv2[a * CAP + e];
+    }
+}
+
 // block-diagonal duplication of the pattern: rows n..2n-1 get columns + n
 __global__ void k_dup_pattern(int64_t n, int64_t nnz, int* __restrict__ rp, int* __restrict__ col) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1092,9 +1230,40 @@ bool is_symmetric(const Csr& A, double tol, int stride, cudaStream_t s, HostScra
     return read_scalar(bad.get(), s, hs) == 0;
 }
 
+namespace {
+// one-pass S_p when every row fits kSelfpOneCap columns; false = not built
+template <int DIM, int CAP>
+bool selfp_onepass(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
+                   HostScratch& hs) {
+    const int64_t n = P.n_nodes;
+    DBuf<int> cnt(n + 1), tcol(n * CAP), ovf(1);
+    DBuf<double> tv1(n * CAP), tv2(n * CAP);
+    DPP_CK(cudaMemsetAsync(cnt.get(), 0, (n + 1) * sizeof(int), s));
+    DPP_CK(cudaMemsetAsync(ovf.get(), 0, sizeof(int), s));
+    k_selfp_onepass<DIM, CAP><<<grid_for(n, 4), 128, 0, s>>>(
+        n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(), mdiag, cnt.get(),
+        tcol.get(), tv1.get(), tv2.get(), ovf.get());
+    DPP_LAUNCH_CK();
+    if (read_scalar(ovf.get(), s, hs)) return false;
+    const int64_t nnz = exclusive_scan(cnt.get(), cnt.get(), n + 1, s, hs);
+    S.n_rows = S.n_cols = 2 * n;
+    S.nnz = 2 * nnz;
+    S.row_ptr.alloc(2 * n + 1);
+    S.col.alloc(std::max<int64_t>(2 * nnz, 1));
+    S.val.alloc(std::max<int64_t>(2 * nnz, 1));
+    k_selfp_compact<CAP><<<grid_for((n + 1) * 32, 256), 256, 0, s>>>(
+        n, nnz, cnt.get(), tcol.get(), tv1.get(), tv2.get(), S.row_ptr.get(), S.col.get(), S.val.get());
+    DPP_LAUNCH_CK();
+    DPP_CK(cudaStreamSynchronize(s));
+    return true;
+}
+}  // namespace
+
 void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
                  HostScratch& hs) {
-    // pattern of G*G with G the pair graph (self pairs included)
+    if (P.dim == 3 ? selfp_onepass<3, 128>(P, mdiag, S, s, hs) : selfp_onepass<2, 64>(P, mdiag, S, s, hs))
+        return;
+    // two passes: pattern of G*G with G the pair graph (self pairs included), then values
     CsrView G;
     G.n_rows = G.n_cols = P.n_nodes;
     G.nnz = P.n_pairs;
