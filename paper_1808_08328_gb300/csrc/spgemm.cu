@@ -28,6 +28,14 @@
 //      the sequential (p, q) order and the result is deterministic. Rows
 //      wider than the largest shared accumulator (1024 columns) use one warp
 //      with the accumulator in C's own storage.
+// Products with many rows (at least 16384) skip the counting pass: each row of
+// at most 128 columns is collected, ranked and accumulated once into a
+// fixed-capacity staging row, then a scan and a compaction copy build C; only
+// the wider rows are counted, and they take a block-per-row kernel. Products
+// with few rows give rows with many products to a block of 8 warps each.
+// Symmetric Galerkin products may be formed as their upper triangle and
+// mirrored (symmetrize_upper). S_p is built the same one-pass way, with its
+// pattern (the pair graph squared) collected by the same product loop.
 #include <climits>
 
 #include "amg.cuh"
