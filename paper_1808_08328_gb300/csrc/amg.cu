@@ -318,48 +318,43 @@ __global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
 // Strength of connection, one warp per row: j != i is a strong neighbour of i
 // when |a_ij| >= theta sqrt(|a_ii| |a_jj|), tested as a_ij^2 >= theta^2 |a_ii| |a_jj|
 // (no FP64 square root, which is slow on this GPU's FP64 pipe). Ballots keep
-// the row's column order, so the fill pass writes exactly the entries the
-// count pass counted.
+// the row's column order.
 __device__ __forceinline__ bool is_strong(int64_t i, int j, double aij, double di,
                                           const double* __restrict__ dabs, double theta2) {
     return j != i && aij * aij >= theta2 * (di * dabs[j]);
 }
 
-__global__ void k_strength_count(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+// One pass: the strong columns of row i go to tmp[rp[i] ...] (the row's own
+// range in A) and their number to cnt[i]; k_strength_compact then packs them.
+__global__ void k_strength_stage(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
                                  const double* __restrict__ val, const double* __restrict__ dabs,
-                                 double theta2, int* __restrict__ cnt) {
+                                 double theta2, int* __restrict__ cnt, int* __restrict__ tmp) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
     const double di = dabs[i];
     const int p1 = rp[i + 1];
-    int c = 0;
-    for (int p0 = rp[i]; p0 < p1; p0 += 32) {
-        const int p = p0 + lane;
-        const bool st = p < p1 && is_strong(i, col[p], val[p], di, dabs, theta2);
-        c += __popc(__ballot_sync(0xffffffffu, st));
-    }
-    if (lane == 0) cnt[i] = c;
-}
-
-__global__ void k_strength_fill(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
-                                const double* __restrict__ val, const double* __restrict__ dabs,
-                                double theta2, const int* __restrict__ srp, int* __restrict__ scol) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;
-    const double di = dabs[i];
-    const int p1 = rp[i + 1];
-    int q = srp[i];
+    int q = rp[i];
     for (int p0 = rp[i]; p0 < p1; p0 += 32) {
         const int p = p0 + lane;
         const int j = p < p1 ? col[p] : -1;
         const bool st = p < p1 && is_strong(i, j, val[p], di, dabs, theta2);
         const unsigned m = __ballot_sync(0xffffffffu, st);
-        if (st) scol[q + __popc(m & ((1u << lane) - 1u))] = j;
+        if (st) tmp[q + __popc(m & ((1u << lane) - 1u))] = j;
         q += __popc(m);
     }
+    if (lane == 0) cnt[i] = q - rp[i];
 }
+
+__global__ void k_strength_compact(int64_t n, const int* __restrict__ rp, const int* __restrict__ tmp,
+                                   const int* __restrict__ srp, int* __restrict__ scol) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int c = srp[i + 1] - srp[i];
+    for (int e = lane; e < c; e += 32) scol[srp[i] + e] = tmp[rp[i] + e];
+}
+
 
 enum : int { kOut = 0, kUnd = 1, kIn = 2 };
 
@@ -393,13 +388,20 @@ __global__ void k_mis_max(int64_t n, const int* __restrict__ srp, const int* __r
     if (valid && sub == 0) tout[i] = m;
 }
 
+// decide the undecided rows, and write the next round's keys (t0_next) for all
 __global__ void k_mis_update(int64_t n, int* __restrict__ state, const uint64_t* __restrict__ t0,
-                             const uint64_t* __restrict__ t2, int* __restrict__ undecided) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || state[i] != kUnd) return;
-    if (t2[i] == t0[i]) state[i] = kIn;
-    else if ((int)(t2[i] >> 62) == kIn) state[i] = kOut;
-    else atomicAdd(undecided, 1);
+                             const uint64_t* __restrict__ t2, uint64_t* __restrict__ t0_next,
+                             int* __restrict__ undecided) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int st = state[i];
+    if (st == kUnd) {
+        if (t2[i] == t0[i]) st = kIn;
+        else if ((int)(t2[i] >> 62) == kIn) st = kOut;
+        else atomicAdd(undecided, 1);
+        state[i] = st;
+    }
+    t0_next[i] = mis_key(st, i);
 }
 
 // flag[0..n) = root indicator, flag[n] = 0 (the scan below runs over n + 1 entries)
@@ -740,35 +742,37 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         S.n_rows = S.n_cols = n;
         S.row_ptr.alloc(n + 1);
         DPP_CK(cudaMemsetAsync(S.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
-        k_strength_count<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+        DBuf<int> stage(std::max<int64_t>(L.A.nnz, 1));
+        k_strength_stage<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
                                                       L.A.val.get(), dabs.get(), theta2,
-                                                      S.row_ptr.get());
+                                                      S.row_ptr.get(), stage.get());
         DPP_LAUNCH_CK();
         S.nnz = exclusive_scan(S.row_ptr.get(), S.row_ptr.get(), n + 1, s, hs);
         S.col.alloc(std::max<int64_t>(S.nnz, 1));
-        k_strength_fill<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
-                                                     L.A.val.get(), dabs.get(), theta2,
-                                                     S.row_ptr.get(), S.col.get());
+        k_strength_compact<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), stage.get(),
+                                                        S.row_ptr.get(), S.col.get());
         DPP_LAUNCH_CK();
 
         pr_str.stop();
         // distance-2 maximal independent set
         ProfScope pr_mis("setup_mis", s, 0);
         DBuf<int> state(n), undecided(1);
-        DBuf<uint64_t> t0(n), t1(n), t2(n);
+        DBuf<uint64_t> t0a(n), t0b(n), t1(n), t2(n);
         k_fill_int<<<grid_for(n, B), B, 0, s>>>(n, kUnd, state.get());
         DPP_LAUNCH_CK();
+        k_mis_t0<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0a.get());
+        DPP_LAUNCH_CK();
+        uint64_t* t0 = t0a.get();
+        uint64_t* t0n = t0b.get();
         for (int round = 0; round < 64; ++round) {
             DPP_CK(cudaMemsetAsync(undecided.get(), 0, sizeof(int), s));
-            k_mis_t0<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get());
-            DPP_LAUNCH_CK();
-            k_mis_max<<<grid_for(n * kMisLanes, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t0.get(), t1.get());
+            k_mis_max<<<grid_for(n * kMisLanes, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t0, t1.get());
             DPP_LAUNCH_CK();
             k_mis_max<<<grid_for(n * kMisLanes, B), B, 0, s>>>(n, S.row_ptr.get(), S.col.get(), t1.get(), t2.get());
             DPP_LAUNCH_CK();
-            k_mis_update<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0.get(), t2.get(),
-                                                      undecided.get());
+            k_mis_update<<<grid_for(n, B), B, 0, s>>>(n, state.get(), t0, t2.get(), t0n, undecided.get());
             DPP_LAUNCH_CK();
+            std::swap(t0, t0n);
             // the count is read every other round (a round after the last
             // decision changes nothing), which halves the host round trips
             if ((round & 1) && read_scalar(undecided.get(), s, hs) == 0) break;

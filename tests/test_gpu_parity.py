@@ -171,6 +171,21 @@ def test_fp64_solve_matches_oracle(DPPSystem, name, make):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_reorthogonalisation_threshold_keeps_the_solution(DPPSystem, precision):
+    # eta = 1: a second Gram-Schmidt pass at every step; eta = 0: never. Both
+    # must reach the bar, and the solutions agree to well below it.
+    P = inputs.heterogeneous_problem(3, 8, seed=5, beta=1.0)
+    s = DPPSystem.from_problem(P, precision=precision).setup_pc(precision=precision)
+    xa, ia = s.solve(rtol=1e-10, reorth_eta=1.0)
+    xb, ib = s.solve(rtol=1e-10, reorth_eta=0.0)
+    assert ia["status"] == 0 and ib["status"] == 0
+    assert abs(ia["iterations"] - ib["iterations"]) <= 1
+    err = oracle.field_rel_errors(xb.cpu().numpy(), xa.cpu().numpy())
+    assert max(err.values()) <= 1e-8, err
+    s.close()
+
+
 def test_pc_apply_is_linear_and_transpose_consistent(DPPSystem):
     P = inputs.heterogeneous_problem(2, 16, seed=7)
     s = DPPSystem.from_problem(P).setup_pc()
