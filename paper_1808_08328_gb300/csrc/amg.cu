@@ -40,7 +40,33 @@ namespace dpp {
 namespace {
 
 // ------------------------------------------------------------------ CSR SpMV
-// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x. T: values, vectors and arithmetic.
+// Chebyshev step fused into the residual SpMV (MODE 3): with r = b - A x,
+// d = c1 d + c2 Dinv r and xo = x + d, written to xo (not x, which other rows
+// still read). c1 = 0 does not read d.
+template <class T>
+struct ChebOut {
+    const T* dinv = nullptr;
+    T* d = nullptr;
+    T* xo = nullptr;
+    T c1 = T(0), c2 = T(0);
+};
+
+template <int MODE, class T>
+__device__ __forceinline__ void spmv_out(int64_t row, T acc, const T* __restrict__ x, const T* __restrict__ b,
+                                         T* __restrict__ y, const ChebOut<T>& ch) {
+    if (MODE == 0) y[row] = acc;
+    else if (MODE == 1) y[row] = b[row] - acc;
+    else if (MODE == 2) y[row] += acc;
+    else {
+        const T r = b[row] - acc;
+        const T dn = (ch.c1 != T(0) ? ch.c1 * ch.d[row] : T(0)) + ch.c2 * ch.dinv[row] * r;
+        ch.d[row] = dn;
+        ch.xo[row] = x[row] + dn;
+    }
+}
+
+// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x; 3: Chebyshev step (above).
+// T: values, vectors and arithmetic.
 // L lanes share a row; each lane walks its entries four at a time with four
 // independent partial sums, so that several gathers are in flight.
 template <int L, int MODE, class T>
@@ -48,7 +74,8 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
                                                   const int* __restrict__ col,
                                                   const T* __restrict__ val,
                                                   const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y) {
+                                                  const T* __restrict__ b, T* __restrict__ y,
+                                                  ChebOut<T> ch) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = t / L;
     const int lane = (int)(t % L);
@@ -70,11 +97,7 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
     T acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
-    if (active && lane == 0) {
-        if (MODE == 0) y[row] = acc;
-        else if (MODE == 1) y[row] = b[row] - acc;
-        else y[row] += acc;
-    }
+    if (active && lane == 0) spmv_out<MODE, T>(row, acc, x, b, y, ch);
 }
 
 // ------------------------------------------------------------------ SELL-32 SpMV
@@ -90,7 +113,8 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __
                                                    const int* __restrict__ col,
                                                    const T* __restrict__ val,
                                                    const T* __restrict__ x,
-                                                   const T* __restrict__ b, T* __restrict__ y) {
+                                                   const T* __restrict__ b, T* __restrict__ y,
+                                                   ChebOut<T> ch) {
     constexpr int U = sizeof(T) == 4 ? 8 : 4;
     constexpr int SPB = 8 / H;  // slices per 256-thread block
     static_assert(H == 1 || H == 2, "one or two warps per slice");
@@ -131,9 +155,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __
         acc += part[warp / H][lane];
     }
     if (!live) return;
-    if (MODE == 0) y[row] = acc;
-    else if (MODE == 1) y[row] = b[row] - acc;
-    else y[row] += acc;
+    spmv_out<MODE, T>(row, acc, x, b, y, ch);
 }
 
 // slice widths: w[s] = 32 * (longest row of slice s); one warp per slice
@@ -174,13 +196,15 @@ template <> const float* vals<float>(const Csr& A) { return A.val32.get(); }
 
 template <int MODE, class T>
 void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStream_t s,
-                const char* family = nullptr) {
+                const char* family = nullptr, ChebOut<T> ch = ChebOut<T>()) {
     const bool sell = lanes == 0 && A.has_sell() &&
                       (sizeof(T) == 8 ? A.sell_val.get() != nullptr : A.sell_val32.get() != nullptr);
     // algorithmic bytes: values and column indices of the nonzeros, the row
     // pointers (CSR only), x once, y (and b) once; SELL padding is not counted
+    // (MODE 3 moves b, Dinv, d, and writes d and the new x: 5 values per row)
     const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (sell ? 0.0 : (double)(A.n_rows + 1) * 4.0) +
-                       (double)A.n_cols * sizeof(T) + (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : 2);
+                       (double)A.n_cols * sizeof(T) +
+                       (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : MODE == 3 ? 5 : 2);
     ProfScope prof(family ? family : (sizeof(T) == 8 ? "amg_spmv_setup" : "amg_spmv_setup_fp32"), s, alg);
     const int B = 256;
     if (sell) {
@@ -191,7 +215,7 @@ void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStrea
         constexpr int H = sizeof(T) == 4 ? 2 : 1;
         const int64_t n_sl = (A.n_rows + 31) / 32;
         k_sell_spmv<MODE, T, H><<<grid_for(n_sl, 8 / H), B, 0, s>>>(A.n_rows, A.sell_off.get(),
-                                                                   A.sell_col.get(), sv, x, b, y);
+                                                                   A.sell_col.get(), sv, x, b, y, ch);
         DPP_LAUNCH_CK();
         return;
     }
@@ -202,12 +226,12 @@ void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStrea
     const int* cl = A.col.get();
     const T* v = vals<T>(A);
     switch (lanes) {
-        case 1: k_csr_spmv<1, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 2: k_csr_spmv<2, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 4: k_csr_spmv<4, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 8: k_csr_spmv<8, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        case 16: k_csr_spmv<16, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
-        default: k_csr_spmv<32, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y); break;
+        case 1: k_csr_spmv<1, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y, ch); break;
+        case 2: k_csr_spmv<2, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y, ch); break;
+        case 4: k_csr_spmv<4, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y, ch); break;
+        case 8: k_csr_spmv<8, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y, ch); break;
+        case 16: k_csr_spmv<16, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y, ch); break;
+        default: k_csr_spmv<32, MODE, T><<<g, B, 0, s>>>(A.n_rows, rp, cl, v, x, b, y, ch); break;
     }
     DPP_LAUNCH_CK();
 }
@@ -256,21 +280,16 @@ __global__ void k_diag_inv(int64_t n, const int* __restrict__ rp, const int* __r
     if (dabs) dabs[i] = fabs(d);
 }
 
-// Chebyshev vector step: zero_init: d = c2 Dinv b, x = d.  else: d = c1 d + c2 Dinv r, x += d
+// First Chebyshev step from a zero start: d = c2 Dinv b, x = d (the later steps
+// are fused into the residual SpMV, MODE 3)
 template <class T>
-__global__ void k_cheb_update(int64_t n, const T* __restrict__ dinv, const T* __restrict__ r,
-                              T* __restrict__ d, T* __restrict__ x, T c1, T c2, int zero_init) {
+__global__ void k_cheb_start(int64_t n, const T* __restrict__ dinv, const T* __restrict__ b,
+                             T* __restrict__ d, T* __restrict__ x, T c2) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        if (zero_init) {
-            T v = c2 * dinv[i] * r[i];
-            d[i] = v;
-            x[i] = v;
-        } else {
-            T v = c1 * d[i] + c2 * dinv[i] * r[i];
-            d[i] = v;
-            x[i] += v;
-        }
+        const T v = c2 * dinv[i] * b[i];
+        d[i] = v;
+        x[i] = v;
     }
 }
 
@@ -717,6 +736,7 @@ void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
         DPP_LAUNCH_CK();
         check_dev(st, s, hs, "a level matrix has a non-positive diagonal entry");
         L.x.alloc(n);
+        L.xt.alloc(n);
         L.b.alloc(n);
         L.r.alloc(n);
         L.d.alloc(n);
@@ -858,27 +878,40 @@ void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, c
     const double hi = 1.1 * L.lmax, lo = L.lmax / pc.opts.cheb_ratio;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     const int64_t n = L.A.n_rows;
-    T* r = lv<T>(L.r, L.r32);
+    T* tmp = lv<T>(L.xt, L.xt32);
     T* d = lv<T>(L.d, L.d32);
     const T* dinv = lv<T>(L.dinv, L.dinv32);
     double rho = 1.0 / sigma;
-    for (int k = 0; k < deg; ++k) {
-        if (k == 0) {
-            if (zero_init) {
-                k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, b, d, x, T(0), T(1.0 / theta), 1);
-            } else {
-                spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
-                k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, r, d, x, T(0), T(1.0 / theta), 0);
-            }
-        } else {
+    // Every step after a zero start is one fused SpMV + update (MODE 3) that
+    // writes the new iterate to the other of x and tmp; the start buffer is
+    // chosen so that the last step lands in x.
+    const int fused = zero_init ? deg - 1 : deg;
+    T* cur = x;
+    int k = 0;
+    if (zero_init) {
+        cur = (fused % 2 == 0) ? x : tmp;
+        k_cheb_start<T><<<sgrid(n), 256, 0, s>>>(n, dinv, b, d, cur, T(1.0 / theta));
+        DPP_LAUNCH_CK();
+        k = 1;
+    }
+    for (; k < deg; ++k) {
+        double c1 = 0.0, c2 = 1.0 / theta;
+        if (k > 0) {
             const double rho_new = 1.0 / (2.0 * sigma - rho);
-            spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
-            k_cheb_update<T><<<sgrid(n), 256, 0, s>>>(n, dinv, r, d, x, T(rho_new * rho),
-                                                      T(2.0 * rho_new / delta), 0);
+            c1 = rho_new * rho;
+            c2 = 2.0 * rho_new / delta;
             rho = rho_new;
         }
-        DPP_LAUNCH_CK();
+        ChebOut<T> ch;
+        ch.dinv = dinv;
+        ch.d = d;
+        ch.xo = (cur == x) ? tmp : x;
+        ch.c1 = T(c1);
+        ch.c2 = T(c2);
+        spmv_lanes<3, T>(L.lanes, L.A, cur, b, nullptr, s, fam, ch);
+        cur = ch.xo;
     }
+    if (cur != x) DPP_CK(cudaMemcpyAsync(x, cur, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
 }
 
 template <class T>
@@ -1058,6 +1091,7 @@ void amg_make_fp32(PcImpl& pc, cudaStream_t s) {
         }
         const int64_t n = L.A.n_rows;
         L.x32.alloc(n);
+        L.xt32.alloc(n);
         L.b32.alloc(n);
         L.r32.alloc(n);
         L.d32.alloc(n);

@@ -78,9 +78,9 @@ struct Level {
     double lmax = 0;          // estimate of the largest eigenvalue of D^-1 A
     int lanes = 4;            // CSR SpMV lanes per row of A (autotuned)
     int lanes_P = 4, lanes_R = 4;  // lanes per row of P and R (autotuned)
-    // V-cycle work vectors (length n_rows)
-    DBuf<double> x, b, r, d;
-    DBuf<float> x32, b32, r32, d32;
+    // V-cycle work vectors (length n_rows); xt: the smoother's second iterate buffer
+    DBuf<double> x, xt, b, r, d;
+    DBuf<float> x32, xt32, b32, r32, d32;
 };
 
 struct PcImpl {
