@@ -109,7 +109,11 @@ typedef struct {
     int32_t sell_min_rows;     /* level matrices with at least this many rows also get a SELL-32
                                   copy (0 = library default, 65536) */
     int32_t spmv_format;       /* AMG SpMV format: 0 = autotuned among SELL-32 (where built) and
-                                  CSR (default), 1 = CSR only, 2 = SELL-32 wherever built */
+                                  CSR (default), 1 = CSR only, 2 = SELL-32 wherever built.
+                                  The autotuned choices are cached for the process per size
+                                  class; if the environment variable DPP_TUNE_CACHE names a
+                                  file, they are read from it and new ones are appended to it
+                                  (one JSON object per line). */
 } dpp_pc_opts;
 
 /* Krylov options. */
