@@ -241,21 +241,47 @@ __global__ void k_cell_geometry(const double* __restrict__ X, const int* __restr
     cf[7] = 0.0;
 }
 
-// One thread per node pair: fixed-order gather over the cells of the row node.
+// Fixed-order gather over the cells of the row node, one thread per node pair.
 // The per-cell factors come precomputed from k_cell_geometry (no division here;
 // FP64 division is costly on GB300's FP64 pipe).
+//
+// The FP64 pipe is the limit, and it is charged per warp instruction however
+// few lanes are active. So a thread first marks which of its row node's cells
+// contain the pair (integer work), then runs the FP64 terms over the marked
+// cells only; the lanes of a warp take their terms side by side. Threads
+// [0, n_nodes) do the self pairs, which share all of the node's cells, and
+// threads [n_nodes, n_nodes + n_pairs) the other pairs (a self pair there is
+// skipped), so no warp waits on a 24-cell self pair beside 4-6-cell edge pairs.
+// Each pair still sums its cells in the order of the node's cell list.
 template <int DIM>
 __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __restrict__ col,
-                                 const int* __restrict__ row_ptr, int64_t n_pairs,
+                                 const int* __restrict__ row_ptr, int64_t n_pairs, int64_t n_nodes,
                                  const int* __restrict__ nc_ptr, const int* __restrict__ nc_list,
                                  const int* __restrict__ cells, const double* __restrict__ geo,
                                  const double* __restrict__ coef,
                                  const int* __restrict__ slice_ptr, double* __restrict__ sell_val) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pairs) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes + n_pairs) return;
     constexpr int S = GeoLayout<DIM>::stride;
     constexpr int NV = pair_values(DIM);
-    const int a = pair_row[p], b = col[p];
+    int a, b;
+    int64_t p;
+    if (t < n_nodes) {  // self pair of node t: its slot in the sorted row
+        a = b = (int)t;
+        int lo = row_ptr[a], hi = row_ptr[a + 1];
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (col[mid] < a) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= row_ptr[a + 1] || col[lo] != a) return;  // a node in no cell has no pairs
+        p = lo;
+    } else {
+        p = t - n_nodes;
+        a = pair_row[p];
+        b = col[p];
+        if (a == b) return;
+    }
     const int j = (int)(p - row_ptr[a]);
     const double self = (a == b) ? 2.0 : 1.0;
     // sums over the cells of the pair: mass factors, d terms and the
@@ -263,9 +289,9 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
     double m1 = 0, m2 = 0, d1 = 0, d2 = 0, bm = 0, sa[DIM], sb[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) sa[k] = sb[k] = 0;
-    for (int q = nc_ptr[a]; q < nc_ptr[a + 1]; ++q) {
-        const int c = nc_list[q];
-        int la = -1, lb = -1;
+    auto local = [&](int c, int& la, int& lb) {
+        la = -1;
+        lb = -1;
         if constexpr (DIM == 3) {
             const int4 v = *reinterpret_cast<const int4*>(cells + (int64_t)c * 4);
             la = (v.x == a) ? 0 : (v.y == a) ? 1 : (v.z == a) ? 2 : 3;
@@ -273,12 +299,13 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
         } else {
 #pragma unroll
             for (int v = 0; v <= DIM; ++v) {
-                int n = cells[(int64_t)c * (DIM + 1) + v];
+                const int n = cells[(int64_t)c * (DIM + 1) + v];
                 if (n == a) la = v;
                 if (n == b) lb = v;
             }
         }
-        if (lb < 0) continue;
+    };
+    auto term = [&](int c, int la, int lb) {
         const double* g = geo + (int64_t)c * S;
         const double* ga = g + 1 + la * DIM;
         const double* gb = g + 1 + lb * DIM;
@@ -296,6 +323,32 @@ __global__ void k_assemble_pairs(const int* __restrict__ pair_row, const int* __
             sa[k] += cf[0] * ga[k];
             sb[k] += cf[0] * gb[k];
         }
+    };
+    const int q0 = nc_ptr[a], q1 = nc_ptr[a + 1];
+    const int qm = min(q1, q0 + 64);
+    unsigned long long mask = 0;
+    if (a == b) {  // every cell of the node holds the self pair
+        mask = (qm - q0 == 64) ? ~0ull : ((1ull << (qm - q0)) - 1ull);
+    } else {
+        for (int q = q0; q < qm; ++q) {
+            int la, lb;
+            local(nc_list[q], la, lb);
+            if (lb >= 0) mask |= 1ull << (q - q0);
+        }
+    }
+    while (mask) {
+        const int q = q0 + __ffsll((long long)mask) - 1;
+        mask &= mask - 1ull;
+        const int c = nc_list[q];
+        int la, lb;
+        local(c, la, lb);
+        term(c, la, lb);
+    }
+    for (int q = qm; q < q1; ++q) {  // nodes in more than 64 cells
+        const int c = nc_list[q];
+        int la, lb;
+        local(c, la, lb);
+        if (lb >= 0) term(c, la, lb);
     }
     m1 *= self;
     m2 *= self;
@@ -558,8 +611,8 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
     // 6. pair values
     P.sell_val.alloc(P.n_groups * P.nv * kSell);
     DPP_CK(cudaMemsetAsync(P.sell_val.get(), 0, P.sell_val.bytes(), s));
-    k_assemble_pairs<DIM><<<grid_for(P.n_pairs, B), B, 0, s>>>(
-        P.pair_row.get(), P.col.get(), P.row_ptr.get(), P.n_pairs, P.nc_ptr.get(),
+    k_assemble_pairs<DIM><<<grid_for(P.n_pairs + P.n_nodes, B), B, 0, s>>>(
+        P.pair_row.get(), P.col.get(), P.row_ptr.get(), P.n_pairs, P.n_nodes, P.nc_ptr.get(),
         P.nc_list.get(), P.cells.get(), P.geo.get(), P.ccoef.get(), P.slice_ptr.get(),
         P.sell_val.get());
     DPP_LAUNCH_CK();
