@@ -14,6 +14,8 @@ a wrong quadrature.
   * The mass-balance invariant (Eqs. "DG_GE_Darcy_mass_balance_1/2" with q = 1).
   * Network swap symmetry, and decoupling at beta = 0.
   * Wathen's element bound for the Jacobi-scaled P1 mass matrix.
+  * The selfp Schur blocks on the constant pressure, in closed form from the
+    mesh alone (divergence theorem on the boundary facets).
 """
 import os
 
@@ -200,6 +202,68 @@ def test_selfp_schur_is_spd_and_has_two_ring_pattern():
     G = sp.csr_matrix((np.ones(r.size), (r, c)), shape=(m.n_nodes,) * 2)
     G2 = (G @ G).astype(bool)
     assert ((abs(S1) > 0).astype(bool) > G2).nnz == 0
+
+
+def _boundary_facets_with_normals(coords, cells, d):
+    """Facets of the unit box mesh that belong to one cell, with |F| and the
+    outward normal of the box face they lie on."""
+    from itertools import combinations
+    count = {}
+    for c in cells:
+        for f in combinations(sorted(int(v) for v in c), d):
+            count[f] = count.get(f, 0) + 1
+    out = []
+    for f, k in count.items():
+        if k != 1:
+            continue
+        X = coords[list(f)]
+        n = np.zeros(d)
+        for ax in range(d):
+            if np.all(np.abs(X[:, ax]) < 1e-12):
+                n[ax] = -1.0
+            elif np.all(np.abs(X[:, ax] - 1.0) < 1e-12):
+                n[ax] = 1.0
+        assert np.abs(n).sum() == 1.0, "a boundary facet off the box faces"
+        if d == 2:
+            area = np.linalg.norm(X[1] - X[0])
+        else:
+            area = 0.5 * np.linalg.norm(np.cross(X[1] - X[0], X[2] - X[0]))
+        out.append((f, area, n))
+    return out
+
+
+@pytest.mark.parametrize("dim,n", [(2, 6), (3, 3)])
+def test_selfp_schur_constant_mode_closed_form(dim, n):
+    # S_pi = D_ii - C_i diag(A_i)^-1 B_i with C_i = -B_i^T (Section 4.2). On the
+    # constant pressure 1:
+    #   * L 1 = 0 and 1^T M 1 = |Omega| = 1, so 1^T D_ii 1 = beta/mu;
+    #   * (B_i 1)_a = sum_b K_up(a, b) = -int_Omega grad phi_a
+    #     = -sum over boundary facets F of a of |F|/d n_F (divergence theorem);
+    #   * diag(A_i)_a = sum over the cells of a of mu/(2 k_i) 2|K|/((d+1)(d+2)).
+    # So 1^T S_pi 1 = beta/mu + sum_a |(B_i 1)_a|^2 / diag(A_i)_a. A dropped D
+    # term, a wrong Schur sign, a lumped or mis-scaled diag(A) or a wrong B
+    # all change it.
+    from math import factorial
+    mu, beta = 1.3, 0.7
+    P = inputs.heterogeneous_problem(dim, n, seed=5, beta=beta, mu=mu)
+    m = P.mesh
+    K, _ = assemble_problem(P)
+    S = oracle.selfp_schur(K, m.n_nodes, dim)
+    X, C = m.coords, m.cells
+    vol = np.abs(np.linalg.det(X[C[:, 1:]] - X[C[:, :1]])) / factorial(dim)
+    b1 = np.zeros((m.n_nodes, dim))
+    for f, area, nrm in _boundary_facets_with_normals(X, C, dim):
+        for v in f:
+            b1[v] -= area / dim * nrm
+    one = np.ones(m.n_nodes)
+    for Si, lk in zip(S, (P.logk1, P.logk2)):
+        w = mu / (2.0 * np.exp(lk)) * 2.0 * vol / ((dim + 1) * (dim + 2))
+        dA = np.zeros(m.n_nodes)
+        for j in range(dim + 1):
+            np.add.at(dA, C[:, j], w)
+        expected = beta / mu + float(np.sum(b1 ** 2 / dA[:, None]))
+        got = float(one @ (Si @ one))
+        assert abs(got - expected) <= 1e-12 * expected, (got, expected)
 
 
 # --------------------------------------------------------------------------- MMS
