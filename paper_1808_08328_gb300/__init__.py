@@ -19,7 +19,7 @@ from .binding import (DppError, DPP_FP64, DPP_MIXED_FP32_FP64, DPP_MEM_DEVICE, D
 
 def __getattr__(name):
     # torch-dependent helpers are imported lazily so the binding loads without torch
-    if name in ("DPPSystem", "DPPSolve"):
+    if name in ("DPPSystem", "DPPSolve", "DPPBatch", "solve_batched"):
         from . import system
         return getattr(system, name)
     raise AttributeError(name)
