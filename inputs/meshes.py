@@ -109,6 +109,34 @@ def unit_cube_kuhn(n: int) -> Mesh:
     return Mesh(3, coords, cells, boundary_facets(cells, 3), n)
 
 
+def disc_wheel(sectors: int, rings: int) -> Mesh:
+    """Triangles of a regular polygon of radius 1: a centre node and `rings`
+    concentric rings of `sectors` nodes. The centre lies in `sectors` cells,
+    every other interior node in 6, so a large `sectors` gives one node with
+    many more cells (and neighbours) than the structured meshes have.
+    ``n`` of the returned mesh is `rings`.
+    """
+    if sectors < 3 or rings < 1:
+        raise ValueError("need sectors >= 3 and rings >= 1")
+    th = 2.0 * np.pi * np.arange(sectors) / sectors
+    coords = [np.zeros((1, 2))]
+    for r in range(1, rings + 1):
+        coords.append(np.stack([r / rings * np.cos(th), r / rings * np.sin(th)], axis=1))
+    coords = np.concatenate(coords).astype(np.float64)
+    ring = lambda r, j: 1 + (r - 1) * sectors + (j % sectors)
+    cells = []
+    for j in range(sectors):
+        cells.append((0, ring(1, j), ring(1, j + 1)))
+    for r in range(1, rings):
+        for j in range(sectors):
+            a, b = ring(r, j), ring(r, j + 1)
+            c, d = ring(r + 1, j), ring(r + 1, j + 1)
+            cells.append((a, c, d))
+            cells.append((a, d, b))
+    cells = np.asarray(cells, dtype=np.int32)
+    return Mesh(2, coords, cells, boundary_facets(cells, 2), rings)
+
+
 def unit_mesh(dim: int, n: int) -> Mesh:
     if dim == 2:
         return unit_square_tri(n)

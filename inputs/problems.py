@@ -19,7 +19,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 from .fields import constant_logk, lognormal_logk
-from .meshes import Mesh, unit_mesh
+from .meshes import Mesh, disc_wheel, unit_mesh
 from .mms import PAPER, MMSParams, boundary_pressures
 
 
@@ -63,3 +63,14 @@ def heterogeneous_problem(dim: int, n: int, seed: int = 0, beta: float = 1.0,
     p01, p02 = boundary_pressures(mesh.coords, PAPER)
     return Problem(mesh, lk1, lk2, mu, beta, np.zeros(dim), p01, p02,
                    name=f"het{dim}d_n{n}_s{seed}", meta={"seed": seed})
+
+
+def wheel_problem(sectors: int = 70, rings: int = 4, seed: int = 0, beta: float = 1.0,
+                  mu: float = 1.0) -> Problem:
+    """Log-normal fields on the disc wheel mesh, with the paper's boundary
+    pressures evaluated at the rim nodes."""
+    mesh = disc_wheel(sectors, rings)
+    lk1, lk2 = lognormal_logk(mesh.n_cells, seed)
+    p01, p02 = boundary_pressures(mesh.coords, PAPER)
+    return Problem(mesh, lk1, lk2, mu, beta, np.zeros(2), p01, p02,
+                   name=f"wheel_s{sectors}_r{rings}_s{seed}", meta={"seed": seed})

@@ -27,7 +27,10 @@ pytestmark = [pytest.mark.gpu, needs_gpu]
 CASES = [("mms2d_n7", lambda: inputs.mms_problem(2, 7)),
          ("het2d_n32", lambda: inputs.heterogeneous_problem(2, 32, seed=1, beta=1.0)),
          ("het3d_n5", lambda: inputs.heterogeneous_problem(3, 5, seed=2, beta=0.5)),
-         ("mms3d_n6", lambda: inputs.mms_problem(3, 6))]
+         ("mms3d_n6", lambda: inputs.mms_problem(3, 6)),
+         # a node in 70 cells: the assembly's per-pair cell masks cover 64
+         # cells, the rest take the tail loop
+         ("wheel2d_s70", lambda: inputs.wheel_problem(70, 4, seed=2, beta=0.8))]
 
 
 @pytest.fixture(scope="module")
@@ -82,6 +85,21 @@ def test_selfp_schur_matches_definition(DPPSystem, dim, n):
     K, _ = assemble_problem(P)
     S1, S2 = oracle.selfp_schur(K, P.mesh.n_nodes, dim)
     ref = sp.block_diag([S1, S2]).tocsr()
+    s = DPPSystem.from_problem(P).setup_pc()
+    sz, (rp, col, val), _ = s.level(0, with_p=False)
+    S = csr_from_export(rp, col, val, ref.shape)
+    assert abs(S - ref).max() <= 1e-12 * abs(ref).max()
+    s.close()
+
+
+def test_selfp_schur_wide_rows_match_definition(DPPSystem):
+    # The wheel's centre and first-ring rows of S_p have 75 to 141 columns,
+    # more than the one-pass staging rows hold (64 in 2D): the two-pass path.
+    P = inputs.wheel_problem(70, 4, seed=6, beta=1.5)
+    K, _ = assemble_problem(P)
+    S1, S2 = oracle.selfp_schur(K, P.mesh.n_nodes, 2)
+    ref = sp.block_diag([S1, S2]).tocsr()
+    assert np.diff(ref.indptr).max() > 64
     s = DPPSystem.from_problem(P).setup_pc()
     sz, (rp, col, val), _ = s.level(0, with_p=False)
     S = csr_from_export(rp, col, val, ref.shape)
@@ -152,7 +170,8 @@ def test_release_cached_memory_keeps_live_handles(DPPSystem):
 SOLVES = [("het2d_n32", lambda: inputs.heterogeneous_problem(2, 32, seed=0, beta=1.0)),
           ("mms2d_n32", lambda: inputs.mms_problem(2, 32)),
           ("het3d_n8", lambda: inputs.heterogeneous_problem(3, 8, seed=0, beta=1.0)),
-          ("mms3d_n10", lambda: inputs.mms_problem(3, 10))]
+          ("mms3d_n10", lambda: inputs.mms_problem(3, 10)),
+          ("wheel2d_s70", lambda: inputs.wheel_problem(70, 4, seed=0, beta=1.0))]
 
 
 @pytest.mark.parametrize("name,make", SOLVES, ids=[c[0] for c in SOLVES])

@@ -6,7 +6,8 @@ a wrong quadrature.
   * DoF counts against the paper's tables (golden file).
   * Quadrature against closed-form simplex integrals.
   * Linear and constant patch tests: CG-VMS is consistent, and P1 reproduces
-    a linear pressure with a constant Darcy velocity exactly.
+    a linear pressure with a constant Darcy velocity exactly (also on a disc
+    wheel mesh with slanted boundary normals and a 70-cell node).
   * Sparse LU against dense LU.
   * Block-structure identities of K (Eq. "S4_cg_stiffness_matrix").
   * MMS convergence rate 2 in every field (Sections 5.1 and 5.2, slope
@@ -122,6 +123,22 @@ def test_linear_patch_is_reproduced_exactly(dim, n):
     assert np.allclose(xn[:, 2 * d + 1], P.mesh.coords @ a + 0.3, atol=1e-11)
     assert np.allclose(xn[:, :d], -(2.0 / mu) * a[None, :], atol=1e-10)
     assert np.allclose(xn[:, d + 1:2 * d + 1], -(0.05 / mu) * a[None, :], atol=1e-11)
+
+
+def test_linear_patch_on_the_disc_wheel():
+    # The wheel's rim facets have 70 different outward normals (the box meshes
+    # only axis-aligned ones), and its centre node lies in 70 cells. P1 must
+    # still reproduce p = a.x + c with u = -(k/mu) a exactly.
+    a = np.array([0.9, -0.6])
+    W = inputs.wheel_problem(70, 3, seed=0)
+    m = W.mesh
+    P = inputs.Problem(m, np.full(m.n_cells, np.log(1.7)), np.full(m.n_cells, np.log(0.2)),
+                       1.3, 2.0, np.zeros(2), m.coords @ a - 0.4, m.coords @ a - 0.4)
+    _, _, xn = _solve(P, coords=False)
+    assert np.allclose(xn[:, 2], m.coords @ a - 0.4, atol=1e-11)
+    assert np.allclose(xn[:, 5], m.coords @ a - 0.4, atol=1e-11)
+    assert np.allclose(xn[:, :2], -(1.7 / 1.3) * a[None, :], atol=1e-10)
+    assert np.allclose(xn[:, 3:5], -(0.2 / 1.3) * a[None, :], atol=1e-10)
 
 
 @pytest.mark.parametrize("dim,n", [(2, 4), (3, 2)])
