@@ -153,8 +153,9 @@ void dpp_solve_opts_default(dpp_solve_opts* o);
  * an FP32 copy of the values. On success *out is a new handle.
  * Errors: INVALID_ARGUMENT (null pointers, dim not 2 or 3, an index out of
  * range, a zero-volume cell, mu <= 0 or beta < 0, a bfacet that is not a
- * cell face), NONFINITE (NaN or Inf in coords, log k or p0), OUT_OF_MEMORY,
- * CUDA.
+ * cell face, a node with more than 95 distinct neighbours), NONFINITE (NaN
+ * or Inf in coords, log k or p0), OUT_OF_MEMORY, CUDA. A node may lie in any
+ * number of cells.
  */
 dpp_status dpp_assemble(const dpp_problem_desc* desc, int32_t precision, dpp_stream_t stream,
                         dpp_problem* out);
