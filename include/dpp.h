@@ -165,6 +165,11 @@ dpp_status dpp_assemble(const dpp_problem_desc* desc, int32_t precision, dpp_str
  * S_pi = Ki_pp - Ki_pu diag(Ki_uu)^-1 Ki_up (Eqs. "S4_sp1", "S4_sp2") on the
  * device, then one smoothed-aggregation AMG hierarchy on blockdiag(S_p1,
  * S_p2). Synchronises `stream`. Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA.
+ * Size limit: row pointers are int32, so the nonzeros of blockdiag(S_p1,
+ * S_p2), of every level matrix and of every prolongator must each stay below
+ * 2^31. blockdiag(S_p1, S_p2) has up to 2 x 65 entries per node on 3D Kuhn
+ * meshes, which reaches the limit near 16 M nodes (about 130 M DoF). This is
+ * not checked yet: larger problems must not be passed.
  */
 dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t stream,
                         dpp_pc* out);
