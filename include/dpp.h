@@ -168,8 +168,9 @@ dpp_status dpp_assemble(const dpp_problem_desc* desc, int32_t precision, dpp_str
  * Size limit: row pointers are int32, so the nonzeros of blockdiag(S_p1,
  * S_p2), of every level matrix and of every prolongator must each stay below
  * 2^31. blockdiag(S_p1, S_p2) has up to 2 x 65 entries per node on 3D Kuhn
- * meshes, which reaches the limit near 16 M nodes (about 130 M DoF). This is
- * not checked yet: larger problems must not be passed.
+ * meshes, which reaches the limit near 16 M nodes (about 130 M DoF). A larger
+ * matrix is detected when its row pointers are formed and fails with
+ * INVALID_ARGUMENT (dpp_assemble does the same for the node pairs).
  */
 dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t stream,
                         dpp_pc* out);

@@ -63,20 +63,31 @@ void scan_rec(const int* in, int* out, int64_t n, cudaStream_t s) {
     }
 }
 
-__global__ void k_total(const int* in, const int* out, int64_t n, int* total) {
-    *total = (n > 0) ? out[n - 1] + in[n - 1] : 0;
+// Sum of the (non-negative) counts in 64 bits, so that a total the int32
+// prefix sums cannot hold is detected instead of wrapping.
+__global__ void k_sum64(const int* __restrict__ in, int64_t n, unsigned long long* total) {
+    unsigned long long acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        acc += (unsigned long long)(unsigned)in[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
 }
 }  // namespace
 
 int64_t exclusive_scan(const int* in, int* out, int64_t n, cudaStream_t s, HostScratch& hs) {
     if (n <= 0) return 0;
-    // Save the last input before a possibly aliasing scan overwrites it.
-    DBuf<int> last(2);
-    DPP_CK(cudaMemcpyAsync(last.get(), in + (n - 1), sizeof(int), cudaMemcpyDeviceToDevice, s));
-    scan_rec(in, out, n, s);
-    k_total<<<1, 1, 0, s>>>(last.get(), out + (n - 1), 1, last.get() + 1);
+    // The total is taken before a possibly aliasing scan overwrites the input.
+    DBuf<unsigned long long> total(1);
+    DPP_CK(cudaMemsetAsync(total.get(), 0, sizeof(unsigned long long), s));
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * kSMs);
+    k_sum64<<<(unsigned)blocks, 256, 0, s>>>(in, n, total.get());
     DPP_LAUNCH_CK();
-    return (int64_t)read_scalar(last.get() + 1, s, hs);
+    scan_rec(in, out, n, s);
+    const unsigned long long t = read_scalar(total.get(), s, hs);
+    if (t > (unsigned long long)INT32_MAX)
+        fail(DPP_ERR_INVALID_ARGUMENT, "a matrix has 2^31 or more nonzeros (int32 row pointers)");
+    return (int64_t)t;
 }
 
 }  // namespace dpp
