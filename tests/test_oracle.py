@@ -334,9 +334,11 @@ def test_mms_solution_satisfies_strong_form():
 
 # --------------------------------------------------------------------------- invariants
 
-@pytest.mark.parametrize("dim,n", [(2, 8), (3, 3)])
+@pytest.mark.parametrize("dim,n", [(2, 8), (3, 3), (2, 0)])
 def test_mass_balance_invariant(dim, n):
-    P = inputs.heterogeneous_problem(dim, n, seed=4, beta=1.7)
+    # n = 0: the disc wheel (70 thin cells around its centre)
+    P = (inputs.heterogeneous_problem(dim, n, seed=4, beta=1.7) if n else
+         inputs.wheel_problem(70, 3, seed=4, beta=1.7))
     _, _, xn = _solve(P)
     b1, b2 = oracle.mass_balance(xn, P.mesh.coords, P.mesh.cells, P.mu, P.beta)
     scale = np.abs(xn).max()
@@ -361,10 +363,11 @@ def test_swap_symmetry_and_beta_zero_decoupling():
     assert not np.allclose(xa[:, 3:], xb[:, 3:])
 
 
-@pytest.mark.parametrize("dim,n", [(2, 5), (3, 2)])
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 2), (2, 0)])
 def test_wathen_bound_for_jacobi_scaled_mass(dim, n):
     # eig(diag(M)^-1 M) lies in [1/2, (d+2)/2] for any positive per-cell weights
-    m = inputs.unit_mesh(dim, n)
+    # and any simplices (n = 0: the disc wheel, with its thin centre cells)
+    m = inputs.unit_mesh(dim, n) if n else inputs.disc_wheel(70, 3)
     geom = geometry(m.coords, m.cells)
     lam, wq = cell_rule(dim)
     wts = np.exp(inputs.rng(11).normal(0, 2, m.n_cells))
