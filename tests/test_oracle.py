@@ -74,6 +74,18 @@ def test_mesh_is_a_conforming_partition(dim, n):
     assert m.n_cells == (2 if dim == 2 else 6) * n ** dim
 
 
+def test_disc_wheel_is_a_conforming_partition_of_its_polygon():
+    S, R = 70, 3
+    m = inputs.disc_wheel(S, R)
+    g = geometry(m.coords, m.cells)
+    assert np.all(g.vol > 0)
+    assert np.isclose(g.vol.sum(), 0.5 * S * np.sin(2 * np.pi / S))    # the polygon's area
+    assert m.n_nodes == 1 + S * R and m.n_cells == S * (2 * R - 1)
+    assert m.n_bfacets == S                                             # the rim edges only
+    assert np.allclose(np.linalg.norm(m.coords[m.bfacets], axis=2), 1.0)
+    assert np.bincount(m.cells.ravel()).max() == S                      # the centre node
+
+
 # --------------------------------------------------------------------------- quadrature
 
 @pytest.mark.parametrize("dim", [2, 3])
