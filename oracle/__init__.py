@@ -18,6 +18,9 @@ solvers for the four-field double porosity/permeability model", 2018):
   * solve.py: an FP64 sparse direct solve of K x = f (SuperLU). The
     preconditioned FGMRES on the GPU reaches this same solution, up to its
     tolerance.
+  * iterative.py: the same solution for meshes too large to factor, by a
+    flexible GMRES driven to a true residual of 1e-13, preconditioned by the
+    Method 2 Schur factorisation with incomplete-LU pieces.
   * errors.py: L2 errors against the manufactured solutions (Section 5,
     "errornorm" against the P1 interpolant), per-field parity norms, and
     mass-balance integrals (Eqs. "DG_GE_Darcy_mass_balance_1/2").
@@ -34,6 +37,7 @@ from .quadrature import cell_rule, facet_rule
 from .assembly import (Geometry, geometry, element_matrices, element_rhs_body,
                        assemble, assemble_rhs, assemble_rows, slot_index, to_nodal, from_nodal)
 from .solve import solve_direct, solve_dense, residual
+from .iterative import solve_field_split_gmres
 from .errors import (p1_mass_matrix, interp_l2_errors, field_rel_errors, field_slices,
                      mass_balance, FIELDS)
 from .blocks import field_split_blocks, selfp_schur
@@ -43,7 +47,7 @@ from .adjoint import (objective, objective_grad_x, adjoint_solve, adjoint_gradie
 __all__ = [
     "cell_rule", "facet_rule", "Geometry", "geometry", "element_matrices", "element_rhs_body",
     "assemble", "assemble_rhs", "assemble_rows", "slot_index", "to_nodal", "from_nodal",
-    "solve_direct", "solve_dense", "residual",
+    "solve_direct", "solve_dense", "residual", "solve_field_split_gmres",
     "p1_mass_matrix", "interp_l2_errors", "field_rel_errors", "field_slices", "mass_balance",
     "FIELDS", "field_split_blocks", "selfp_schur",
     "objective", "objective_grad_x", "adjoint_solve", "adjoint_gradients",

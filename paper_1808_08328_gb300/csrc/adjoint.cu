@@ -26,54 +26,14 @@ __global__ void k_cell_sensitivity(int64_t n_cells, const int* __restrict__ cell
                                    double mu, double gb0, double gb1, double gb2,
                                    double* __restrict__ g1, double* __restrict__ g2,
                                    double* __restrict__ gbeta_cell) {
-    constexpr int S = GeoLayout<DIM>::stride;
-    constexpr int NS = 2 * DIM + 2;
-    constexpr int NV = DIM + 1;
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     const double gbv[3] = {gb0, gb1, gb2};
-    int v[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) v[a] = cells[c * NV + a];
-    const double* g = geo + c * S;
-    const double vol = g[0];
-    const double k1 = kk[2 * c], k2 = kk[2 * c + 1];
-    const double cm = vol / ((DIM + 1) * (DIM + 2));
-    double mu1 = 0, mu2 = 0, lp1 = 0, lp2 = 0, f1 = 0, f2 = 0, mb = 0;
-#pragma unroll
-    for (int a = 0; a < NV; ++a) {
-        const double* la = lam + (int64_t)v[a] * NS;
-        const double* ga = g + 1 + a * DIM;
-        double gdot = 0;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) gdot += ga[k] * gbv[k];
-        f1 += la[DIM] * gdot;
-        f2 += la[2 * DIM + 1] * gdot;
-#pragma unroll
-        for (int b = 0; b < NV; ++b) {
-            const double* xb = x + (int64_t)v[b] * NS;
-            const double* gbb = g + 1 + b * DIM;
-            const double m = cm * (a == b ? 2.0 : 1.0);
-            double lg = 0, uu1 = 0, uu2 = 0;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) {
-                lg += ga[k] * gbb[k];
-                uu1 += la[k] * xb[k];
-                uu2 += la[DIM + 1 + k] * xb[DIM + 1 + k];
-            }
-            mu1 += m * uu1;
-            mu2 += m * uu2;
-            lp1 += vol * lg * la[DIM] * xb[DIM];
-            lp2 += vol * lg * la[2 * DIM + 1] * xb[2 * DIM + 1];
-            mb += m * (la[DIM] - la[2 * DIM + 1]) * (xb[DIM] - xb[2 * DIM + 1]);
-        }
-    }
-    // lambda^T dK x with dK = -1/2 mu/k M (uu) + 1/2 k/mu L (pp); minus lambda^T df
-    const double t1 = -0.5 * mu / k1 * mu1 + 0.5 * k1 / mu * lp1 - 0.5 * k1 / mu * vol * f1;
-    const double t2 = -0.5 * mu / k2 * mu2 + 0.5 * k2 / mu * lp2 - 0.5 * k2 / mu * vol * f2;
-    g1[c] = -t1;
-    g2[c] = -t2;
-    gbeta_cell[c] = -mb / mu;
+    double t1, t2, tb;
+    cell_sensitivity<DIM>(c, cells, geo, kk, x, lam, mu, gbv, t1, t2, tb);
+    g1[c] = t1;
+    g2[c] = t2;
+    gbeta_cell[c] = tb;
 }
 
 }  // namespace

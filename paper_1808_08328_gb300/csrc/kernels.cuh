@@ -35,6 +35,68 @@ void mass_diag_inv(const ProblemImpl& P, double* mdiag, bool lumped, cudaStream_
 template <class T>
 void scatter_p(const ProblemImpl& P, const T* yp, T* z, cudaStream_t s);
 
+// ---- adjoint sensitivities of one cell (shared by adjoint.cu and noalloc.cu) ----
+// For cell c of the CG-VMS form: g1 = dJ/dlog k1_c and g2 = dJ/dlog k2_c, i.e.
+// -lambda^T (dK/dlog k_i x - df/dlog k_i) with the derivative -1/2 mu/k_i M_c on
+// the velocity block, +1/2 k_i/mu L_c on the pressure block and
+// +1/2 k_i/mu |K| g_a . gamma_b on the load; and the cell's share of dJ/dbeta,
+// -(1/mu) (lambda_p1 - lambda_p2)^T M_c (x_p1 - x_p2). M_c = |K| (1 + delta_ab) /
+// ((d+1)(d+2)) and L_c = |K| g_a . g_b are exact for P1.
+template <int DIM>
+__device__ __forceinline__ void cell_sensitivity(int64_t c, const int* __restrict__ cells,
+                                                 const double* __restrict__ geo,
+                                                 const double* __restrict__ kk,
+                                                 const double* __restrict__ x,
+                                                 const double* __restrict__ lam, double mu,
+                                                 const double (&gbv)[3], double& g1, double& g2,
+                                                 double& beta_term) {
+    constexpr int S = GeoLayout<DIM>::stride;
+    constexpr int NS = 2 * DIM + 2;
+    constexpr int NV = DIM + 1;
+    int v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = cells[c * NV + a];
+    const double* g = geo + c * S;
+    const double vol = g[0];
+    const double k1 = kk[2 * c], k2 = kk[2 * c + 1];
+    const double cm = vol / ((DIM + 1) * (DIM + 2));
+    double mu1 = 0, mu2 = 0, lp1 = 0, lp2 = 0, f1 = 0, f2 = 0, mb = 0;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+        const double* la = lam + (int64_t)v[a] * NS;
+        const double* ga = g + 1 + a * DIM;
+        double gdot = 0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) gdot += ga[k] * gbv[k];
+        f1 += la[DIM] * gdot;
+        f2 += la[2 * DIM + 1] * gdot;
+#pragma unroll
+        for (int b = 0; b < NV; ++b) {
+            const double* xb = x + (int64_t)v[b] * NS;
+            const double* gbb = g + 1 + b * DIM;
+            const double m = cm * (a == b ? 2.0 : 1.0);
+            double lg = 0, uu1 = 0, uu2 = 0;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                lg += ga[k] * gbb[k];
+                uu1 += la[k] * xb[k];
+                uu2 += la[DIM + 1 + k] * xb[DIM + 1 + k];
+            }
+            mu1 += m * uu1;
+            mu2 += m * uu2;
+            lp1 += vol * lg * la[DIM] * xb[DIM];
+            lp2 += vol * lg * la[2 * DIM + 1] * xb[2 * DIM + 1];
+            mb += m * (la[DIM] - la[2 * DIM + 1]) * (xb[DIM] - xb[2 * DIM + 1]);
+        }
+    }
+    // lambda^T dK x with dK = -1/2 mu/k M (uu) + 1/2 k/mu L (pp); minus lambda^T df
+    const double t1 = -0.5 * mu / k1 * mu1 + 0.5 * k1 / mu * lp1 - 0.5 * k1 / mu * vol * f1;
+    const double t2 = -0.5 * mu / k2 * mu2 + 0.5 * k2 / mu * lp2 - 0.5 * k2 / mu * vol * f2;
+    g1 = -t1;
+    g2 = -t2;
+    beta_term = -mb / mu;
+}
+
 // ---- vector kernels (n doubles) ----
 struct Reducer {
     DBuf<double> partial;   // [rows][kRedBlocks]

@@ -39,11 +39,8 @@ constexpr int64_t kNoAllocMaxCells = (int64_t)kNoAllocMaxBlocks * kNoAllocThread
 
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 
-// Same cell formula as the allocating path: with the CG-VMS form,
-//   dJ/dlog k_i,c = -lambda^T (dK/dlog k_i,c x - df/dlog k_i,c), where the derivative is
-//   -1/2 mu/k_i M_c (velocity block), +1/2 k_i/mu L_c (pressure block) and
-//   +1/2 k_i/mu |K| g_a.gamma_b (load);
-//   dJ/dbeta = -(1/mu) sum_c (lambda_p1 - lambda_p2)^T M_c (x_p1 - x_p2).
+// The per-cell formula is dpp::cell_sensitivity, the one the allocating path
+// uses; only the reduction of the beta term differs (block partials here).
 template <int DIM>
 __global__ void __launch_bounds__(kNoAllocThreads)
 k_cell_sensitivity_partials(int64_t n_cells, const int* __restrict__ cells,
@@ -51,55 +48,15 @@ k_cell_sensitivity_partials(int64_t n_cells, const int* __restrict__ cells,
                             const double* __restrict__ x, const double* __restrict__ lam, double mu,
                             double gb0, double gb1, double gb2, double* __restrict__ g1,
                             double* __restrict__ g2, double* __restrict__ partials) {
-    constexpr int S = dpp::GeoLayout<DIM>::stride;
-    constexpr int NS = 2 * DIM + 2;
-    constexpr int NV = DIM + 1;
     __shared__ double sh[kNoAllocThreads / 32];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double beta_term = 0.0;
     if (c < n_cells) {
         const double gbv[3] = {gb0, gb1, gb2};
-        int v[NV];
-#pragma unroll
-        for (int a = 0; a < NV; ++a) v[a] = cells[c * NV + a];
-        const double* g = geo + c * S;
-        const double vol = g[0];
-        const double k1 = kk[2 * c], k2 = kk[2 * c + 1];
-        const double cm = vol / ((DIM + 1) * (DIM + 2));
-        double mu1 = 0, mu2 = 0, lp1 = 0, lp2 = 0, f1 = 0, f2 = 0, mb = 0;
-#pragma unroll
-        for (int a = 0; a < NV; ++a) {
-            const double* la = lam + (int64_t)v[a] * NS;
-            const double* ga = g + 1 + a * DIM;
-            double gdot = 0;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) gdot += ga[k] * gbv[k];
-            f1 += la[DIM] * gdot;
-            f2 += la[2 * DIM + 1] * gdot;
-#pragma unroll
-            for (int b = 0; b < NV; ++b) {
-                const double* xb = x + (int64_t)v[b] * NS;
-                const double* gbb = g + 1 + b * DIM;
-                const double m = cm * (a == b ? 2.0 : 1.0);
-                double lg = 0, uu1 = 0, uu2 = 0;
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) {
-                    lg += ga[k] * gbb[k];
-                    uu1 += la[k] * xb[k];
-                    uu2 += la[DIM + 1 + k] * xb[DIM + 1 + k];
-                }
-                mu1 += m * uu1;
-                mu2 += m * uu2;
-                lp1 += vol * lg * la[DIM] * xb[DIM];
-                lp2 += vol * lg * la[2 * DIM + 1] * xb[2 * DIM + 1];
-                mb += m * (la[DIM] - la[2 * DIM + 1]) * (xb[DIM] - xb[2 * DIM + 1]);
-            }
-        }
-        const double t1 = -0.5 * mu / k1 * mu1 + 0.5 * k1 / mu * lp1 - 0.5 * k1 / mu * vol * f1;
-        const double t2 = -0.5 * mu / k2 * mu2 + 0.5 * k2 / mu * lp2 - 0.5 * k2 / mu * vol * f2;
-        g1[c] = -t1;
-        g2[c] = -t2;
-        beta_term = -mb / mu;
+        double t1, t2;
+        dpp::cell_sensitivity<DIM>(c, cells, geo, kk, x, lam, mu, gbv, t1, t2, beta_term);
+        g1[c] = t1;
+        g2[c] = t2;
     }
     const double s = dpp::block_sum(beta_term, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -146,35 +103,44 @@ extern "C" dpp_status dpp_adjoint_gradients_noalloc(dpp_problem prob, const doub
                                                    const double* lambda, double* dJ_dlogk1,
                                                    double* dJ_dlogk2, double* dJ_dbeta,
                                                    dpp_stream_t stream) {
-    if (!prob || !x || !lambda || !dJ_dlogk1 || !dJ_dlogk2 || !dJ_dbeta)
-        return report(DPP_ERR_INVALID_ARGUMENT, "dpp_adjoint_gradients_noalloc: null argument");
-    const dpp::ProblemImpl& P = prob->impl;
-    if (P.n_cells > kNoAllocMaxCells)
-        return report(DPP_ERR_INVALID_ARGUMENT,
-                      "dpp_adjoint_gradients_noalloc: n_cells exceeds the fixed scratch limit of "
-                      "4194304 cells (use dpp_adjoint_solve for larger meshes)");
-    double* partials = nullptr;
-    cudaError_t e = scratch_address(&partials);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: cudaGetSymbolAddress failed");
+    // Like every other entry point: the thread-local message is cleared on
+    // entry, and no exception leaves the library.
+    dpp::set_last_error_message("");
+    try {
+        if (!prob || !x || !lambda || !dJ_dlogk1 || !dJ_dlogk2 || !dJ_dbeta)
+            return report(DPP_ERR_INVALID_ARGUMENT, "dpp_adjoint_gradients_noalloc: null argument");
+        const dpp::ProblemImpl& P = prob->impl;
+        if (P.n_cells > kNoAllocMaxCells)
+            return report(DPP_ERR_INVALID_ARGUMENT,
+                          "dpp_adjoint_gradients_noalloc: n_cells exceeds the fixed scratch limit of "
+                          "4194304 cells (use dpp_adjoint_solve for larger meshes)");
+        double* partials = nullptr;
+        cudaError_t e = scratch_address(&partials);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: cudaGetSymbolAddress failed");
+        }
+        const int nblk = (int)((P.n_cells + kNoAllocThreads - 1) / kNoAllocThreads);
+        cudaStream_t s = (cudaStream_t)stream;
+        if (P.dim == 2)
+            k_cell_sensitivity_partials<2><<<nblk, kNoAllocThreads, 0, s>>>(
+                P.n_cells, P.cells.get(), P.geo.get(), P.kk.get(), x, lambda, P.mu, P.gb[0], P.gb[1],
+                P.gb[2], dJ_dlogk1, dJ_dlogk2, partials);
+        else
+            k_cell_sensitivity_partials<3><<<nblk, kNoAllocThreads, 0, s>>>(
+                P.n_cells, P.cells.get(), P.geo.get(), P.kk.get(), x, lambda, P.mu, P.gb[0], P.gb[1],
+                P.gb[2], dJ_dlogk1, dJ_dlogk2, partials);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: launch failed");
+        dpp::count_launch();
+        k_sum_partials<<<1, kNoAllocThreads, 0, s>>>(partials, nblk, dJ_dbeta);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: launch failed");
+        dpp::count_launch();
+        return DPP_OK;
+    } catch (const dpp::Error& e) {
+        return report(e.status, e.what());
+    } catch (...) {
+        return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: unexpected failure");
     }
-    const int nblk = (int)((P.n_cells + kNoAllocThreads - 1) / kNoAllocThreads);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (P.dim == 2)
-        k_cell_sensitivity_partials<2><<<nblk, kNoAllocThreads, 0, s>>>(
-            P.n_cells, P.cells.get(), P.geo.get(), P.kk.get(), x, lambda, P.mu, P.gb[0], P.gb[1],
-            P.gb[2], dJ_dlogk1, dJ_dlogk2, partials);
-    else
-        k_cell_sensitivity_partials<3><<<nblk, kNoAllocThreads, 0, s>>>(
-            P.n_cells, P.cells.get(), P.geo.get(), P.kk.get(), x, lambda, P.mu, P.gb[0], P.gb[1],
-            P.gb[2], dJ_dlogk1, dJ_dlogk2, partials);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: launch failed");
-    dpp::count_launch();
-    k_sum_partials<<<1, kNoAllocThreads, 0, s>>>(partials, nblk, dJ_dbeta);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return report(DPP_ERR_CUDA, "dpp_adjoint_gradients_noalloc: launch failed");
-    dpp::count_launch();
-    return DPP_OK;
 }

@@ -5,7 +5,9 @@ log-normal fields drawn from separate seeds and beta log-uniform in
 [0.1, 10], is solved in one call. This is the recipe of the batched workload
 at sizes the oracle factors in seconds. Every instance must meet the single-solve
 bar: per-field relative L2 error <= 1e-8 against its own direct solve, at its
-own true relative residual <= 1e-10. The faults are injected on the host: a NaN
+own true relative residual <= 1e-10. The same holds on the first 16 instances
+of the benchmark's own 256-instance recipe (N up to 128), whose union is large
+enough for the SELL-32 paths. The faults are injected on the host: a NaN
 in one instance's log k, an out-of-range node id in another, and an iteration
 cap. They must give per-instance statuses and leave the other instances
 correct.
@@ -50,6 +52,38 @@ def test_batched_matches_per_instance_oracle(precision):
     for P, x, inf in zip(probs, xs, infos):
         assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
         _check(P, x)
+
+
+@pytest.fixture(scope="module")
+def recipe_slice():
+    """The first 16 instances of the 256-instance batch recipe (N ~ U{16..128}),
+    with each instance's oracle solution. Their union has more than 65,536
+    level-0 rows, so the SELL-32 level-0 and prolongator paths of the
+    benchmark's batched run are taken."""
+    probs = [inputs.heterogeneous_problem(2, n, seed=si, beta=b)
+             for (n, si, b) in inputs.batch_recipe(256, 0)[:16]]
+    refs = []
+    for P in probs:
+        K, f = assemble_problem(P)
+        refs.append((K, f, oracle.to_nodal(oracle.solve_direct(K, f), P.mesh.n_nodes)))
+    return probs, refs
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_batched_recipe_slice_matches_oracle(recipe_slice, precision):
+    system_cls()
+    from paper_1808_08328_gb300.system import solve_batched
+    probs, refs = recipe_slice
+    assert sum(2 * P.mesh.n_nodes for P in probs) > 65536
+    assert max(P.mesh.n for P in probs) >= 100
+    xs, infos, st = solve_batched(probs, precision=precision, rtol=1e-10)
+    assert st == 0
+    for P, (K, f, ref), x, inf in zip(probs, refs, xs, infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+        xn = x.cpu().numpy()
+        assert oracle.residual(K, oracle.from_nodal(xn), f) <= 1.5e-10
+        err = oracle.field_rel_errors(xn, ref)
+        assert max(err.values()) <= 1e-8, (P.mesh.n, err)
 
 
 def test_batched_faults_are_per_instance():

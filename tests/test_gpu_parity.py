@@ -30,7 +30,16 @@ CASES = [("mms2d_n7", lambda: inputs.mms_problem(2, 7)),
          ("mms3d_n6", lambda: inputs.mms_problem(3, 6)),
          # a node in 70 cells: the assembly's per-pair cell masks cover 64
          # cells, the rest take the tail loop
-         ("wheel2d_s70", lambda: inputs.wheel_problem(70, 4, seed=2, beta=0.8))]
+         ("wheel2d_s70", lambda: inputs.wheel_problem(70, 4, seed=2, beta=0.8)),
+         # a constant body force gamma*b: the load's k-weighted pressure rows
+         ("het2d_n13_gb", lambda: _with_gb(inputs.heterogeneous_problem(2, 13, seed=3, beta=1.2),
+                                           [1.5, -0.7])),
+         ("het3d_n5_gb", lambda: _with_gb(inputs.heterogeneous_problem(3, 5, seed=4, beta=0.9),
+                                          [0.4, -1.1, 2.0]))]
+
+
+def _with_gb(P, gb):
+    return P.with_(gamma_b=np.asarray(gb, dtype=np.float64))
 
 
 @pytest.fixture(scope="module")
@@ -171,7 +180,9 @@ SOLVES = [("het2d_n32", lambda: inputs.heterogeneous_problem(2, 32, seed=0, beta
           ("mms2d_n32", lambda: inputs.mms_problem(2, 32)),
           ("het3d_n8", lambda: inputs.heterogeneous_problem(3, 8, seed=0, beta=1.0)),
           ("mms3d_n10", lambda: inputs.mms_problem(3, 10)),
-          ("wheel2d_s70", lambda: inputs.wheel_problem(70, 4, seed=0, beta=1.0))]
+          ("wheel2d_s70", lambda: inputs.wheel_problem(70, 4, seed=0, beta=1.0)),
+          ("het3d_n9_gb", lambda: _with_gb(inputs.heterogeneous_problem(3, 9, seed=1, beta=1.0),
+                                           [0.8, 0.3, -1.4]))]
 
 
 @pytest.mark.parametrize("name,make", SOLVES, ids=[c[0] for c in SOLVES])
@@ -219,18 +230,26 @@ def test_pc_apply_is_linear_and_transpose_consistent(DPPSystem):
     s.close()
 
 
-def test_adjoint_matches_oracle(DPPSystem):
-    P = inputs.heterogeneous_problem(2, 10, seed=1, beta=1.3)
-    Pobs = inputs.heterogeneous_problem(2, 10, seed=2, beta=1.3)
+@pytest.mark.parametrize("dim,n,gb", [(2, 10, None), (2, 10, [1.7, -0.9]),
+                                      (3, 5, [0.6, -1.2, 0.9])],
+                         ids=["2d", "2d_gb", "3d_gb"])
+def test_adjoint_matches_oracle(DPPSystem, dim, n, gb):
+    # With a body force the load depends on log k, so the gradient carries the
+    # -lambda^T df/dlog k term as well as the K sensitivities.
+    P = inputs.heterogeneous_problem(dim, n, seed=1, beta=1.3)
+    Pobs = inputs.heterogeneous_problem(dim, n, seed=2, beta=1.3)
+    if gb is not None:
+        P, Pobs = _with_gb(P, gb), _with_gb(Pobs, gb)
     K, f = assemble_problem(P)
     Ko, fo = assemble_problem(Pobs)
     xn = oracle.to_nodal(oracle.solve_direct(K, f), P.mesh.n_nodes)
-    p1_obs = oracle.to_nodal(oracle.solve_direct(Ko, fo), P.mesh.n_nodes)[:, 2]
+    p1_obs = oracle.to_nodal(oracle.solve_direct(Ko, fo), P.mesh.n_nodes)[:, dim]
     g = oracle.objective_grad_x(xn, p1_obs)
     lam_ref = oracle.adjoint_solve(K, g)
     g1r, g2r, gbr = oracle.adjoint_gradients(P, xn, lam_ref)
     s = DPPSystem.from_problem(P).setup_pc()
     x, _ = s.solve(rtol=1e-13)
+    assert oracle.field_rel_errors(x.cpu().numpy(), xn)["p1"] <= 1e-10
     gx = torch.tensor(oracle.objective_grad_x(x.cpu().numpy(), p1_obs), device="cuda")
     lam, g1, g2, gb, info = s.adjoint(x, gx, rtol=1e-13)
     assert info["status"] == 0

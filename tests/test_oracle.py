@@ -110,7 +110,7 @@ def test_facet_rule_integrates_p1_products_exactly(dim):
 
 # --------------------------------------------------------------------------- patch tests
 
-def _linear_problem(dim, n, a, c1, c2, k1, k2, beta, perturb=True):
+def _linear_problem(dim, n, a, c1, c2, k1, k2, beta, perturb=True, gamma_b=None):
     m = inputs.unit_mesh(dim, n)
     if perturb:  # move interior nodes so the patch test is not a structured-mesh accident
         rng = inputs.rng(7)
@@ -120,8 +120,9 @@ def _linear_problem(dim, n, a, c1, c2, k1, k2, beta, perturb=True):
         m.coords = X
     p01 = m.coords @ a + c1
     p02 = m.coords @ a + c2
+    gb = np.zeros(dim) if gamma_b is None else np.asarray(gamma_b, dtype=np.float64)
     return inputs.Problem(m, np.full(m.n_cells, np.log(k1)), np.full(m.n_cells, np.log(k2)),
-                          1.3, beta, np.zeros(dim), p01, p02)
+                          1.3, beta, gb, p01, p02)
 
 
 @pytest.mark.parametrize("dim,n", [(2, 4), (3, 3)])
@@ -135,6 +136,33 @@ def test_linear_patch_is_reproduced_exactly(dim, n):
     assert np.allclose(xn[:, 2 * d + 1], P.mesh.coords @ a + 0.3, atol=1e-11)
     assert np.allclose(xn[:, :d], -(2.0 / mu) * a[None, :], atol=1e-10)
     assert np.allclose(xn[:, d + 1:2 * d + 1], -(0.05 / mu) * a[None, :], atol=1e-11)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4), (3, 3)])
+def test_body_force_patch_is_reproduced_exactly(dim, n):
+    # Darcy's law with a constant body force (Eqs. "DG_GE_Darcy_BLM_1/2"):
+    # mu/k_i u_i + grad p_i = gamma b. With p1 = p2 = a.x + c there is no mass
+    # transfer, so u_i = (k_i/mu)(gamma b - a) is constant and divergence-free:
+    # an exact solution in P1 for constant k. CG-VMS is consistent, so the
+    # discrete solution reproduces it only if the load vector carries the
+    # body-force terms of Eq. "S4_cg_rhs" with the right weights and signs:
+    # 1/2 (w; gamma b) on the velocity rows and 1/2 (grad q; k/mu gamma b) on
+    # the pressure rows. A dropped 1/2 or a flipped sign of either term breaks it.
+    a = np.array([0.7, -1.1, 0.4][:dim])
+    gb = np.array([1.9, 0.6, -1.3][:dim])
+    P = _linear_problem(dim, n, a, -0.2, -0.2, k1=2.0, k2=0.05, beta=3.0, gamma_b=gb)
+    K, f, xn = _solve(P, coords=False)
+    mu, d = P.mu, dim
+    assert np.abs(f).max() > 0.1
+    assert np.allclose(xn[:, d], P.mesh.coords @ a - 0.2, atol=1e-11)
+    assert np.allclose(xn[:, 2 * d + 1], P.mesh.coords @ a - 0.2, atol=1e-11)
+    assert np.allclose(xn[:, :d], (2.0 / mu) * (gb - a)[None, :], atol=1e-10)
+    assert np.allclose(xn[:, d + 1:2 * d + 1], (0.05 / mu) * (gb - a)[None, :], atol=1e-11)
+    # gamma b = a: the body force balances the pressure gradient and u = 0
+    P0 = _linear_problem(dim, n, a, 0.5, 0.5, k1=2.0, k2=0.05, beta=3.0, gamma_b=a)
+    _, _, x0 = _solve(P0, coords=False)
+    assert np.allclose(x0[:, :d], 0.0, atol=1e-11)
+    assert np.allclose(x0[:, d + 1:2 * d + 1], 0.0, atol=1e-11)
 
 
 def test_linear_patch_on_the_disc_wheel():
@@ -346,15 +374,35 @@ def test_mms_solution_satisfies_strong_form():
 
 # --------------------------------------------------------------------------- invariants
 
-@pytest.mark.parametrize("dim,n", [(2, 8), (3, 3), (2, 0)])
-def test_mass_balance_invariant(dim, n):
-    # n = 0: the disc wheel (70 thin cells around its centre)
+@pytest.mark.parametrize("dim,n,gb", [(2, 8, 0.0), (3, 3, 0.0), (2, 0, 0.0), (2, 8, 1.5),
+                                      (3, 3, -0.8)])
+def test_mass_balance_invariant(dim, n, gb):
+    # n = 0: the disc wheel (70 thin cells around its centre). A body force
+    # does not change the invariant: its pressure-row load 1/2 (grad q; k/mu
+    # gamma b) vanishes for q = 1.
     P = (inputs.heterogeneous_problem(dim, n, seed=4, beta=1.7) if n else
          inputs.wheel_problem(70, 3, seed=4, beta=1.7))
+    P = P.with_(gamma_b=gb * np.linspace(1.0, -0.5, dim))
     _, _, xn = _solve(P)
     b1, b2 = oracle.mass_balance(xn, P.mesh.coords, P.mesh.cells, P.mu, P.beta)
     scale = np.abs(xn).max()
     assert abs(b1) < 1e-11 * scale and abs(b2) < 1e-11 * scale
+
+
+@pytest.mark.parametrize("dim,n,gb", [(2, 12, 0.0), (3, 5, 0.0), (3, 4, 1.2)])
+def test_field_split_gmres_reaches_the_direct_solution(dim, n, gb):
+    # The oracle for meshes too large to factor: flexible GMRES to a true
+    # residual of 1e-13. It must land on the sparse-LU solution.
+    P = inputs.heterogeneous_problem(dim, n, seed=6, beta=1.4)
+    P = P.with_(gamma_b=gb * np.linspace(1.0, -0.5, dim))
+    K, f = assemble_problem(P)
+    x, it, res = oracle.solve_field_split_gmres(K, f, P.mesh.n_nodes, dim)
+    assert res <= 1e-13 and oracle.residual(K, x, f) <= 1e-13
+    assert it < 60
+    xd = oracle.solve_dense(K, f) if K.shape[0] < 3000 else oracle.solve_direct(K, f)
+    err = oracle.field_rel_errors(oracle.to_nodal(x, P.mesh.n_nodes),
+                                  oracle.to_nodal(xd, P.mesh.n_nodes))
+    assert max(err.values()) <= 1e-11, err
 
 
 def test_swap_symmetry_and_beta_zero_decoupling():

@@ -4,7 +4,8 @@ The objective is J = sum over nodes (p1 - p1_obs)^2. p1_obs is the oracle's p1
 for log-k fields drawn from the next seed. The adjoint gradient (transpose solve
 plus per-cell element sensitivities) must agree with
   * the global complex-step derivative (Martins et al., ACM TOMS 2003), to
-    1e-9 relative: both are exact up to rounding;
+    1e-9 relative: both are exact up to rounding. With and without a body
+    force, which makes the load vector depend on log k;
   * central differences with h = 1e-6, to 1e-5 relative to the largest
     sampled gradient entry: the FD truncation and cancellation error is
     about 1e-10 |J| / h.
@@ -17,9 +18,12 @@ import oracle
 from oracle.assembly import assemble_problem
 
 
-def _setup(dim, n, seed=0):
+def _setup(dim, n, seed=0, gamma_b=None):
     P = inputs.heterogeneous_problem(dim, n, seed=seed, beta=1.3)
     Pobs = inputs.heterogeneous_problem(dim, n, seed=seed + 1, beta=1.3)
+    if gamma_b is not None:
+        P = P.with_(gamma_b=np.asarray(gamma_b, dtype=np.float64))
+        Pobs = Pobs.with_(gamma_b=np.asarray(gamma_b, dtype=np.float64))
     K, f = assemble_problem(P)
     Kobs, fobs = assemble_problem(Pobs)
     xn = oracle.to_nodal(oracle.solve_direct(K, f), P.mesh.n_nodes)
@@ -29,9 +33,12 @@ def _setup(dim, n, seed=0):
     return P, p1_obs, oracle.adjoint_gradients(P, xn, lam)
 
 
-@pytest.mark.parametrize("dim,n", [(2, 5), (3, 2)])
-def test_adjoint_matches_complex_step(dim, n):
-    P, p1_obs, (g1, g2, gb) = _setup(dim, n)
+@pytest.mark.parametrize("dim,n,gamma_b", [(2, 5, None), (3, 2, None), (2, 5, [2.0, -1.5]),
+                                           (3, 2, [0.5, 1.0, -2.0])])
+def test_adjoint_matches_complex_step(dim, n, gamma_b):
+    # With a body force the load depends on k (1/2 (grad q; k/mu gamma b)), so
+    # the adjoint's -lambda^T df/dlog k term is exercised too.
+    P, p1_obs, (g1, g2, gb) = _setup(dim, n, gamma_b=gamma_b)
     cells = inputs.sample_cells(P.mesh.n_cells, 4, seed=2)
     for c in cells:
         cs1 = oracle.complex_step_gradient(P, p1_obs, "logk1", int(c))

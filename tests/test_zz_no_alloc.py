@@ -20,11 +20,13 @@ from gpu_helpers import needs_gpu, system_cls, torch
 pytestmark = [pytest.mark.gpu, needs_gpu]
 
 
-@pytest.mark.parametrize("dim,n", [(2, 12), (3, 6)])
-def test_noalloc_gradients_match_adjoint_solve(dim, n):
+@pytest.mark.parametrize("dim,n,gb", [(2, 12, None), (3, 6, None), (3, 5, [0.3, -1.0, 0.8])])
+def test_noalloc_gradients_match_adjoint_solve(dim, n, gb):
     from paper_1808_08328_gb300 import binding as B
     DPPSystem = system_cls()
     P = inputs.heterogeneous_problem(dim, n, seed=4, beta=1.7)
+    if gb is not None:  # a body force: the load's log-k derivative enters too
+        P = P.with_(gamma_b=np.asarray(gb, dtype=np.float64))
     s = DPPSystem.from_problem(P).setup_pc()
     x, info = s.solve(rtol=1e-12)
     assert info["status"] == 0
