@@ -15,12 +15,13 @@
  *     "CG_VMS_Weak_form", Section 3.3), P1 on triangles and tetrahedra.
  *     Blocks: Eq. "S4_cg_stiffness_matrix"; load: Eq. "S4_cg_rhs"; system
  *     K u = f: Eq. "S4_linear_problem" (Section 4).
- *   - Solver: Method 2 of Section 4.2 ("splitting by fields"). A full
- *     Schur factorisation of [[A, B], [C, D]] with A = blockdiag(K1_uu,
- *     K2_uu); the selfp Schur matrix S_p = D - C diag(A)^-1 B, additively
- *     split into its two diagonal blocks (Eqs. "S4_sp1", "S4_sp2"); one
- *     multigrid V-cycle per block; single-sweep inner solves inside an outer
- *     Krylov method.
+ *   - Solver: Method 2 of Section 4.2 ("splitting by fields", the default).
+ *     A full Schur factorisation of [[A, B], [C, D]] with A =
+ *     blockdiag(K1_uu, K2_uu); the selfp Schur matrix S_p = D - C diag(A)^-1
+ *     B, additively split into its two diagonal blocks (Eqs. "S4_sp1",
+ *     "S4_sp2"); one multigrid V-cycle per block; single-sweep inner solves
+ *     inside an outer Krylov method. Method 1 of Section 4.1 ("splitting by
+ *     scales") is the other composition (dpp_pc_opts::composition).
  *
  * Conventions for every entry point:
  *   - Device pointers are CUDA global-memory addresses on the current device.
@@ -96,7 +97,7 @@ typedef struct {
     const double* p02;        /* [n_nodes] micro pressure data, read at bfacet nodes */
 } dpp_problem_desc;
 
-/* Preconditioner options (Section 4.2, Method 2; defaults from dpp_pc_opts_default). */
+/* Preconditioner options (Section 4; defaults from dpp_pc_opts_default). */
 typedef struct {
     int32_t cheb_degree_mass;  /* Chebyshev-Jacobi degree for A^-1 (default 2) */
     int32_t cheb_degree_amg;   /* Chebyshev-Jacobi pre/post smoothing degree (default 2) */
@@ -114,6 +115,19 @@ typedef struct {
                                   class; if the environment variable DPP_TUNE_CACHE names a
                                   file, they are read from it and new ones are appended to it
                                   (one JSON object per line). */
+    int32_t composition;       /* 0: Method 2 of Section 4.2, splitting by fields (default): one
+                                  Schur factorisation over {u1, u2} | {p1, p2} and one SA-AMG
+                                  hierarchy on blockdiag(S_p1, S_p2).
+                                  1: Method 1 of Section 4.1, splitting by scales: an additive
+                                  split {u1, p1} | {u2, p2} (K12_pp dropped), each network with
+                                  its own Schur factorisation, selfp matrix S^i_p (Eqs.
+                                  "S4_sp1", "S4_sp2") and SA-AMG hierarchy. */
+    int32_t mass_solver;       /* inner solve of the velocity block A = blockdiag(K1_uu, K2_uu):
+                                  0: Chebyshev-Jacobi of degree cheb_degree_mass on the exact
+                                  Wathen interval (default);
+                                  1: ILU(0) of each network's mass matrix in natural row order,
+                                  the paper's block Jacobi / ILU(0) sub-solver (Sections 4.1,
+                                  4.2); level-scheduled, one launch per dependency level. */
 } dpp_pc_opts;
 
 /* Krylov options. */
@@ -130,6 +144,10 @@ typedef struct {
     double reorth_eta;         /* second Gram-Schmidt pass when ||w|| drops below reorth_eta
                                   times its value before the first pass (DGKS test; 0 = never,
                                   1 = always; default 0.1) */
+    int32_t matrix_free;       /* 1: the Krylov step's K z is applied element by element from the
+                                  cells' geometry and k (dpp_apply_K_mf; FP32 in the mixed mode,
+                                  dpp_apply_K32_mf) instead of from the assembled pair values.
+                                  Residuals keep the assembled FP64 K. Default 0. */
 } dpp_solve_opts;
 
 typedef struct {
@@ -161,10 +179,12 @@ dpp_status dpp_assemble(const dpp_problem_desc* desc, int32_t precision, dpp_str
                         dpp_problem* out);
 
 /*
- * Build the field-split preconditioner of Section 4.2 (Method 2). It forms
- * S_pi = Ki_pp - Ki_pu diag(Ki_uu)^-1 Ki_up (Eqs. "S4_sp1", "S4_sp2") on the
- * device, then one smoothed-aggregation AMG hierarchy on blockdiag(S_p1,
- * S_p2). Synchronises `stream`. Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA.
+ * Build the block preconditioner of Section 4: Method 2 (splitting by fields,
+ * the default) or Method 1 (splitting by scales), as opts->composition says.
+ * It forms S_pi = Ki_pp - Ki_pu diag(Ki_uu)^-1 Ki_up (Eqs. "S4_sp1",
+ * "S4_sp2") on the device, then smoothed-aggregation AMG: one hierarchy on
+ * blockdiag(S_p1, S_p2) (Method 2) or one per S_pi (Method 1).
+ * Synchronises `stream`. Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA.
  * Size limit: row pointers are int32, so the nonzeros of blockdiag(S_p1,
  * S_p2), of every level matrix and of every prolongator must each stay below
  * 2^31. blockdiag(S_p1, S_p2) has up to 2 x 65 entries per node on 3D Kuhn
@@ -255,6 +275,25 @@ dpp_status dpp_apply_K(dpp_problem prob, int32_t transpose, const double* x, dou
 dpp_status dpp_apply_K32(dpp_problem prob, int32_t transpose, const float* x, double* y,
                          dpp_stream_t stream);
 
+/*
+ * Matrix-free y = K x (transpose != 0: K^T x), element by element (an
+ * alternative evaluation of Eq. "S4_cg_stiffness_matrix"). No pair values are
+ * read: each node gathers, over its incident cells in increasing cell id, the
+ * element's action from the cell's vertex coordinates, k1, k2, mu and beta.
+ * The cell-level sums it needs are sum u, sum p, grad p_h and div u_h per
+ * network. The gather is deterministic (no atomics). x, y: device
+ * [n_nodes][2d+2] FP64. Agrees with dpp_apply_K up to rounding.
+ */
+dpp_status dpp_apply_K_mf(dpp_problem prob, int32_t transpose, const double* x, double* y,
+                          dpp_stream_t stream);
+
+/* As dpp_apply_K_mf with FP32 geometry, k, x and arithmetic, and FP64 output:
+ * the matrix-free counterpart of dpp_apply_K32. The first call makes FP32
+ * copies of the coordinates and k (kept with the problem). x: device float
+ * [n_nodes][2d+2]; y: device double. */
+dpp_status dpp_apply_K32_mf(dpp_problem prob, int32_t transpose, const float* x, double* y,
+                            dpp_stream_t stream);
+
 /* Copy f (device, [n_nodes][2d+2]) into `f`. */
 dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream);
 
@@ -271,13 +310,33 @@ dpp_status dpp_export_pairs(dpp_problem prob, int32_t* row_ptr, int32_t* col, do
 dpp_status dpp_pc_apply(dpp_problem prob, dpp_pc pc, int32_t transpose, const double* r,
                         double* z, dpp_stream_t stream);
 
-/* Sizes of AMG level `level`: out[0] = rows, out[1] = nnz, out[2] = levels,
- * out[3] = columns of the prolongator P (0 on the coarsest level), out[4] = nnz(P). */
+/* z = Ainv r on the velocity slots (the preconditioner's inner solve of A =
+ * blockdiag(K1_uu, K2_uu) alone: Chebyshev-Jacobi or ILU(0) per
+ * mass_solver); the pressure slots of z are zero. r, z: device
+ * [n_nodes][2d+2], distinct. */
+dpp_status dpp_pc_apply_mass(dpp_problem prob, dpp_pc pc, const double* r, double* z,
+                             dpp_stream_t stream);
+
+/* Number of AMG hierarchies: 1 for the field split (on blockdiag(S_p1, S_p2)),
+ * 2 for the scale split (hierarchy 0 on S_p1, hierarchy 1 on S_p2). */
+dpp_status dpp_pc_hierarchies(dpp_pc pc, int32_t* n);
+
+/* Sizes of level `level` of AMG hierarchy `hierarchy`: out[0] = rows, out[1] =
+ * nnz, out[2] = levels, out[3] = columns of the prolongator P (0 on the
+ * coarsest level), out[4] = nnz(P). dpp_pc_level_sizes is hierarchy 0. */
+dpp_status dpp_pc_hierarchy_level_sizes(dpp_pc pc, int32_t hierarchy, int32_t level,
+                                        int64_t out[5]);
 dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]);
 
-/* Export the CSR matrix of AMG level `level` (level 0 = blockdiag(S_p1, S_p2))
- * and, for level < levels-1, its prolongator P (device arrays sized from
- * dpp_pc_level_sizes). Null P pointers skip P. */
+/* Export the CSR matrix of AMG level `level` of hierarchy `hierarchy` (level 0
+ * = blockdiag(S_p1, S_p2) for the field split; S_p1 or S_p2 for the scale
+ * split) and, for level < levels-1, its prolongator P (device arrays sized
+ * from the level sizes). Null P pointers skip P. dpp_pc_export_level is
+ * hierarchy 0. */
+dpp_status dpp_pc_hierarchy_export_level(dpp_pc pc, int32_t hierarchy, int32_t level,
+                                         int32_t* row_ptr, int32_t* col, double* val,
+                                         int32_t* p_row_ptr, int32_t* p_col, double* p_val,
+                                         dpp_stream_t stream);
 dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32_t* col,
                                double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
                                dpp_stream_t stream);

@@ -27,6 +27,8 @@ solvers for the four-field double porosity/permeability model", 2018):
   * blocks.py: the field-split blocks A, B, C, D and the selfp Schur matrices
     S_p1, S_p2 (Eqs. "S4_sp1", "S4_sp2", Section 4.2), by their definitions on
     the assembled K.
+  * inner.py: the inner solves of the velocity block A: ILU(0) and the
+    Chebyshev-Jacobi polynomial, by their textbook definitions.
   * adjoint.py: the adjoint gradient of J = sum (p1 - p1_obs)^2 with respect to
     the per-cell log k1, log k2 and beta. Cross-checks are complex-step and
     central finite differences.
@@ -41,6 +43,7 @@ from .iterative import solve_field_split_gmres
 from .errors import (p1_mass_matrix, interp_l2_errors, field_rel_errors, field_slices,
                      mass_balance, FIELDS)
 from .blocks import field_split_blocks, selfp_schur
+from .inner import ilu0, ilu0_factors, ilu0_solve, chebyshev_jacobi
 from .adjoint import (objective, objective_grad_x, adjoint_solve, adjoint_gradients,
                       complex_step_gradient, fd_gradient)
 
@@ -49,7 +52,8 @@ __all__ = [
     "assemble", "assemble_rhs", "assemble_rows", "slot_index", "to_nodal", "from_nodal",
     "solve_direct", "solve_dense", "residual", "solve_field_split_gmres",
     "p1_mass_matrix", "interp_l2_errors", "field_rel_errors", "field_slices", "mass_balance",
-    "FIELDS", "field_split_blocks", "selfp_schur",
+    "FIELDS", "field_split_blocks", "selfp_schur", "ilu0", "ilu0_factors", "ilu0_solve",
+    "chebyshev_jacobi",
     "objective", "objective_grad_x", "adjoint_solve", "adjoint_gradients",
     "complex_step_gradient", "fd_gradient",
 ]

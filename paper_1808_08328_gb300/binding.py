@@ -48,6 +48,7 @@ class dpp_pc_opts(C.Structure):
         ("strength_theta", C.c_double), ("cheb_ratio", C.c_double),
         ("use_lumped_diag", C.c_int32), ("precision", C.c_int32),
         ("sell_min_rows", C.c_int32), ("spmv_format", C.c_int32),
+        ("composition", C.c_int32), ("mass_solver", C.c_int32),
     ]
 
 
@@ -56,7 +57,7 @@ class dpp_solve_opts(C.Structure):
         ("rtol", C.c_double), ("restart", C.c_int32), ("max_iters", C.c_int32),
         ("x0_zero", C.c_int32), ("x_memory", C.c_int32), ("check_every", C.c_int32),
         ("inner_rtol", C.c_double), ("wait_budget_cycles", C.c_int64),
-        ("reorth_eta", C.c_double),
+        ("reorth_eta", C.c_double), ("matrix_free", C.c_int32),
     ]
 
 
@@ -98,11 +99,18 @@ _SIGS = {
     "dpp_problem_sizes": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "dpp_apply_K": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "dpp_apply_K32": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "dpp_apply_K_mf": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "dpp_apply_K32_mf": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "dpp_get_rhs": (C.c_int, [_P, _P, _P]),
     "dpp_export_pairs": (C.c_int, [_P, _P, _P, _P, _P]),
     "dpp_pc_apply": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
     "dpp_pc_level_sizes": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64)]),
     "dpp_pc_export_level": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+    "dpp_pc_hierarchies": (C.c_int, [_P, C.POINTER(C.c_int32)]),
+    "dpp_pc_apply_mass": (C.c_int, [_P, _P, _P, _P, _P]),
+    "dpp_pc_hierarchy_level_sizes": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
+    "dpp_pc_hierarchy_export_level": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P,
+                                                _P]),
     "dpp_adjoint_gradients_noalloc": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "dpp_release_cached_memory": (C.c_int, []),
     "dpp_launch_count": (C.c_int64, []),
@@ -263,6 +271,15 @@ def dpp_apply_K32(prob: int, transpose: bool, x, y, stream: int = 0) -> None:
     _check(load().dpp_apply_K32(prob, 1 if transpose else 0, _ptr(x), _ptr(y), stream or None))
 
 
+def dpp_apply_K_mf(prob: int, transpose: bool, x, y, stream: int = 0) -> None:
+    _check(load().dpp_apply_K_mf(prob, 1 if transpose else 0, _ptr(x), _ptr(y), stream or None))
+
+
+def dpp_apply_K32_mf(prob: int, transpose: bool, x, y, stream: int = 0) -> None:
+    _check(load().dpp_apply_K32_mf(prob, 1 if transpose else 0, _ptr(x), _ptr(y),
+                                   stream or None))
+
+
 def dpp_get_rhs(prob: int, f, stream: int = 0) -> None:
     _check(load().dpp_get_rhs(prob, _ptr(f), stream or None))
 
@@ -275,16 +292,27 @@ def dpp_pc_apply(prob: int, pc: int, transpose: bool, r, z, stream: int = 0) -> 
     _check(load().dpp_pc_apply(prob, pc, 1 if transpose else 0, _ptr(r), _ptr(z), stream or None))
 
 
-def dpp_pc_level_sizes(pc: int, level: int) -> dict:
+def dpp_pc_apply_mass(prob: int, pc: int, r, z, stream: int = 0) -> None:
+    _check(load().dpp_pc_apply_mass(prob, pc, _ptr(r), _ptr(z), stream or None))
+
+
+def dpp_pc_hierarchies(pc: int) -> int:
+    n = C.c_int32(0)
+    _check(load().dpp_pc_hierarchies(pc, C.byref(n)))
+    return int(n.value)
+
+
+def dpp_pc_level_sizes(pc: int, level: int, hierarchy: int = 0) -> dict:
     out = (C.c_int64 * 5)()
-    _check(load().dpp_pc_level_sizes(pc, level, out))
+    _check(load().dpp_pc_hierarchy_level_sizes(pc, hierarchy, level, out))
     return {"rows": out[0], "nnz": out[1], "levels": out[2], "p_cols": out[3], "p_nnz": out[4]}
 
 
 def dpp_pc_export_level(pc: int, level: int, row_ptr, col, val, p_row_ptr=None, p_col=None,
-                        p_val=None, stream: int = 0) -> None:
-    _check(load().dpp_pc_export_level(pc, level, _ptr(row_ptr), _ptr(col), _ptr(val),
-                                      _ptr(p_row_ptr), _ptr(p_col), _ptr(p_val), stream or None))
+                        p_val=None, stream: int = 0, hierarchy: int = 0) -> None:
+    _check(load().dpp_pc_hierarchy_export_level(pc, hierarchy, level, _ptr(row_ptr), _ptr(col),
+                                                _ptr(val), _ptr(p_row_ptr), _ptr(p_col),
+                                                _ptr(p_val), stream or None))
 
 
 def dpp_adjoint_gradients_noalloc(prob: int, x, lam, g1, g2, gb, stream: int = 0) -> None:

@@ -22,7 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
 SOURCES = ["scan.cu", "assemble.cu", "spmv.cu", "blas.cu", "spgemm.cu", "amg.cu", "pc.cu",
-           "solver.cu", "adjoint.cu", "batched.cu", "abi.cu", "noalloc.cu"]
+           "solver.cu", "adjoint.cu", "batched.cu", "abi.cu", "noalloc.cu", "matfree.cu",
+           "ilu.cu"]
 
 
 def nvcc() -> str:

@@ -16,6 +16,7 @@ namespace dpp {
 void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s);
 void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
               cudaStream_t s);
+void pc_apply_mass(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, cudaStream_t s);
 dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, const double* rhs,
                   double* x, bool transpose, dpp_solve_info& info, cudaStream_t s,
                   HostScratch& hs);
@@ -215,6 +216,8 @@ void dpp_pc_opts_default(dpp_pc_opts* o) {
     o->precision = DPP_FP64;
     o->sell_min_rows = 0;
     o->spmv_format = 0;
+    o->composition = 0;
+    o->mass_solver = 0;
 }
 
 void dpp_solve_opts_default(dpp_solve_opts* o) {
@@ -228,6 +231,7 @@ void dpp_solve_opts_default(dpp_solve_opts* o) {
     o->inner_rtol = 1e-4;
     o->wait_budget_cycles = 0;
     o->reorth_eta = 0.1;
+    o->matrix_free = 0;
 }
 
 const char* dpp_status_string(int32_t s) {
@@ -300,6 +304,10 @@ dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t 
         require(o.precision == DPP_FP64 || o.precision == DPP_MIXED_FP32_FP64, "bad precision");
         require(o.sell_min_rows >= 0, "sell_min_rows >= 0");
         require(o.spmv_format >= 0 && o.spmv_format <= 2, "spmv_format in {0,1,2}");
+        require(o.composition == kFieldSplit || o.composition == kScaleSplit,
+                "composition in {0 (field split), 1 (scale split)}");
+        require(o.mass_solver == 0 || o.mass_solver == 1,
+                "mass_solver in {0 (Chebyshev-Jacobi), 1 (ILU(0))}");
         cudaStream_t s = (cudaStream_t)stream;
         auto* h = new dpp_pc_s();
         try {
@@ -335,10 +343,13 @@ static dpp_status solve_common(const char* name, dpp_problem prob, dpp_pc pc,
         require(o.restart >= 1 && o.restart <= 64, "restart in [1,64]");
         require(o.max_iters >= 1, "max_iters >= 1");
         require(o.x_memory == DPP_MEM_DEVICE || o.x_memory == DPP_MEM_HOST, "bad x_memory");
+        require(o.matrix_free == 0 || o.matrix_free == 1, "matrix_free in {0,1}");
+        if (o.matrix_free && pc->impl.precision == DPP_MIXED_FP32_FP64)
+            matrix_free_prepare32(prob->impl, (cudaStream_t)stream);
         const ProblemImpl& P = prob->impl;
         cudaStream_t s = (cudaStream_t)stream;
         const int64_t n = P.n_nodes * P.ns;
-        inf.levels = (int)pc->impl.levels.size();
+        inf.levels = (int)pc->impl.amg[0].levels.size();
         inf.ms_assemble = P.ms_assemble;
         inf.ms_setup = pc->impl.ms_setup;
         EventTimer t(s);
@@ -495,7 +506,7 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
             inf.ms_assemble = ms_asm;
             inf.ms_setup = ms_setup;
             inf.ms_solve = ms_solve;
-            inf.levels = (int)pc.impl.levels.size();
+            inf.levels = (int)pc.impl.amg[0].levels.size();
             if (codes[i]) {
                 inf.status = codes[i];
                 worst = (dpp_status)codes[i];
@@ -577,6 +588,27 @@ dpp_status dpp_apply_K32(dpp_problem prob, int32_t transpose, const float* x, do
     });
 }
 
+dpp_status dpp_apply_K_mf(dpp_problem prob, int32_t transpose, const double* x, double* y,
+                          dpp_stream_t stream) {
+    return guarded("dpp_apply_K_mf", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
+        require(prob && x && y && x != y, "null or aliased argument");
+        apply_K_mf(prob->impl, x, y, transpose != 0, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_apply_K32_mf(dpp_problem prob, int32_t transpose, const float* x, double* y,
+                            dpp_stream_t stream) {
+    return guarded("dpp_apply_K32_mf", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
+        require(prob && x && y, "null argument");
+        matrix_free_prepare32(prob->impl, (cudaStream_t)stream);
+        apply_K32_mf(prob->impl, x, y, transpose != 0, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
 dpp_status dpp_get_rhs(dpp_problem prob, double* f, dpp_stream_t stream) {
     return guarded("dpp_get_rhs", [&]() -> dpp_status {
         StreamScope scope_((cudaStream_t)stream);
@@ -619,10 +651,31 @@ dpp_status dpp_pc_apply(dpp_problem prob, dpp_pc pc, int32_t transpose, const do
     });
 }
 
-dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]) {
+dpp_status dpp_pc_apply_mass(dpp_problem prob, dpp_pc pc, const double* r, double* z,
+                             dpp_stream_t stream) {
+    return guarded("dpp_pc_apply_mass", [&]() -> dpp_status {
+        StreamScope scope_((cudaStream_t)stream);
+        require(prob && pc && r && z && r != z, "null or aliased argument");
+        require(pc->owner == prob, "pc was built for a different problem");
+        pc_apply_mass(prob->impl, pc->impl, r, z, (cudaStream_t)stream);
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_pc_hierarchies(dpp_pc pc, int32_t* n) {
+    return guarded("dpp_pc_hierarchies", [&]() -> dpp_status {
+        require(pc && n, "null argument");
+        *n = pc->impl.n_amg;
+        return DPP_OK;
+    });
+}
+
+dpp_status dpp_pc_hierarchy_level_sizes(dpp_pc pc, int32_t hierarchy, int32_t level,
+                                        int64_t out[5]) {
     return guarded("dpp_pc_level_sizes", [&]() -> dpp_status {
         require(pc && out, "null argument");
-        const auto& L = pc->impl.levels;
+        require(hierarchy >= 0 && hierarchy < pc->impl.n_amg, "hierarchy out of range");
+        const auto& L = pc->impl.amg[hierarchy].levels;
         require(level >= 0 && level < (int)L.size(), "level out of range");
         out[0] = L[level].A.n_rows;
         out[1] = L[level].A.nnz;
@@ -633,13 +686,19 @@ dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]) {
     });
 }
 
-dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32_t* col,
-                               double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
-                               dpp_stream_t stream) {
+dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]) {
+    return dpp_pc_hierarchy_level_sizes(pc, 0, level, out);
+}
+
+dpp_status dpp_pc_hierarchy_export_level(dpp_pc pc, int32_t hierarchy, int32_t level,
+                                         int32_t* row_ptr, int32_t* col, double* val,
+                                         int32_t* p_row_ptr, int32_t* p_col, double* p_val,
+                                         dpp_stream_t stream) {
     return guarded("dpp_pc_export_level", [&]() -> dpp_status {
         StreamScope scope_((cudaStream_t)stream);
         require(pc && row_ptr && col && val, "null argument");
-        const auto& L = pc->impl.levels;
+        require(hierarchy >= 0 && hierarchy < pc->impl.n_amg, "hierarchy out of range");
+        const auto& L = pc->impl.amg[hierarchy].levels;
         require(level >= 0 && level < (int)L.size(), "level out of range");
         cudaStream_t s = (cudaStream_t)stream;
         const Csr& A = L[level].A;
@@ -658,6 +717,13 @@ dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32
         DPP_CK(cudaStreamSynchronize(s));
         return DPP_OK;
     });
+}
+
+dpp_status dpp_pc_export_level(dpp_pc pc, int32_t level, int32_t* row_ptr, int32_t* col,
+                               double* val, int32_t* p_row_ptr, int32_t* p_col, double* p_val,
+                               dpp_stream_t stream) {
+    return dpp_pc_hierarchy_export_level(pc, 0, level, row_ptr, col, val, p_row_ptr, p_col, p_val,
+                                         stream);
 }
 
 }  // extern "C"

@@ -650,7 +650,7 @@ std::vector<std::pair<int, int>> diag_blocks(const Csr& A, cudaStream_t s) {
 // Inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), block
 // by block in compact storage. Blocks of at most kGjSmall rows are inverted
 // one CTA each in shared memory, in one launch; larger ones pivot by pivot.
-void block_inverse(PcImpl& pc, const Csr& A, cudaStream_t s) {
+void block_inverse(Amg& pc, const Csr& A, cudaStream_t s) {
     const int64_t n = A.n_rows;
     const auto blocks = diag_blocks(A, s);
     std::vector<int> blk(3 * blocks.size()), rowblk(n), small;
@@ -702,10 +702,8 @@ void block_inverse(PcImpl& pc, const Csr& A, cudaStream_t s) {
 
 }  // namespace
 
-void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s) {
+void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScratch& hs) {
     ProfScope prof_all("setup_amg", s, 0);
-    auto& hs = pc.hs;
-    const dpp_pc_opts& o = pc.opts;
     pc.levels.clear();
     pc.levels.emplace_back();
     pc.levels[0].A = std::move(A0);
@@ -872,10 +870,10 @@ template <> double* lv<double>(DBuf<double>& d, DBuf<float>&) { return d.get(); 
 template <> float* lv<float>(DBuf<double>&, DBuf<float>& f) { return f.get(); }
 
 template <class T>
-void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s,
+void cheb_smooth(const dpp_pc_opts& o, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s,
                  const char* fam = nullptr) {
-    const int deg = std::max(1, pc.opts.cheb_degree_amg);
-    const double hi = 1.1 * L.lmax, lo = L.lmax / pc.opts.cheb_ratio;
+    const int deg = std::max(1, o.cheb_degree_amg);
+    const double hi = 1.1 * L.lmax, lo = L.lmax / o.cheb_ratio;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     const int64_t n = L.A.n_rows;
     T* tmp = lv<T>(L.xt, L.xt32);
@@ -915,7 +913,7 @@ void cheb_smooth(const PcImpl& pc, Level& L, const T* b, T* x, bool zero_init, c
 }
 
 template <class T>
-void vcycle_level(PcImpl& pc, size_t l, const T* b, T* x, cudaStream_t s) {
+void vcycle_level(Amg& pc, const dpp_pc_opts& o, size_t l, const T* b, T* x, cudaStream_t s) {
     Level& L = pc.levels[l];
     if (l + 1 == pc.levels.size()) {
         const int64_t n = pc.coarse_n;
@@ -933,12 +931,12 @@ void vcycle_level(PcImpl& pc, size_t l, const T* b, T* x, cudaStream_t s) {
     const char* fam = (l == 0) ? (f64 ? "amg_spmv_L0" : "amg_spmv_L0_fp32")
                                : (f64 ? "amg_spmv_Lc" : "amg_spmv_Lc_fp32");
     const char* fam_pr = f64 ? "amg_spmv_PR" : "amg_spmv_PR_fp32";
-    cheb_smooth<T>(pc, L, b, x, true, s, fam);
+    cheb_smooth<T>(o, L, b, x, true, s, fam);
     spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
     spmv_lanes<0, T>(L.lanes_R, L.R, r, nullptr, cb, s, fam_pr);
-    vcycle_level<T>(pc, l + 1, cb, cx, s);
+    vcycle_level<T>(pc, o, l + 1, cb, cx, s);
     spmv_lanes<2, T>(L.lanes_P, L.P, cx, nullptr, x, s, fam_pr);
-    cheb_smooth<T>(pc, L, b, x, false, s, fam);
+    cheb_smooth<T>(o, L, b, x, false, s, fam);
 }
 
 void to_f32(const DBuf<double>& in, DBuf<float>& out, cudaStream_t s) {
@@ -1047,7 +1045,7 @@ int tune_lanes(const Csr& A, const T* x, const T* b, T* y, int kind, cudaStream_
 }
 
 template <class T>
-void tune_levels(PcImpl& pc, cudaStream_t s) {
+void tune_levels(Amg& pc, const dpp_pc_opts& o, cudaStream_t s) {
     for (size_t l = 0; l < pc.levels.size(); ++l) {
         Level& L = pc.levels[l];
         T* x = lv<T>(L.x, L.x32);
@@ -1055,7 +1053,7 @@ void tune_levels(PcImpl& pc, cudaStream_t s) {
         T* r = lv<T>(L.r, L.r32);
         DPP_CK(cudaMemsetAsync(x, 0, L.A.n_rows * sizeof(T), s));
         DPP_CK(cudaMemsetAsync(b, 0, L.A.n_rows * sizeof(T), s));
-        if (pc.opts.spmv_format == 2 && L.A.has_sell()) L.lanes = 0;  // SELL-32 as asked
+        if (o.spmv_format == 2 && L.A.has_sell()) L.lanes = 0;  // SELL-32 as asked
         else L.lanes = tune_lanes<1, T>(L.A, x, b, r, 0, s);
         if (l + 1 < pc.levels.size()) {
             Level& C = pc.levels[l + 1];
@@ -1063,7 +1061,7 @@ void tune_levels(PcImpl& pc, cudaStream_t s) {
             T* cb = lv<T>(C.b, C.b32);
             DPP_CK(cudaMemsetAsync(cx, 0, C.A.n_rows * sizeof(T), s));
             L.lanes_R = tune_lanes<0, T>(L.R, r, nullptr, cb, 1, s);
-            if (pc.opts.spmv_format == 2 && L.P.has_sell()) L.lanes_P = 0;
+            if (o.spmv_format == 2 && L.P.has_sell()) L.lanes_P = 0;
             else L.lanes_P = tune_lanes<2, T>(L.P, cx, nullptr, x, 2, s);
         }
     }
@@ -1072,13 +1070,13 @@ void tune_levels(PcImpl& pc, cudaStream_t s) {
 
 }  // namespace
 
-void amg_tune(PcImpl& pc, cudaStream_t s) {
+void amg_tune(Amg& pc, const dpp_pc_opts& o, int precision, cudaStream_t s) {
     ProfScope pr("setup_tune", s, 0);
-    if (pc.precision == DPP_MIXED_FP32_FP64) tune_levels<float>(pc, s);
-    else tune_levels<double>(pc, s);
+    if (precision == DPP_MIXED_FP32_FP64) tune_levels<float>(pc, o, s);
+    else tune_levels<double>(pc, o, s);
 }
 
-void amg_make_fp32(PcImpl& pc, cudaStream_t s) {
+void amg_make_fp32(Amg& pc, cudaStream_t s) {
     for (size_t l = 0; l < pc.levels.size(); ++l) {
         Level& L = pc.levels[l];
         to_f32(L.A.val, L.A.val32, s);
@@ -1100,10 +1098,10 @@ void amg_make_fp32(PcImpl& pc, cudaStream_t s) {
 }
 
 template <class T>
-void amg_vcycle(PcImpl& pc, const T* b, T* x, cudaStream_t s) {
-    vcycle_level<T>(pc, 0, b, x, s);
+void amg_vcycle(Amg& h, const dpp_pc_opts& o, const T* b, T* x, cudaStream_t s) {
+    vcycle_level<T>(h, o, 0, b, x, s);
 }
-template void amg_vcycle<double>(PcImpl&, const double*, double*, cudaStream_t);
-template void amg_vcycle<float>(PcImpl&, const float*, float*, cudaStream_t);
+template void amg_vcycle<double>(Amg&, const dpp_pc_opts&, const double*, double*, cudaStream_t);
+template void amg_vcycle<float>(Amg&, const dpp_pc_opts&, const float*, float*, cudaStream_t);
 
 }  // namespace dpp

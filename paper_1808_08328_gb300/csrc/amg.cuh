@@ -38,14 +38,15 @@ void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs);
 void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
                  HostScratch& hs);
 
-void amg_setup(PcImpl& pc, Csr&& A0, cudaStream_t s);
+// Build one hierarchy on A0 (SPD) with the options' coarsening parameters.
+void amg_setup(Amg& h, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScratch& hs);
 // FP32 copies of every level (values, 1/diag, work vectors) for the mixed mode.
-void amg_make_fp32(PcImpl& pc, cudaStream_t s);
-// Autotune the CSR SpMV lanes of every level matrix for the pc's precision.
-void amg_tune(PcImpl& pc, cudaStream_t s);
+void amg_make_fp32(Amg& h, cudaStream_t s);
+// Autotune the SpMV format / CSR lanes of every level for `precision`.
+void amg_tune(Amg& h, const dpp_pc_opts& o, int precision, cudaStream_t s);
 // x = (one V-cycle) b on level 0; b is not modified. T = double uses the FP64
 // hierarchy; T = float the FP32 copies (the coarsest solve stays FP64).
 template <class T>
-void amg_vcycle(PcImpl& pc, const T* b, T* x, cudaStream_t s);
+void amg_vcycle(Amg& h, const dpp_pc_opts& o, const T* b, T* x, cudaStream_t s);
 
 }  // namespace dpp

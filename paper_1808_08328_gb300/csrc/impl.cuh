@@ -60,6 +60,8 @@ struct ProblemImpl {
     int n_inst = 1;
     std::vector<int64_t> inst_node_off, inst_cell_off;
     std::vector<double> inst_mu, inst_beta;
+    // FP32 copies for the matrix-free FP32 operator (made on first use)
+    DBuf<float> coords32, kk32, cell_mu_beta32;
     DBuf<double> geo;       // [n_cells][GeoLayout<dim>::stride]
     DBuf<double> kk;        // [n_cells][2]: k1, k2
     DBuf<double> ccoef;     // [n_cells][kCellCoef]: factors of the pair values
@@ -83,18 +85,40 @@ struct Level {
     DBuf<float> x32, xt32, b32, r32, d32;
 };
 
-struct PcImpl {
-    int dim = 0;
-    int64_t n_nodes = 0;
-    int precision = DPP_FP64;
-    dpp_pc_opts opts{};
-    double mass_lmin = 0.5, mass_lmax = 2.0;  // Wathen bounds of D^-1 M (TRI: [1/2, 2], TET: [1/2, 5/2])
+// One smoothed-aggregation hierarchy: its level matrices, transfers, work
+// vectors and the inverse of its coarsest matrix.
+struct Amg {
     std::vector<Level> levels;
     DBuf<double> coarse_inv;  // inverse of the coarsest matrix: its diagonal blocks, row-major
     DBuf<int> coarse_blk;     // per block: first row, size, offset into coarse_inv
     DBuf<int> coarse_rowblk;  // block of each coarsest row
     int64_t coarse_n = 0;
     bool symmetric = false;   // level-0 matrix found symmetric: Galerkin products mirrored
+};
+
+// ILU(0) of the two velocity mass blocks on the node-pair pattern (ilu.cu).
+struct MassIlu {
+    DBuf<double> lu;          // [n_pairs][2]: packed L (unit lower) and U factors, per network
+    DBuf<float> lu32;         // FP32 copy (mixed precision)
+    DBuf<int> dpos;           // position of the diagonal in each row
+    std::vector<int> lower_ptr, upper_ptr;  // level boundaries (host)
+    DBuf<int> lower_rows, upper_rows;       // rows ordered by level
+};
+
+// Preconditioner compositions of Section 4 (values of dpp_pc_opts::composition).
+enum : int { kFieldSplit = 0, kScaleSplit = 1 };
+
+struct PcImpl {
+    int dim = 0;
+    int64_t n_nodes = 0;
+    int precision = DPP_FP64;
+    dpp_pc_opts opts{};
+    double mass_lmin = 0.5, mass_lmax = 2.0;  // Wathen bounds of D^-1 M (TRI: [1/2, 2], TET: [1/2, 5/2])
+    // Method 2 (field split): one hierarchy on blockdiag(S_p1, S_p2) (n_amg = 1).
+    // Method 1 (scale split): amg[i] on S^(i+1)_p alone, one per network (n_amg = 2).
+    Amg amg[2];
+    int n_amg = 1;
+    MassIlu ilu;              // mass_solver = 1 only
     // preconditioner work vectors (node-interleaved, n_nodes * ns)
     DBuf<double> yu, su, tmp, dcheb;
     DBuf<double> tp, yp;      // split pressures [2][n_nodes]

@@ -15,6 +15,12 @@ void apply_K(const ProblemImpl& P, const double* x, double* y, const double* b, 
              bool use32, cudaStream_t s);
 // y = K32 x with FP32 values, FP32 x and FP32 arithmetic, FP64 output.
 void apply_K32(const ProblemImpl& P, const float* x, double* y, bool transpose, cudaStream_t s);
+// Matrix-free y = K x (transpose: K^T x) from the cells' geometry and k, with no
+// assembled values (matfree.cu): FP64 throughout, or FP32 geometry, k, x and
+// arithmetic with FP64 output (after matrix_free_prepare32).
+void apply_K_mf(const ProblemImpl& P, const double* x, double* y, bool transpose, cudaStream_t s);
+void apply_K32_mf(const ProblemImpl& P, const float* x, double* y, bool transpose, cudaStream_t s);
+void matrix_free_prepare32(ProblemImpl& P, cudaStream_t s);
 // One Chebyshev step on the velocity block A = blockdiag(K1_uu, K2_uu), in type T
 // (values of the same type). first: x_out = c2 * Dinv r, d = x_out. else:
 // res = r - A x_in; d = c1 d + c2 Dinv res; x_out = x_in + d. Only u slots change.
@@ -29,6 +35,11 @@ void apply_C_resid(const ProblemImpl& P, const T* r, const T* yu, T* tp, bool tr
 template <class T>
 void apply_B_resid(const ProblemImpl& P, const T* r, const T* yp, T* su, bool transpose,
                    cudaStream_t s);
+// ILU(0) of the velocity mass blocks (ilu.cu): factor at setup; apply writes
+// target's velocity slots = (L U)^-1 r's velocity slots (target != r).
+void mass_ilu_setup(const ProblemImpl& P, PcImpl& pc, cudaStream_t s);
+template <class T>
+void mass_ilu_apply(const ProblemImpl& P, const PcImpl& pc, const T* r, T* target, cudaStream_t s);
 // mdiag[a][net] = 1 / m_net(a, a) (or the row sum when lumped)
 void mass_diag_inv(const ProblemImpl& P, double* mdiag, bool lumped, cudaStream_t s);
 // z_p(net)[a] = yp[net][a] (copy split pressures into interleaved p slots)

@@ -111,11 +111,13 @@ dpp_status fgmres(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, con
                 if (mixed) {
                     float* zj = Z32 + (size_t)j * n;
                     pc_apply32(P, pc, vj, zj, transpose, s);
-                    apply_K32(P, zj, W.w.get(), transpose, s);
+                    if (o.matrix_free) apply_K32_mf(P, zj, W.w.get(), transpose, s);
+                    else apply_K32(P, zj, W.w.get(), transpose, s);
                 } else {
                     double* zj = Z + (size_t)j * n;
                     pc_apply(P, pc, vj, zj, transpose, s);
-                    apply_K(P, zj, W.w.get(), nullptr, transpose, false, s);
+                    if (o.matrix_free) apply_K_mf(P, zj, W.w.get(), transpose, s);
+                    else apply_K(P, zj, W.w.get(), nullptr, transpose, false, s);
                 }
             }
             double* hd = W.dscal.get();

@@ -152,6 +152,18 @@ class DPPSystem:
         B.dpp_apply_K32(self.prob, transpose, x, y, _stream(self.device))
         return y
 
+    def apply_K_mf(self, x: torch.Tensor, transpose: bool = False) -> torch.Tensor:
+        x = x.to(self.device, torch.float64).contiguous()
+        y = torch.empty_like(x)
+        B.dpp_apply_K_mf(self.prob, transpose, x, y, _stream(self.device))
+        return y
+
+    def apply_K32_mf(self, x: torch.Tensor, transpose: bool = False) -> torch.Tensor:
+        x = x.to(self.device, torch.float32).contiguous()
+        y = torch.empty(x.shape, dtype=torch.float64, device=self.device)
+        B.dpp_apply_K32_mf(self.prob, transpose, x, y, _stream(self.device))
+        return y
+
     def rhs(self) -> torch.Tensor:
         f = torch.empty((self.n_nodes, self.ns), dtype=torch.float64, device=self.device)
         B.dpp_get_rhs(self.prob, f, _stream(self.device))
@@ -174,8 +186,17 @@ class DPPSystem:
         B.dpp_pc_apply(self.prob, self.pc, transpose, r, z, _stream(self.device))
         return z
 
-    def level(self, level: int, with_p: bool = True):
-        s = B.dpp_pc_level_sizes(self.pc, level)
+    def pc_apply_mass(self, r: torch.Tensor) -> torch.Tensor:
+        r = r.to(self.device, torch.float64).contiguous()
+        z = torch.empty_like(r)
+        B.dpp_pc_apply_mass(self.prob, self.pc, r, z, _stream(self.device))
+        return z
+
+    def hierarchies(self) -> int:
+        return B.dpp_pc_hierarchies(self.pc)
+
+    def level(self, level: int, with_p: bool = True, hierarchy: int = 0):
+        s = B.dpp_pc_level_sizes(self.pc, level, hierarchy)
         dev = self.device
         rp = torch.empty(s["rows"] + 1, dtype=torch.int32, device=dev)
         col = torch.empty(max(s["nnz"], 1), dtype=torch.int32, device=dev)
@@ -185,7 +206,8 @@ class DPPSystem:
             prp = torch.empty(s["rows"] + 1, dtype=torch.int32, device=dev)
             pcol = torch.empty(s["p_nnz"], dtype=torch.int32, device=dev)
             pval = torch.empty(s["p_nnz"], dtype=torch.float64, device=dev)
-        B.dpp_pc_export_level(self.pc, level, rp, col, val, prp, pcol, pval, _stream(dev))
+        B.dpp_pc_export_level(self.pc, level, rp, col, val, prp, pcol, pval, _stream(dev),
+                              hierarchy=hierarchy)
         return s, (rp, col[:s["nnz"]], val[:s["nnz"]]), (prp, pcol, pval)
 
     def close(self):

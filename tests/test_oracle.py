@@ -389,6 +389,67 @@ def test_mass_balance_invariant(dim, n, gb):
     assert abs(b1) < 1e-11 * scale and abs(b2) < 1e-11 * scale
 
 
+def _weighted_mass(dim, n, seed):
+    m = inputs.unit_mesh(dim, n)
+    geom = geometry(m.coords, m.cells)
+    lam, wq = cell_rule(dim)
+    wts = np.exp(inputs.rng(seed).normal(0, 1, m.n_cells))
+    Me = np.einsum("c,c,q,qa,qb->cab", wts, geom.vol, wq, lam, lam)
+    nv = dim + 1
+    r = np.repeat(m.cells, nv, axis=1).ravel()
+    c = np.tile(m.cells, (1, nv)).ravel()
+    return sp.csr_matrix((Me.ravel(), (r, c)), shape=(m.n_nodes,) * 2)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 3)])
+def test_ilu0_reproduces_the_matrix_on_its_pattern(dim, n):
+    # the defining property of ILU(0): (L U)_ij = A_ij wherever A has an entry
+    M = _weighted_mass(dim, n, 12)
+    LU = oracle.ilu0(M)
+    L, U = oracle.ilu0_factors(LU)
+    assert np.array_equal(LU.indptr, sp.csr_matrix(M).indptr)
+    prod = (L @ U).tocsr()
+    Mc = sp.csr_matrix(M)
+    rows = np.repeat(np.arange(Mc.shape[0]), np.diff(Mc.indptr))
+    assert np.allclose(np.asarray(prod[rows, Mc.indices]).ravel(), Mc.data, rtol=1e-13, atol=0)
+    # the product has fill outside the pattern, so ILU(0) is not the exact LU here
+    assert (abs(prod - Mc) > 1e-12 * abs(Mc).max()).nnz > 0
+
+
+def test_ilu0_of_a_tridiagonal_matrix_is_the_exact_lu():
+    # a 1D P1 mass matrix with random cell weights: LU has no fill, so ILU(0) is exact
+    n = 40
+    w = np.exp(inputs.rng(13).normal(0, 1, n - 1))
+    h = 1.0 / (n - 1)
+    main = np.zeros(n)
+    main[:-1] += 2 * w * h / 6
+    main[1:] += 2 * w * h / 6
+    T = sp.diags([w * h / 6, main, w * h / 6], [-1, 0, 1], format="csr")
+    r = inputs.rng(14).standard_normal(n)
+    x = oracle.ilu0_solve(oracle.ilu0(T), r)
+    assert np.allclose(x, np.linalg.solve(T.toarray(), r), rtol=1e-12, atol=1e-12 * abs(x).max())
+
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (3, 2)])
+def test_chebyshev_jacobi_degree_one_and_error_bound(dim, n):
+    M = _weighted_mass(dim, n, 15)
+    r = inputs.rng(16).standard_normal(M.shape[0])
+    lo, hi = 0.5, 0.5 * (dim + 2)                     # Wathen's interval
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    # degree 1 is the scaled Jacobi step D^-1 r / theta
+    x1 = oracle.chebyshev_jacobi(M, r, 1, lo, hi)
+    assert np.allclose(x1, r / M.diagonal() / theta, rtol=1e-12)
+    # degree k: the error in the M-norm is at most 1 / T_k(theta/delta) of the exact solve's norm
+    xs = np.linalg.solve(M.toarray(), r)
+    Md = M.toarray()
+    nrm = lambda e: np.sqrt(e @ Md @ e)
+    for k in (2, 3, 5):
+        xk = oracle.chebyshev_jacobi(M, r, k, lo, hi)
+        bound = 1.0 / np.cosh(k * np.arccosh(theta / delta))
+        assert nrm(xk - xs) <= bound * nrm(xs) * (1 + 1e-10)
+        assert nrm(xk - xs) >= 1e-6 * bound * nrm(xs)  # an approximation, not the exact solve
+
+
 @pytest.mark.parametrize("dim,n,gb", [(2, 12, 0.0), (3, 5, 0.0), (3, 4, 1.2)])
 def test_field_split_gmres_reaches_the_direct_solution(dim, n, gb):
     # The oracle for meshes too large to factor: flexible GMRES to a true
