@@ -8,7 +8,8 @@ Node numbering is lexicographic with x fastest. The DoF count of the
 four-field P1 system on these meshes is (N+1)^2 * 6 in 2D and (N+1)^3 * 8 in
 3D. These are the CG-VMS TRI and TET columns of the paper's h-size vs DoF
 tables (Section 5.1, Table "2D h-size vs DoF"; Section 5.2, Table "h-size vs
-DoF").
+DoF"). The Q1 meshes (QUAD, HEX: Table "ELE_level_discretization") have the
+same nodes, so the same counts (the QUAD and HEX columns of those tables).
 """
 from __future__ import annotations
 
@@ -22,9 +23,10 @@ import numpy as np
 class Mesh:
     dim: int
     coords: np.ndarray      # float64 [n_nodes, dim]
-    cells: np.ndarray       # int32 [n_cells, dim+1]
-    bfacets: np.ndarray     # int32 [n_bfacets, dim], the facets on the boundary
+    cells: np.ndarray       # int32 [n_cells, dim+1] (simplices) or [n_cells, 2^dim] (Q1)
+    bfacets: np.ndarray     # int32 [n_bfacets, dim] or [n_bfacets, 2^(dim-1)]: boundary facets
     n: int                  # cells per edge of the unit square / cube
+    kind: str = "simplex"   # "simplex" (P1 triangles, tetrahedra) or "q1" (quads, hexahedra)
 
     @property
     def n_nodes(self) -> int:
@@ -137,7 +139,64 @@ def disc_wheel(sectors: int, rings: int) -> Mesh:
     return Mesh(2, coords, cells, boundary_facets(cells, 2), rings)
 
 
-def unit_mesh(dim: int, n: int) -> Mesh:
+def tensor_facets(dim: int):
+    """Local vertex lists of the 2*dim facets of a tensor-ordered Q1 cell.
+
+    Vertex v of the cell sits at the corner whose coordinate bits are
+    (v & 1, (v >> 1) & 1, (v >> 2) & 1). The facet on side s of axis k holds
+    the vertices with bit k equal to s, in increasing order. That order is
+    itself the tensor order of the facet.
+    """
+    nv = 1 << dim
+    return [[v for v in range(nv) if ((v >> k) & 1) == side]
+            for k in range(dim) for side in (0, 1)]
+
+
+def boundary_facets_q1(cells: np.ndarray, dim: int) -> np.ndarray:
+    """Facets of tensor-ordered Q1 cells that belong to exactly one cell."""
+    faces = np.concatenate([cells[:, f] for f in tensor_facets(dim)], axis=0).astype(np.int64)
+    srt = np.sort(faces, axis=1)
+    key = np.zeros(srt.shape[0], dtype=np.int64)
+    for c in range(srt.shape[1]):
+        key = key * (1 << 21) + srt[:, c]
+    uniq, idx, counts = np.unique(key, return_index=True, return_counts=True)
+    return faces[idx[counts == 1]].astype(np.int32)
+
+
+def unit_square_quad(n: int) -> Mesh:
+    """N x N squares on [0,1]^2 as Q1 cells (vertices in tensor order)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    m = n + 1
+    i, j = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    coords = np.stack([i.ravel() / n, j.ravel() / n], axis=1).astype(np.float64)
+    ci, cj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    n00 = (ci + m * cj).ravel()
+    cells = np.stack([n00, n00 + 1, n00 + m, n00 + m + 1], axis=1).astype(np.int32)
+    return Mesh(2, coords, cells, boundary_facets_q1(cells, 2), n, kind="q1")
+
+
+def unit_cube_hex(n: int) -> Mesh:
+    """N^3 cubes on [0,1]^3 as Q1 hexahedra (vertices in tensor order)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    m = n + 1
+    k, j, i = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    coords = np.stack([i.ravel() / n, j.ravel() / n, k.ravel() / n], axis=1).astype(np.float64)
+    ck, cj, ci = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = (ci + m * (cj + m * ck)).ravel()
+    offs = [(v & 1) + m * ((v >> 1) & 1) + m * m * ((v >> 2) & 1) for v in range(8)]
+    cells = np.stack([base + o for o in offs], axis=1).astype(np.int32)
+    return Mesh(3, coords, cells, boundary_facets_q1(cells, 3), n, kind="q1")
+
+
+def unit_mesh(dim: int, n: int, kind: str = "simplex") -> Mesh:
+    if kind == "q1":
+        if dim == 2:
+            return unit_square_quad(n)
+        if dim == 3:
+            return unit_cube_hex(n)
+        raise ValueError("dim must be 2 or 3")
     if dim == 2:
         return unit_square_tri(n)
     if dim == 3:

@@ -48,21 +48,22 @@ class Problem:
         return replace(self, **kw)
 
 
-def mms_problem(dim: int, n: int, prm: MMSParams = PAPER) -> Problem:
-    mesh = unit_mesh(dim, n)
+def mms_problem(dim: int, n: int, prm: MMSParams = PAPER, kind: str = "simplex") -> Problem:
+    mesh = unit_mesh(dim, n, kind)
     lk1, lk2 = constant_logk(mesh.n_cells, prm.k1, prm.k2)
     p01, p02 = boundary_pressures(mesh.coords, prm)
     return Problem(mesh, lk1, lk2, prm.mu, prm.beta, np.zeros(dim), p01, p02,
-                   name=f"mms{dim}d_n{n}")
+                   name=f"mms{dim}d_n{n}" + ("_q1" if kind == "q1" else ""))
 
 
 def heterogeneous_problem(dim: int, n: int, seed: int = 0, beta: float = 1.0,
-                          mu: float = 1.0) -> Problem:
-    mesh = unit_mesh(dim, n)
+                          mu: float = 1.0, kind: str = "simplex") -> Problem:
+    mesh = unit_mesh(dim, n, kind)
     lk1, lk2 = lognormal_logk(mesh.n_cells, seed)
     p01, p02 = boundary_pressures(mesh.coords, PAPER)
     return Problem(mesh, lk1, lk2, mu, beta, np.zeros(dim), p01, p02,
-                   name=f"het{dim}d_n{n}_s{seed}", meta={"seed": seed})
+                   name=f"het{dim}d_n{n}_s{seed}" + ("_q1" if kind == "q1" else ""),
+                   meta={"seed": seed})
 
 
 def wheel_problem(sectors: int = 70, rings: int = 4, seed: int = 0, beta: float = 1.0,

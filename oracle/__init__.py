@@ -15,6 +15,8 @@ solvers for the four-field double porosity/permeability model", 2018):
     "S4_linear_problem", Eqs. "S4_cg_stiffness_matrix" and "S4_cg_rhs",
     Section 4). Pressure data is imposed weakly on the whole boundary, as in the
     paper's appendix CG-VMS listing.
+  * q1.py: the same CG-VMS form on Q1 quadrilaterals and hexahedra (the
+    paper's QUAD and HEX meshes), with the tensor 2-point Gauss rule.
   * solve.py: an FP64 sparse direct solve of K x = f (SuperLU). The
     preconditioned FGMRES on the GPU reaches this same solution, up to its
     tolerance.
@@ -44,6 +46,7 @@ from .errors import (p1_mass_matrix, interp_l2_errors, field_rel_errors, field_s
                      mass_balance, FIELDS)
 from .blocks import field_split_blocks, selfp_schur
 from .inner import ilu0, ilu0_factors, ilu0_solve, chebyshev_jacobi
+from .q1 import assemble_q1, q1_mass_matrix, mass_balance_q1, gauss_tensor, q1_basis
 from .adjoint import (objective, objective_grad_x, adjoint_solve, adjoint_gradients,
                       complex_step_gradient, fd_gradient)
 
@@ -53,7 +56,8 @@ __all__ = [
     "solve_direct", "solve_dense", "residual", "solve_field_split_gmres",
     "p1_mass_matrix", "interp_l2_errors", "field_rel_errors", "field_slices", "mass_balance",
     "FIELDS", "field_split_blocks", "selfp_schur", "ilu0", "ilu0_factors", "ilu0_solve",
-    "chebyshev_jacobi",
+    "chebyshev_jacobi", "assemble_q1", "q1_mass_matrix", "mass_balance_q1", "gauss_tensor",
+    "q1_basis",
     "objective", "objective_grad_x", "adjoint_solve", "adjoint_gradients",
     "complex_step_gradient", "fd_gradient",
 ]

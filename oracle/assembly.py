@@ -244,7 +244,12 @@ def assemble(coords, cells, bfacets, logk1, logk2, mu, beta, gamma_b, p01, p02,
 
 
 def assemble_problem(problem, **kw):
+    """K and f of a problem: P1 on simplices, or Q1 (oracle/q1.py) on tensor-product cells."""
     m = problem.mesh
+    if getattr(m, "kind", "simplex") == "q1":
+        from .q1 import assemble_q1
+        return assemble_q1(m.coords, m.cells, m.bfacets, problem.logk1, problem.logk2, problem.mu,
+                           problem.beta, problem.gamma_b, problem.p01, problem.p02, **kw)
     return assemble(m.coords, m.cells, m.bfacets, problem.logk1, problem.logk2, problem.mu,
                     problem.beta, problem.gamma_b, problem.p01, problem.p02, **kw)
 
