@@ -72,6 +72,10 @@ typedef enum {
 
 typedef enum { DPP_FP64 = 0, DPP_MIXED_FP32_FP64 = 1 } dpp_precision;
 typedef enum { DPP_MEM_DEVICE = 0, DPP_MEM_HOST = 1 } dpp_memory;
+/* Cell types (Table "ELE_level_discretization"): P1 on triangles/tetrahedra, or
+ * Q1 on quadrilaterals/hexahedra with vertices in tensor order (vertex v at
+ * the reference corner with coordinate bits (v & 1, (v >> 1) & 1, (v >> 2) & 1)). */
+typedef enum { DPP_CELL_SIMPLEX = 0, DPP_CELL_Q1 = 1 } dpp_cell_kind;
 
 typedef struct dpp_problem_s* dpp_problem; /* opaque: graph, K pair values, f */
 typedef struct dpp_pc_s* dpp_pc;           /* opaque: S_p blocks and AMG hierarchy */
@@ -82,11 +86,11 @@ typedef struct dpp_pc_s* dpp_pc;           /* opaque: S_p blocks and AMG hierarc
  * copies the arrays to the device inside dpp_assemble.
  */
 typedef struct {
-    int32_t dim;              /* 2 (triangles) or 3 (tetrahedra) */
+    int32_t dim;              /* 2 (triangles, quadrilaterals) or 3 (tetrahedra, hexahedra) */
     int32_t memory;           /* dpp_memory of the arrays below */
     int64_t n_nodes, n_cells, n_bfacets;
     const double* coords;     /* [n_nodes][dim] */
-    const int32_t* cells;     /* [n_cells][dim+1] node ids; either orientation */
+    const int32_t* cells;     /* [n_cells][dim+1] node ids (simplices; either orientation) */
     const int32_t* bfacets;   /* [n_bfacets][dim] boundary facets on Gamma^p (pressure data) */
     const double* log_k1;     /* [n_cells] natural-log macro permeability k1 */
     const double* log_k2;     /* [n_cells] natural-log micro permeability k2 */
@@ -95,6 +99,8 @@ typedef struct {
     double gamma_b[3];        /* constant gamma*b body force (first dim entries used) */
     const double* p01;        /* [n_nodes] macro pressure data, read at bfacet nodes */
     const double* p02;        /* [n_nodes] micro pressure data, read at bfacet nodes */
+    int32_t cell_kind;        /* dpp_cell_kind. For DPP_CELL_Q1, cells are [n_cells][2^dim] and
+                                 bfacets [n_bfacets][2^(dim-1)], both in tensor vertex order */
 } dpp_problem_desc;
 
 /* Preconditioner options (Section 4; defaults from dpp_pc_opts_default). */

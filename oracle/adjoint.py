@@ -1,6 +1,7 @@
 """Adjoint gradients of a pressure-misfit objective (oracle; test infrastructure only).
 
-The system K(theta) x = f(theta) is the CG-VMS system of Eq. "S4_linear_problem".
+The system K(theta) x = f(theta) is the CG-VMS system of Eq. "S4_linear_problem",
+on simplices (assembly.py) or Q1 cells (q1.py).
 theta is one of: a per-cell log k1, a per-cell log k2, or beta. The objective is
 J(x) = sum over nodes (p1 - p1_obs)^2. The adjoint identity gives
     dJ/dtheta = -lambda^T (dK/dtheta x - df/dtheta),  with  K^T lambda = dJ/dx.
@@ -50,6 +51,8 @@ def adjoint_solve(K, g_nodal: np.ndarray) -> np.ndarray:
 def adjoint_gradients(problem, xn: np.ndarray, lamn: np.ndarray, chunk: int = 8192):
     """(dJ/dlogk1 [C], dJ/dlogk2 [C], dJ/dbeta) from the forward x and adjoint lambda."""
     m = problem.mesh
+    if getattr(m, "kind", "simplex") == "q1":
+        return _adjoint_gradients_q1(problem, xn, lamn, chunk)
     d = m.dim
     coords, cells = m.coords, m.cells.astype(np.int64)
     n = m.n_nodes
@@ -78,10 +81,48 @@ def adjoint_gradients(problem, xn: np.ndarray, lamn: np.ndarray, chunk: int = 81
     return g1, g2, gb
 
 
+def _adjoint_gradients_q1(problem, xn, lamn, chunk):
+    """The same gradients on Q1 cells (element routines of q1.py, complex step)."""
+    from .q1 import element_matrices_q1, element_rhs_body_q1, q1_geometry
+    from .q1 import _global_rows as rows_q1
+    m = problem.mesh
+    d = m.dim
+    cells = m.cells.astype(np.int64)
+    x = from_nodal(xn)
+    lam = from_nodal(lamn)
+    w, phi, grad, _ = q1_geometry(np.asarray(m.coords, dtype=np.float64), cells)
+    k1 = np.exp(problem.logk1)
+    k2 = np.exp(problem.logk2)
+    g1 = np.zeros(m.n_cells)
+    g2 = np.zeros(m.n_cells)
+    gb = 0.0
+    ih = 1j * CS_H
+    for s0 in range(0, m.n_cells, chunk):
+        e = slice(s0, min(s0 + chunk, m.n_cells))
+        rows = rows_q1(cells[e], m.n_nodes, d)
+        xe, le = x[rows], lam[rows]
+        for which, out in ((1, g1), (2, g2)):
+            kk1 = np.exp(problem.logk1[e] + (ih if which == 1 else 0.0))
+            kk2 = np.exp(problem.logk2[e] + (ih if which == 2 else 0.0))
+            dK = element_matrices_q1(w[e], phi, grad[e], kk1, kk2, problem.mu, problem.beta, d)
+            dF = element_rhs_body_q1(w[e], phi, grad[e], kk1, kk2, problem.mu, problem.gamma_b, d)
+            out[e] = (-np.einsum("ci,cij,cj->c", le, dK.imag / CS_H, xe)
+                      + np.einsum("ci,ci->c", le, dF.imag / CS_H))
+        dKb = element_matrices_q1(w[e], phi, grad[e], k1[e], k2[e], problem.mu,
+                                  problem.beta + ih, d).imag / CS_H
+        gb += -float(np.einsum("ci,cij,cj->", le, dKb, xe))
+    return g1, g2, gb
+
+
 def _solve_J(problem, p1_obs, logk1, logk2, beta):
     m = problem.mesh
-    K, f = assemble(m.coords, m.cells, m.bfacets, logk1, logk2, problem.mu, beta,
-                    problem.gamma_b, problem.p01, problem.p02)
+    if getattr(m, "kind", "simplex") == "q1":
+        from .q1 import assemble_q1
+        K, f = assemble_q1(m.coords, m.cells, m.bfacets, logk1, logk2, problem.mu, beta,
+                           problem.gamma_b, problem.p01, problem.p02)
+    else:
+        K, f = assemble(m.coords, m.cells, m.bfacets, logk1, logk2, problem.mu, beta,
+                        problem.gamma_b, problem.p01, problem.p02)
     x = lu(K).solve(f)
     xn = to_nodal(x, m.n_nodes)
     d = m.dim

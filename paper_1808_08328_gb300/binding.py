@@ -26,6 +26,7 @@ DPP_ERR_BAD_STATE = 8
 
 DPP_FP64 = 0
 DPP_MIXED_FP32_FP64 = 1
+DPP_CELL_SIMPLEX, DPP_CELL_Q1 = 0, 1
 DPP_MEM_DEVICE = 0
 DPP_MEM_HOST = 1
 
@@ -37,7 +38,7 @@ class dpp_problem_desc(C.Structure):
         ("coords", C.c_void_p), ("cells", C.c_void_p), ("bfacets", C.c_void_p),
         ("log_k1", C.c_void_p), ("log_k2", C.c_void_p),
         ("mu", C.c_double), ("beta", C.c_double), ("gamma_b", C.c_double * 3),
-        ("p01", C.c_void_p), ("p02", C.c_void_p),
+        ("p01", C.c_void_p), ("p02", C.c_void_p), ("cell_kind", C.c_int32),
     ]
 
 

@@ -258,6 +258,8 @@ dpp_status dpp_assemble(const dpp_problem_desc* d, int32_t precision, dpp_stream
         require(d != nullptr && out != nullptr, "null descriptor or output handle");
         *out = nullptr;
         require(d->dim == 2 || d->dim == 3, "dim must be 2 or 3");
+        require(d->cell_kind == DPP_CELL_SIMPLEX || d->cell_kind == DPP_CELL_Q1,
+                "cell_kind must be DPP_CELL_SIMPLEX or DPP_CELL_Q1");
         require(d->memory == DPP_MEM_DEVICE || d->memory == DPP_MEM_HOST, "bad memory kind");
         require(precision == DPP_FP64 || precision == DPP_MIXED_FP32_FP64, "bad precision");
         require(d->n_nodes > 0 && d->n_cells > 0 && d->n_bfacets >= 0, "sizes must be positive");
@@ -344,6 +346,8 @@ static dpp_status solve_common(const char* name, dpp_problem prob, dpp_pc pc,
         require(o.max_iters >= 1, "max_iters >= 1");
         require(o.x_memory == DPP_MEM_DEVICE || o.x_memory == DPP_MEM_HOST, "bad x_memory");
         require(o.matrix_free == 0 || o.matrix_free == 1, "matrix_free in {0,1}");
+        require(!o.matrix_free || prob->impl.kind == DPP_CELL_SIMPLEX,
+                "matrix_free supports simplices only");
         if (o.matrix_free && pc->impl.precision == DPP_MIXED_FP32_FP64)
             matrix_free_prepare32(prob->impl, (cudaStream_t)stream);
         const ProblemImpl& P = prob->impl;
@@ -593,6 +597,8 @@ dpp_status dpp_apply_K_mf(dpp_problem prob, int32_t transpose, const double* x, 
     return guarded("dpp_apply_K_mf", [&]() -> dpp_status {
         StreamScope scope_((cudaStream_t)stream);
         require(prob && x && y && x != y, "null or aliased argument");
+        if (prob->impl.kind != DPP_CELL_SIMPLEX)
+            fail(DPP_ERR_BAD_STATE, "the matrix-free apply supports simplices only");
         apply_K_mf(prob->impl, x, y, transpose != 0, (cudaStream_t)stream);
         return DPP_OK;
     });
@@ -603,6 +609,8 @@ dpp_status dpp_apply_K32_mf(dpp_problem prob, int32_t transpose, const float* x,
     return guarded("dpp_apply_K32_mf", [&]() -> dpp_status {
         StreamScope scope_((cudaStream_t)stream);
         require(prob && x && y, "null argument");
+        if (prob->impl.kind != DPP_CELL_SIMPLEX)
+            fail(DPP_ERR_BAD_STATE, "the matrix-free apply supports simplices only");
         matrix_free_prepare32(prob->impl, (cudaStream_t)stream);
         apply_K32_mf(prob->impl, x, y, transpose != 0, (cudaStream_t)stream);
         return DPP_OK;

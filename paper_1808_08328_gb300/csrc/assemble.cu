@@ -16,7 +16,7 @@
 // Every sum runs over the cells that contain both a and b, in increasing cell
 // id. It is a fixed-order gather (no floating-point atomics), so K is
 // bit-reproducible.
-#include "impl.cuh"
+#include "q1.cuh"
 
 namespace dpp {
 
@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kMaxRow = 96;  // max node-pair row length (distinct neighbours + self)
 
-template <int DIM>
+template <int NVC>
 __global__ void k_validate_cells(const int* __restrict__ cells, int64_t n_cells, int64_t n_nodes,
                                  const double* __restrict__ lk1, const double* __restrict__ lk2,
                                  int* status) {
@@ -32,8 +32,8 @@ __global__ void k_validate_cells(const int* __restrict__ cells, int64_t n_cells,
     if (c >= n_cells) return;
     int bad = 0;
 #pragma unroll
-    for (int v = 0; v <= DIM; ++v) {
-        int a = cells[c * (DIM + 1) + v];
+    for (int v = 0; v < NVC; ++v) {
+        int a = cells[c * NVC + v];
         if (a < 0 || a >= n_nodes) bad |= kDevBadIndex;
     }
     if (!isfinite(lk1[c]) || !isfinite(lk2[c])) bad |= kDevNonFinite;
@@ -80,8 +80,9 @@ __global__ void k_sort_segments(const int* __restrict__ ptr, int* __restrict__ l
     }
 }
 
-// Distinct neighbours (self included) of node a, sorted, in a local array.
-template <int DIM>
+// Distinct neighbours (self included) of node a, sorted, in a local array
+// (NVC vertices per cell).
+template <int NVC>
 __device__ int gather_neighbours(int a, const int* __restrict__ nc_ptr,
                                  const int* __restrict__ nc_list, const int* __restrict__ cells,
                                  int* nb, bool* overflow) {
@@ -89,8 +90,8 @@ __device__ int gather_neighbours(int a, const int* __restrict__ nc_ptr,
     for (int k = nc_ptr[a]; k < nc_ptr[a + 1]; ++k) {
         int c = nc_list[k];
 #pragma unroll
-        for (int v = 0; v <= DIM; ++v) {
-            int b = cells[(int64_t)c * (DIM + 1) + v];
+        for (int v = 0; v < NVC; ++v) {
+            int b = cells[(int64_t)c * NVC + v];
             int pos = 0;
             while (pos < len && nb[pos] < b) ++pos;
             if (pos < len && nb[pos] == b) continue;
@@ -103,7 +104,7 @@ __device__ int gather_neighbours(int a, const int* __restrict__ nc_ptr,
     return len;
 }
 
-template <int DIM>
+template <int NVC>
 __global__ void k_pair_count(const int* __restrict__ nc_ptr, const int* __restrict__ nc_list,
                              const int* __restrict__ cells, int64_t n_nodes, int* __restrict__ len,
                              int* status) {
@@ -111,11 +112,11 @@ __global__ void k_pair_count(const int* __restrict__ nc_ptr, const int* __restri
     if (a >= n_nodes) return;
     int nb[kMaxRow];
     bool of = false;
-    len[a] = gather_neighbours<DIM>((int)a, nc_ptr, nc_list, cells, nb, &of);
+    len[a] = gather_neighbours<NVC>((int)a, nc_ptr, nc_list, cells, nb, &of);
     if (of) atomicOr(status, kDevOverflow);
 }
 
-template <int DIM>
+template <int NVC>
 __global__ void k_pair_fill(const int* __restrict__ nc_ptr, const int* __restrict__ nc_list,
                             const int* __restrict__ cells, int64_t n_nodes,
                             const int* __restrict__ row_ptr, int* __restrict__ col,
@@ -124,7 +125,7 @@ __global__ void k_pair_fill(const int* __restrict__ nc_ptr, const int* __restric
     if (a >= n_nodes) return;
     int nb[kMaxRow];
     bool of = false;
-    int len = gather_neighbours<DIM>((int)a, nc_ptr, nc_list, cells, nb, &of);
+    int len = gather_neighbours<NVC>((int)a, nc_ptr, nc_list, cells, nb, &of);
     int s = row_ptr[a];
     for (int j = 0; j < len; ++j) {
         col[s + j] = nb[j];
@@ -548,17 +549,61 @@ void build_incidence(const int* ent, int64_t n_ent, int per, int64_t n_nodes, DB
     DPP_CK(cudaStreamSynchronize(s));
 }
 
+// Steps 5-7 for Q1 cells: the cell tables, the pair values and the load.
 template <int DIM>
+void assemble_q1_values(ProblemImpl& P, cudaStream_t s) {
+    using Lay = q1::Layout<DIM>;
+    const int B = 128;
+    P.q1tab.alloc(P.n_cells * Lay::stride);
+    P.kk.alloc(P.n_cells * 2);
+    q1::k_cell_tables<DIM><<<grid_for(P.n_cells * Lay::NVC, B), B, 0, s>>>(
+        P.coords.get(), P.cells.get(), P.n_cells, P.logk1.get(), P.logk2.get(), P.q1tab.get(),
+        P.kk.get(), P.dstatus.get());
+    DPP_LAUNCH_CK();
+    check_status(P, s, "dpp_assemble cell geometry");
+    P.sell_val.alloc(P.n_groups * P.nv * kSell);
+    DPP_CK(cudaMemsetAsync(P.sell_val.get(), 0, P.sell_val.bytes(), s));
+    q1::k_assemble_pairs<DIM><<<grid_for(P.n_pairs, B), B, 0, s>>>(
+        P.pair_row.get(), P.col.get(), P.row_ptr.get(), P.n_pairs, P.nc_ptr.get(), P.nc_list.get(),
+        P.cells.get(), P.q1tab.get(), P.kk.get(), P.mu, P.beta, P.cell_mu_beta.get(),
+        P.slice_ptr.get(), P.sell_val.get());
+    DPP_LAUNCH_CK();
+    if (P.precision == DPP_MIXED_FP32_FP64) {
+        P.sell_val32.alloc(P.sell_val.n);
+        k_to_float<<<grid_for(P.sell_val.n, 256), 256, 0, s>>>(P.sell_val.get(), P.sell_val32.get(),
+                                                              P.sell_val.n);
+        DPP_LAUNCH_CK();
+    }
+    P.facet_tab.alloc(std::max<int64_t>(P.n_bfacets * Lay::fstride, 1));
+    if (P.n_bfacets) {
+        q1::k_facet_tables<DIM><<<grid_for(P.n_bfacets, B), B, 0, s>>>(
+            P.bfacets.get(), P.n_bfacets, P.nc_ptr.get(), P.nc_list.get(), P.cells.get(),
+            P.coords.get(), P.p01.get(), P.p02.get(), P.facet_tab.get(), P.dstatus.get());
+        DPP_LAUNCH_CK();
+    }
+    P.f.alloc(P.n_nodes * P.ns);
+    q1::k_rhs<DIM><<<grid_for(P.n_nodes, B), B, 0, s>>>(
+        P.n_nodes, P.nc_ptr.get(), P.nc_list.get(), P.cells.get(), P.q1tab.get(), P.kk.get(),
+        P.nf_ptr.get(), P.nf_list.get(), P.bfacets.get(), P.facet_tab.get(), P.p01.get(),
+        P.p02.get(), P.mu, P.cell_mu_beta.get(), P.gb[0], P.gb[1], P.gb[2], P.f.get());
+    DPP_LAUNCH_CK();
+    check_status(P, s, "dpp_assemble");
+}
+
+// NVC: vertices per cell (DIM + 1 for simplices, 2^DIM for Q1 cells).
+template <int DIM, int NVC>
 void assemble_dim(ProblemImpl& P, cudaStream_t s) {
+    constexpr bool kQ1 = NVC != DIM + 1;
+    constexpr int NFV = kQ1 ? (1 << (DIM - 1)) : DIM;  // vertices per boundary facet
     const int B = 256;
     auto& hs = P.hs;
     // 1. validation of every index and value before any indexed access
-    k_validate_cells<DIM><<<grid_for(P.n_cells, B), B, 0, s>>>(
+    k_validate_cells<NVC><<<grid_for(P.n_cells, B), B, 0, s>>>(
         P.cells.get(), P.n_cells, P.n_nodes, P.logk1.get(), P.logk2.get(), P.dstatus.get());
     DPP_LAUNCH_CK();
     if (P.n_bfacets) {
-        k_validate_facets<<<grid_for(P.n_bfacets * DIM, B), B, 0, s>>>(
-            P.bfacets.get(), P.n_bfacets, DIM, P.n_nodes, P.dstatus.get());
+        k_validate_facets<<<grid_for(P.n_bfacets * NFV, B), B, 0, s>>>(
+            P.bfacets.get(), P.n_bfacets, NFV, P.n_nodes, P.dstatus.get());
         DPP_LAUNCH_CK();
     }
     k_validate_coords<<<grid_for(P.n_nodes * DIM, B), B, 0, s>>>(P.coords.get(), P.n_nodes * DIM,
@@ -567,20 +612,20 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
     check_status(P, s, "dpp_assemble input check");
 
     // 2. incidence lists node -> cells and node -> boundary facets
-    build_incidence(P.cells.get(), P.n_cells, DIM + 1, P.n_nodes, P.nc_ptr, P.nc_list, s, hs);
-    build_incidence(P.bfacets.get(), P.n_bfacets, DIM, P.n_nodes, P.nf_ptr, P.nf_list, s, hs);
+    build_incidence(P.cells.get(), P.n_cells, NVC, P.n_nodes, P.nc_ptr, P.nc_list, s, hs);
+    build_incidence(P.bfacets.get(), P.n_bfacets, NFV, P.n_nodes, P.nf_ptr, P.nf_list, s, hs);
 
     // 3. node-pair graph (CSR with sorted columns)
     P.row_ptr.alloc(P.n_nodes + 1);
     DPP_CK(cudaMemsetAsync(P.row_ptr.get(), 0, (P.n_nodes + 1) * sizeof(int), s));
-    k_pair_count<DIM><<<grid_for(P.n_nodes, 128), 128, 0, s>>>(
+    k_pair_count<NVC><<<grid_for(P.n_nodes, 128), 128, 0, s>>>(
         P.nc_ptr.get(), P.nc_list.get(), P.cells.get(), P.n_nodes, P.row_ptr.get(), P.dstatus.get());
     DPP_LAUNCH_CK();
     check_status(P, s, "dpp_assemble pair graph");
     P.n_pairs = exclusive_scan(P.row_ptr.get(), P.row_ptr.get(), P.n_nodes + 1, s, hs);
     P.col.alloc(P.n_pairs);
     P.pair_row.alloc(P.n_pairs);
-    k_pair_fill<DIM><<<grid_for(P.n_nodes, 128), 128, 0, s>>>(
+    k_pair_fill<NVC><<<grid_for(P.n_nodes, 128), 128, 0, s>>>(
         P.nc_ptr.get(), P.nc_list.get(), P.cells.get(), P.n_nodes, P.row_ptr.get(), P.col.get(),
         P.pair_row.get());
     DPP_LAUNCH_CK();
@@ -598,6 +643,11 @@ void assemble_dim(ProblemImpl& P, cudaStream_t s) {
                                                            P.n_slices, P.slice_ptr.get(),
                                                            P.sell_col.get());
     DPP_LAUNCH_CK();
+
+    if constexpr (kQ1) {
+        assemble_q1_values<DIM>(P, s);
+        return;
+    }
 
     // 5. cell geometry and permeabilities
     P.geo.alloc(P.n_cells * GeoLayout<DIM>::stride);
@@ -654,8 +704,11 @@ void assemble_problem(ProblemImpl& P, const dpp_problem_desc& d, cudaStream_t s)
     P.beta = d.beta;
     for (int k = 0; k < 3; ++k) P.gb[k] = (k < d.dim) ? d.gamma_b[k] : 0.0;
     upload(P.coords, d.coords, (size_t)d.n_nodes * d.dim, host, s);
-    upload(P.cells, d.cells, (size_t)d.n_cells * (d.dim + 1), host, s);
-    upload(P.bfacets, d.bfacets, (size_t)d.n_bfacets * d.dim, host, s);
+    P.kind = d.cell_kind;
+    P.nvc = (P.kind == DPP_CELL_Q1) ? (1 << d.dim) : d.dim + 1;
+    P.nfv = (P.kind == DPP_CELL_Q1) ? (1 << (d.dim - 1)) : d.dim;
+    upload(P.cells, d.cells, (size_t)d.n_cells * P.nvc, host, s);
+    upload(P.bfacets, d.bfacets, (size_t)d.n_bfacets * P.nfv, host, s);
     upload(P.logk1, d.log_k1, (size_t)d.n_cells, host, s);
     upload(P.logk2, d.log_k2, (size_t)d.n_cells, host, s);
     upload(P.p01, d.p01, (size_t)d.n_nodes, host, s);
@@ -670,8 +723,13 @@ void assemble_uploaded(ProblemImpl& P, cudaStream_t s) {
     P.nv = pair_values(P.dim);
     P.dstatus.alloc(1);
     DPP_CK(cudaMemsetAsync(P.dstatus.get(), 0, sizeof(int), s));
-    if (P.dim == 2) assemble_dim<2>(P, s);
-    else assemble_dim<3>(P, s);
+    if (P.kind == DPP_CELL_Q1) {
+        if (P.dim == 2) assemble_dim<2, 4>(P, s);
+        else assemble_dim<3, 8>(P, s);
+    } else {
+        if (P.dim == 2) assemble_dim<2, 3>(P, s);
+        else assemble_dim<3, 4>(P, s);
+    }
 }
 
 }  // namespace dpp

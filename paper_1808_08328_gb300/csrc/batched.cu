@@ -358,7 +358,8 @@ void assemble_union(ProblemImpl& P, int n, const dpp_problem_desc* descs, std::v
                   (d.memory == DPP_MEM_DEVICE || d.memory == DPP_MEM_HOST) && d.n_nodes > 0 &&
                   d.n_cells > 0 && d.n_bfacets >= 0 && d.coords && d.cells && d.log_k1 &&
                   d.log_k2 && d.p01 && d.p02 && (d.n_bfacets == 0 || d.bfacets) && d.mu > 0 &&
-                  std::isfinite(d.mu) && d.beta >= 0 && std::isfinite(d.beta);
+                  std::isfinite(d.mu) && d.beta >= 0 && std::isfinite(d.beta) &&
+                  d.cell_kind == DPP_CELL_SIMPLEX;  // the batched union takes simplices
         for (int k = 0; k < dim && ok; ++k) ok = d.gamma_b[k] == descs[0].gamma_b[k];
         if (!ok) codes[b] = DPP_ERR_INVALID_ARGUMENT;
     }

@@ -36,6 +36,8 @@ struct Csr {
 
 struct ProblemImpl {
     int dim = 0, ns = 0, nv = 0;  // dimension, DoF per node (2d+2), values per pair
+    int kind = DPP_CELL_SIMPLEX;  // dpp_cell_kind
+    int nvc = 0, nfv = 0;         // vertices per cell and per boundary facet
     int64_t n_nodes = 0, n_cells = 0, n_bfacets = 0, n_pairs = 0;
     double mu = 1, beta = 0, gb[3] = {0, 0, 0};
     int precision = DPP_FP64;
@@ -63,6 +65,8 @@ struct ProblemImpl {
     // FP32 copies for the matrix-free FP32 operator (made on first use)
     DBuf<float> coords32, kk32, cell_mu_beta32;
     DBuf<double> geo;       // [n_cells][GeoLayout<dim>::stride]
+    DBuf<double> q1tab;     // Q1 cells: [n_cells][q1::Layout<dim>::stride] element integrals
+    DBuf<double> facet_tab; // Q1 cells: [n_bfacets][q1::Layout<dim>::fstride] facet integrals
     DBuf<double> kk;        // [n_cells][2]: k1, k2
     DBuf<double> ccoef;     // [n_cells][kCellCoef]: factors of the pair values
     DBuf<double> f;         // [n_nodes][ns]

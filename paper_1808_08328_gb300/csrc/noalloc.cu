@@ -110,6 +110,10 @@ extern "C" dpp_status dpp_adjoint_gradients_noalloc(dpp_problem prob, const doub
         if (!prob || !x || !lambda || !dJ_dlogk1 || !dJ_dlogk2 || !dJ_dbeta)
             return report(DPP_ERR_INVALID_ARGUMENT, "dpp_adjoint_gradients_noalloc: null argument");
         const dpp::ProblemImpl& P = prob->impl;
+        if (P.kind != DPP_CELL_SIMPLEX)
+            return report(DPP_ERR_BAD_STATE,
+                          "dpp_adjoint_gradients_noalloc: simplicial meshes only (use "
+                          "dpp_adjoint_solve for Q1 cells)");
         if (P.n_cells > kNoAllocMaxCells)
             return report(DPP_ERR_INVALID_ARGUMENT,
                           "dpp_adjoint_gradients_noalloc: n_cells exceeds the fixed scratch limit of "

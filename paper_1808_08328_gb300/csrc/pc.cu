@@ -37,6 +37,8 @@
 // which is why the paper's KSP counts for the two methods agree.
 #include "amg.cuh"
 
+#include <cmath>
+
 namespace dpp {
 
 namespace {
@@ -148,7 +150,15 @@ void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
     const int64_t nn = n * P.ns;
     pc.mdiag.alloc(2 * n);
     mass_diag_inv(P, pc.mdiag.get(), pc.opts.use_lumped_diag != 0, s);
-    if (pc.opts.use_lumped_diag) {
+    if (P.kind == DPP_CELL_Q1) {
+        // Q1 element mass on a parallelepiped: the d-fold tensor product of the
+        // 1D P1 mass, so eig(diag(M_e)^-1 M_e) = products of {1/2, 3/2} and
+        // eig(lumped(M_e)^-1 M_e) = products of {1/3, 1}; Wathen's argument
+        // carries these element bounds to the assembled matrix
+        const double d = P.dim;
+        pc.mass_lmin = pc.opts.use_lumped_diag ? std::pow(1.0 / 3.0, d) : std::pow(0.5, d);
+        pc.mass_lmax = pc.opts.use_lumped_diag ? 1.0 : std::pow(1.5, d);
+    } else if (pc.opts.use_lumped_diag) {
         // eig(lumped(M)^-1 M) lies in [1/(d+2), 1] elementwise
         pc.mass_lmin = 1.0 / (P.dim + 2);
         pc.mass_lmax = 1.0;

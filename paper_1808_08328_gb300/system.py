@@ -26,7 +26,8 @@ class DPPSystem:
     """One assembled DPP system (problem handle) and optionally its preconditioner."""
 
     def __init__(self, coords, cells, bfacets, log_k1, log_k2, mu, beta, gamma_b, p01, p02,
-                 precision: int = B.DPP_FP64, device: str | torch.device = "cuda"):
+                 precision: int = B.DPP_FP64, device: str | torch.device = "cuda",
+                 cell_kind: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("DPPSystem needs a CUDA device; libdpp has no CPU fallback")
         self.device = torch.device(device)
@@ -44,6 +45,7 @@ class DPPSystem:
         gb = list(np.asarray(gamma_b, dtype=np.float64).ravel()) + [0.0] * 3
         self.gamma_b = gb[:3]
         self.precision = precision
+        self.cell_kind = int(cell_kind)
         self.n_nodes = int(self.coords.shape[0])
         self.n_cells = int(self.cells.shape[0])
         self.ns = 2 * self.dim + 2
@@ -55,8 +57,9 @@ class DPPSystem:
     @classmethod
     def from_problem(cls, p, precision: int = B.DPP_FP64, device="cuda"):
         m = p.mesh
+        kind = B.DPP_CELL_Q1 if getattr(m, "kind", "simplex") == "q1" else B.DPP_CELL_SIMPLEX
         return cls(m.coords, m.cells, m.bfacets, p.logk1, p.logk2, p.mu, p.beta, p.gamma_b, p.p01,
-                   p.p02, precision=precision, device=device)
+                   p.p02, precision=precision, device=device, cell_kind=kind)
 
     def _desc(self) -> B.dpp_problem_desc:
         d = B.dpp_problem_desc()
@@ -76,6 +79,7 @@ class DPPSystem:
             d.gamma_b[k] = self.gamma_b[k]
         d.p01 = self.p01.data_ptr()
         d.p02 = self.p02.data_ptr()
+        d.cell_kind = self.cell_kind
         return d
 
     # ------------------------------------------------------------------ pc / solve
@@ -284,6 +288,7 @@ class DPPBatch:
             for k in ("coords", "cells", "bfacets", "log_k1", "log_k2", "p01", "p02"):
                 setattr(d, k, t[k].data_ptr() if t[k].numel() else None)
             d.mu, d.beta = float(p.mu), float(p.beta)
+            d.cell_kind = B.DPP_CELL_Q1 if getattr(m, "kind", "simplex") == "q1" else 0
             gb = list(np.asarray(p.gamma_b, dtype=np.float64).ravel()) + [0.0] * 3
             for k in range(3):
                 d.gamma_b[k] = gb[k]

@@ -18,9 +18,9 @@ import oracle
 from oracle.assembly import assemble_problem
 
 
-def _setup(dim, n, seed=0, gamma_b=None):
-    P = inputs.heterogeneous_problem(dim, n, seed=seed, beta=1.3)
-    Pobs = inputs.heterogeneous_problem(dim, n, seed=seed + 1, beta=1.3)
+def _setup(dim, n, seed=0, gamma_b=None, kind="simplex"):
+    P = inputs.heterogeneous_problem(dim, n, seed=seed, beta=1.3, kind=kind)
+    Pobs = inputs.heterogeneous_problem(dim, n, seed=seed + 1, beta=1.3, kind=kind)
     if gamma_b is not None:
         P = P.with_(gamma_b=np.asarray(gamma_b, dtype=np.float64))
         Pobs = Pobs.with_(gamma_b=np.asarray(gamma_b, dtype=np.float64))
@@ -33,12 +33,15 @@ def _setup(dim, n, seed=0, gamma_b=None):
     return P, p1_obs, oracle.adjoint_gradients(P, xn, lam)
 
 
-@pytest.mark.parametrize("dim,n,gamma_b", [(2, 5, None), (3, 2, None), (2, 5, [2.0, -1.5]),
-                                           (3, 2, [0.5, 1.0, -2.0])])
-def test_adjoint_matches_complex_step(dim, n, gamma_b):
+@pytest.mark.parametrize("dim,n,gamma_b,kind", [(2, 5, None, "simplex"), (3, 2, None, "simplex"),
+                                                (2, 5, [2.0, -1.5], "simplex"),
+                                                (3, 2, [0.5, 1.0, -2.0], "simplex"),
+                                                (2, 4, [1.0, -0.5], "q1"), (3, 2, None, "q1")])
+def test_adjoint_matches_complex_step(dim, n, gamma_b, kind):
     # With a body force the load depends on k (1/2 (grad q; k/mu gamma b)), so
-    # the adjoint's -lambda^T df/dlog k term is exercised too.
-    P, p1_obs, (g1, g2, gb) = _setup(dim, n, gamma_b=gamma_b)
+    # the adjoint's -lambda^T df/dlog k term is exercised too. The Q1 cases
+    # check the element sensitivities of q1.py the same way.
+    P, p1_obs, (g1, g2, gb) = _setup(dim, n, gamma_b=gamma_b, kind=kind)
     cells = inputs.sample_cells(P.mesh.n_cells, 4, seed=2)
     for c in cells:
         cs1 = oracle.complex_step_gradient(P, p1_obs, "logk1", int(c))
