@@ -70,12 +70,20 @@ struct ProfScope {
         cudaEventRecord(a, s);
     }
     ~ProfScope() { stop(); }
+    // End the timed range now; the record is made by stop(), so the algorithmic
+    // bytes may still be set in between (for outputs whose size is known later).
+    void end_range() {
+        if (!fam || ended) return;
+        cudaEventRecord(b, s);
+        ended = true;
+    }
     void stop() {  // end the timed range early (idempotent)
         if (!fam) return;
-        cudaEventRecord(b, s);
+        end_range();
         profile_record(fam, a, b, bytes);
         fam = nullptr;
     }
+    bool ended = false;
 };
 
 // Device memory comes from a library-owned, stream-ordered CUDA memory pool

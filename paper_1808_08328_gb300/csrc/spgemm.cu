@@ -953,6 +953,10 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
     DPP_CK(cudaMemsetAsync(ovf.get(), 0, sizeof(int), s));
     DPP_CK(cudaMemsetAsync(ovf2.get(), 0, sizeof(int), s));
     DPP_CK(cudaMemsetAsync(last.get(), 0, sizeof(int), s));
+    // The one-pass product is also timed as a kernel family of its own. Its
+    // algorithmic bytes: A and B (values, columns, row pointers) read once, and
+    // the rows of C written once (known after the launch).
+    ProfScope po("spgemm_onepass", s, 0);
     {
         ProfScope pf("spgemm_fill", s, 0);
         constexpr int HT = 2 * kOneCap;
@@ -963,6 +967,7 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
             tval.get(), ovf.get(), up);
         DPP_LAUNCH_CK();
     }
+    po.end_range();
     const int64_t n_ovf = read_scalar(ovf.get(), s, hs);
     if (n_ovf > 0) {  // wider rows: counted in the larger tiers
         ProfScope pc("spgemm_count", s, 0);
@@ -975,6 +980,9 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
         }
     }
     C.nnz = exclusive_scan(C.row_ptr.get(), C.row_ptr.get(), n + 1, s, hs);
+    po.bytes = 12.0 * (double)(A.nnz + B.nnz + C.nnz) + 4.0 * (double)(A.n_rows + B.n_rows + 2) +
+               4.0 * (double)n;
+    po.stop();
     {
         ProfScope pa("spgemm_alloc", s, 0);
         C.col.alloc(std::max<int64_t>(C.nnz, 1));

@@ -65,7 +65,8 @@ def recipe_slice():
     refs = []
     for P in probs:
         K, f = assemble_problem(P)
-        refs.append((K, f, oracle.to_nodal(oracle.solve_direct(K, f), P.mesh.n_nodes)))
+        refs.append((K, f, oracle.to_nodal(oracle.solve_direct(K, f, coords=P.mesh.coords),
+                                           P.mesh.n_nodes)))
     return probs, refs
 
 
