@@ -434,6 +434,27 @@ def bench_gb300(args):
         torch.cuda.synchronize(dev)
         bms = e2.elapsed_time(e3) / bsteps
         modes["batched"] = world * bt.n_dofs / (bms * 1e-3)
+        # the same 256 instances one by one through dpp_assemble + dpp_setup_pc +
+        # dpp_solve (device-resident inputs), FP64 and mixed: the plain-solve
+        # baseline that the batched form is measured against
+        seq = {}
+        for prec_name, prec_v in (("fp64", 0), ("mixed", 1)):
+            descs = bt.descs
+            xs = bt.xs
+            for dsc, xv in zip(descs[:2], xs[:2]):  # warm the tuner's size classes
+                step(dsc, xv, s_opts, prec_v)
+            torch.cuda.synchronize(dev)
+            e2.record(torch.cuda.current_stream(dev))
+            worst = 0.0
+            for dsc, xv in zip(descs, xs):
+                inf_ = step(dsc, xv, s_opts, prec_v)
+                worst = max(worst, inf_.rel_residual)
+            e3.record(torch.cuda.current_stream(dev))
+            torch.cuda.synchronize(dev)
+            sms = e2.elapsed_time(e3)
+            seq[prec_name] = {"dof_per_s": world * bt.n_dofs / (sms * 1e-3), "ms": sms,
+                              "max_rel_residual": worst}
+        modes["batched_vs_one_by_one"] = seq
         modes["batched_config"] = {"instances": BATCH["n_inst"], "dofs": bt.n_dofs,
                                    "ms_per_step": bms, "status": bst,
                                    "max_rel_residual": max(i["rel_residual"] for i in binfo),

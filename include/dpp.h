@@ -239,14 +239,17 @@ dpp_status dpp_adjoint_solve(dpp_problem prob, dpp_pc pc, const dpp_solve_opts* 
 /*
  * Solve n_inst independent systems (for example permeability realisations on
  * meshes of different sizes) in one batched pass. descs[i] describes instance i
- * exactly as for dpp_assemble; dim and gamma_b must agree across instances, and
- * mu and beta may differ. The instances are assembled as one block-diagonal
+ * exactly as for dpp_assemble (simplicial cells only); dim and gamma_b must
+ * agree across instances, and mu and beta may differ. The instances are assembled as one block-diagonal
  * union. One preconditioner (pc_opts, including its precision) is built on the
  * union; because no strength edge joins two instances, each instance keeps its
  * own aggregates. Every instance then runs its own FGMRES, with its own inner
  * products, Givens rotations, least-squares solves and convergence test on
- * ||f_i - K_i x_i|| / ||f_i|| <= rtol, in lock step with the others. One restart
- * cycle is one replay of a captured CUDA graph. xs[i]: [n_nodes_i][2d+2]
+ * ||f_i - K_i x_i|| / ||f_i|| <= rtol, in lock step with the others. The
+ * whole solve is one CUDA graph, launched once: a conditional WHILE node over
+ * restart cycles around a WHILE node over Arnoldi steps, which the device ends
+ * when no instance is still iterating (restart and max_iters bound both
+ * loops). xs[i]: [n_nodes_i][2d+2]
  * (device or host per opts->x_memory; the initial guess unless opts->x0_zero).
  * infos[i] receives that instance's status, iterations and residual. An
  * instance with invalid input gets INVALID_ARGUMENT or NONFINITE and is left

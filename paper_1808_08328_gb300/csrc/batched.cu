@@ -16,14 +16,14 @@
 // chunk partials in chunk order. The result is deterministic. The small
 // per-instance algebra runs as one device thread per instance, including the
 // test for a second Gram-Schmidt pass, which then runs only over that
-// instance's chunks. A restart cycle (m Arnoldi steps, the update of x, the
-// FP64 true residual and the convergence flags) needs no host
-// synchronisation; its Arnoldi steps are captured as CUDA graphs of a few
-// steps each, and the end of the cycle as one more. Between step graphs the
-// host reads one counter (instances still iterating) and ends the cycle when
-// it is zero; after a cycle it reads the number of instances still active.
-// An instance stops contributing once its residual estimate meets its target;
-// its later basis vectors are zero.
+// instance's chunks. The whole solve is one CUDA graph, launched once: a
+// conditional WHILE node over restart cycles, whose body is a WHILE node over
+// the Arnoldi steps (the step index lives on the device) followed by the end
+// of the cycle (least squares, x += Z y, the FP64 true residual and the
+// convergence flags). Device kernels end each loop when no instance is still
+// iterating (steps) or active (cycles); the restart length and the cycle cap
+// derived from max_iters bound them. An instance stops contributing once its
+// residual estimate meets its target; its later basis vectors are zero.
 #include <cmath>
 #include <cstring>
 
@@ -134,12 +134,15 @@ __global__ void k_fill_mub(int64_t n_cells, const int* __restrict__ cell_inst,
 
 // ------------------------------------------------------------------ segmented Krylov kernels
 // partial[chunk][j] = sum over the chunk of V_j * w (j < nvec), V row-major [nvec][ld]
+// (nvec_dev != nullptr: nvec = *nvec_dev + 1, the Arnoldi step index kept on the device)
 template <class VT>
 __global__ void __launch_bounds__(kSegThreads)
 k_seg_dots(const int64_t* __restrict__ beg, const int64_t* __restrict__ end, const VT* __restrict__ V,
            int64_t ld, int nvec, const double* __restrict__ w, double* __restrict__ partial,
-           int pld, const int* __restrict__ inst, const int* __restrict__ run) {
+           int pld, const int* __restrict__ inst, const int* __restrict__ run,
+           const int* __restrict__ nvec_dev) {
     __shared__ double sh[kSegThreads / 32];
+    if (nvec_dev) nvec = *nvec_dev + 1;
     const int c = blockIdx.x;
     if (run && !run[inst[c]]) return;  // this instance skips the pass (its partials are unused)
     const int64_t b0 = beg[c], b1 = end[c];
@@ -155,7 +158,8 @@ k_seg_dots(const int64_t* __restrict__ beg, const int64_t* __restrict__ end, con
 // out[b][j] = sum over b's chunks (in order) of partial[chunk][j]
 __global__ void k_seg_finish(int nb, const int* __restrict__ inst_ch, const double* __restrict__ partial,
                              int pld, int nvec, double* __restrict__ out, int old,
-                             const int* __restrict__ run) {
+                             const int* __restrict__ run, const int* __restrict__ nvec_dev) {
+    if (nvec_dev) nvec = *nvec_dev + 1;
     const int b = blockIdx.x;
     if (b >= nb) return;
     if (run && !run[b]) return;  // out keeps what k_batch_reorth_flags wrote
@@ -172,8 +176,9 @@ __global__ void __launch_bounds__(kSegThreads)
 k_seg_axpy(const int* __restrict__ inst, const int64_t* __restrict__ beg,
            const int64_t* __restrict__ end, const VT* __restrict__ V, int64_t ld, int nvec,
            const double* __restrict__ coef, int cld, double sign, double* __restrict__ w,
-           const int* __restrict__ run) {
+           const int* __restrict__ run, const int* __restrict__ nvec_dev = nullptr) {
     __shared__ double cs[64];
+    if (nvec_dev) nvec = *nvec_dev + 1;
     const int c = blockIdx.x;
     const int b = inst[c];
     if (run && !run[b]) return;
@@ -197,6 +202,37 @@ k_seg_scale(const int* __restrict__ inst, const int64_t* __restrict__ beg,
     for (int64_t i = beg[c] + threadIdx.x; i < end[c]; i += blockDim.x) y[i] = a * x[i];
 }
 
+// V[j + 1] = x / div[b] with j = *jdev (nothing when j + 1 == m)
+__global__ void __launch_bounds__(kSegThreads)
+k_seg_scale_next(const int* __restrict__ inst, const int64_t* __restrict__ beg,
+                 const int64_t* __restrict__ end, const double* __restrict__ x,
+                 const double* __restrict__ div, double* __restrict__ V, int64_t ld,
+                 const int* __restrict__ jdev, int m) {
+    const int j = *jdev;
+    if (j + 1 >= m) return;
+    const int c = blockIdx.x;
+    const double d = div[inst[c]];
+    const double a = (d != 0.0) ? 1.0 / d : 0.0;
+    double* y = V + (int64_t)(j + 1) * ld;
+    for (int64_t i = beg[c] + threadIdx.x; i < end[c]; i += blockDim.x) y[i] = a * x[i];
+}
+
+// out = column *jdev of V (V row-major [.][ld]), or column *jdev of Z = in
+template <class T>
+__global__ void k_take_col(int64_t n, const T* __restrict__ V, int64_t ld, const int* __restrict__ jdev,
+                           T* __restrict__ out) {
+    const T* v = V + (int64_t)(*jdev) * ld;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = v[i];
+}
+template <class T>
+__global__ void k_put_col(int64_t n, const T* __restrict__ in, T* __restrict__ Z, int64_t ld,
+                          const int* __restrict__ jdev) {
+    T* z = Z + (int64_t)(*jdev) * ld;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) z[i] = in[i];
+}
+
 struct BatchDev {
     double *H, *cs, *sn, *g, *y, *hcol, *hcol2, *nrm2, *hn, *beta, *bnorm, *target, *relres;
     int *ncol, *active, *status, *iters, *n_active;
@@ -207,7 +243,8 @@ struct BatchDev {
 
 // Column j of every instance's Hessenberg matrix: rotations, residual estimate,
 // freeze test. One thread per instance.
-__global__ void k_batch_givens(int nb, int j, int m, BatchDev d) {
+__global__ void k_batch_givens(int nb, int j, int m, BatchDev d, const int* __restrict__ jdev) {
+    if (jdev) j = *jdev;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     if (!d.active[b] || d.ncol[b] <= j) {  // done, or frozen earlier in this cycle
@@ -255,7 +292,9 @@ __global__ void k_batch_givens(int nb, int j, int m, BatchDev d) {
 
 // Second Gram-Schmidt pass needed? (DGKS test per instance, against the norm
 // before the first pass). hcol2 is zeroed for the instances that skip it.
-__global__ void k_batch_reorth_flags(int nb, int j, int pld, double eta2, BatchDev d) {
+__global__ void k_batch_reorth_flags(int nb, int j, int pld, double eta2, BatchDev d,
+                                     const int* __restrict__ jdev) {
+    if (jdev) j = *jdev;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     const bool live = d.active[b] && d.ncol[b] > j;
@@ -320,6 +359,31 @@ __global__ void k_batch_check(int nb, int m, double rtol, double inner_rtol, int
     g[0] = nrm;
     d.target[b] = mixed ? fmax(inner_rtol * nrm, 0.5 * rtol * d.bnorm[b]) : rtol * d.bnorm[b];
     atomicAdd(d.n_active, 1);
+}
+
+// Loop control of the persistent solve graph (one thread). End of an Arnoldi
+// step: advance j; repeat while some instance still iterates and j < m.
+__global__ void k_iter_advance(int* __restrict__ jdev, const int* __restrict__ n_iter, int m,
+                               int* __restrict__ n_steps, cudaGraphConditionalHandle h_iter) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = *jdev + 1;
+    *jdev = j;
+    *n_steps += 1;
+    cudaGraphSetConditional(h_iter, (*n_iter > 0 && j < m) ? 1u : 0u);
+}
+// End of a restart cycle: another cycle while some instance is active and the
+// cycle cap (from max_iters) is not reached; the next cycle starts at j = 0.
+__global__ void k_cycle_advance(int* __restrict__ jdev, const int* __restrict__ n_active,
+                                int* __restrict__ n_cycles, int max_cycles,
+                                cudaGraphConditionalHandle h_cycle,
+                                cudaGraphConditionalHandle h_iter) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int c = *n_cycles + 1;
+    *n_cycles = c;
+    *jdev = 0;
+    const bool more = *n_active > 0 && c < max_cycles;
+    cudaGraphSetConditional(h_cycle, more ? 1u : 0u);
+    cudaGraphSetConditional(h_iter, more ? 1u : 0u);
 }
 
 __global__ void k_sqrt_copy(int nb, const double* __restrict__ a, double* __restrict__ out) {
@@ -554,11 +618,12 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
                st.get(), it.get(), n_active.get(), nrm0.get(), reo.get(), n_iter.get()};
     const double* f = P.f.get();
     auto seg_dot = [&](const double* Vv, int64_t ld, int nvec, const double* wv, double* out, int old,
-                       const int* run) {
+                       const int* run, const int* nvec_dev = nullptr) {
         k_seg_dots<double><<<nch, kSegThreads, 0, s>>>(d_cb.get(), d_ce.get(), Vv, ld, nvec, wv,
-                                                       partial.get(), pld, d_ci.get(), run);
+                                                       partial.get(), pld, d_ci.get(), run, nvec_dev);
         DPP_LAUNCH_CK();
-        k_seg_finish<<<nb, 64, 0, s>>>(nb, d_ich.get(), partial.get(), pld, nvec, out, old, run);
+        k_seg_finish<<<nb, 64, 0, s>>>(nb, d_ich.get(), partial.get(), pld, nvec, out, old, run,
+                                       nvec_dev);
         DPP_LAUNCH_CK();
     };
     // ||f_b||, initial x, residual and flags
@@ -579,43 +644,57 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
     };
     tail();
     const double eta = std::min(std::max(o.reorth_eta, 0.0), 1.0);
-    // Arnoldi step j for every instance: classical Gram-Schmidt, and a second
-    // pass for the instances whose first pass left less than eta of ||w||
-    auto iteration = [&](int j) {
-        double* vj = V.get() + (size_t)j * n;
+    // Loop state on the device: the Arnoldi step j of the current cycle, and
+    // counters of the steps and cycles run (for the launch accounting).
+    DBuf<int> loop(3);  // [0] j, [1] steps run, [2] cycles run
+    int* jdev = loop.get();
+    DPP_CK(cudaMemsetAsync(loop.get(), 0, 3 * sizeof(int), s));
+    // The preconditioner and K read and write fixed vectors; column j of V is
+    // copied in and the preconditioned vector copied out to column j of Z.
+    DBuf<double> vcur(n), zcur(mixed ? 1 : n);
+    DBuf<float> zcur32(mixed ? n : 1);
+    const int cgrid = (int)std::min<int64_t>((n + 255) / 256, 8 * kSMs);
+    // Arnoldi step j = *jdev for every instance: classical Gram-Schmidt, and a
+    // second pass for the instances whose first pass left less than eta of ||w||
+    auto iteration = [&](cudaGraphConditionalHandle h_iter) {
+        k_take_col<double><<<cgrid, 256, 0, s>>>(n, V.get(), n, jdev, vcur.get());
+        DPP_LAUNCH_CK();
         if (mixed) {
-            float* zj = Z32.get() + (size_t)j * n;
-            pc_apply32(P, pc, vj, zj, false, s);
-            apply_K32(P, zj, w.get(), false, s);
+            pc_apply32(P, pc, vcur.get(), zcur32.get(), false, s);
+            k_put_col<float><<<cgrid, 256, 0, s>>>(n, zcur32.get(), Z32.get(), n, jdev);
+            DPP_LAUNCH_CK();
+            apply_K32(P, zcur32.get(), w.get(), false, s);
         } else {
-            double* zj = Z.get() + (size_t)j * n;
-            pc_apply(P, pc, vj, zj, false, s);
-            apply_K(P, zj, w.get(), nullptr, false, false, s);
+            pc_apply(P, pc, vcur.get(), zcur.get(), false, s);
+            k_put_col<double><<<cgrid, 256, 0, s>>>(n, zcur.get(), Z.get(), n, jdev);
+            DPP_LAUNCH_CK();
+            apply_K(P, zcur.get(), w.get(), nullptr, false, false, s);
         }
         seg_dot(w.get(), 0, 1, w.get(), nrm0.get(), 1, nullptr);
-        seg_dot(V.get(), n, j + 1, w.get(), hcol.get(), pld, nullptr);
-        k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1,
-                                                       hcol.get(), pld, -1.0, w.get(), nullptr);
+        seg_dot(V.get(), n, 1, w.get(), hcol.get(), pld, nullptr, jdev);
+        k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, 1,
+                                                       hcol.get(), pld, -1.0, w.get(), nullptr, jdev);
         DPP_LAUNCH_CK();
         seg_dot(w.get(), 0, 1, w.get(), nrm2.get(), 1, nullptr);
-        k_batch_reorth_flags<<<g1(nb), 128, 0, s>>>(nb, j, pld, eta * eta, d);
+        k_batch_reorth_flags<<<g1(nb), 128, 0, s>>>(nb, 0, pld, eta * eta, d, jdev);
         DPP_LAUNCH_CK();
-        seg_dot(V.get(), n, j + 1, w.get(), hcol2.get(), pld, reo.get());
-        k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, j + 1,
-                                                       hcol2.get(), pld, -1.0, w.get(), reo.get());
+        seg_dot(V.get(), n, 1, w.get(), hcol2.get(), pld, reo.get(), jdev);
+        k_seg_axpy<double><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), V.get(), n, 1,
+                                                       hcol2.get(), pld, -1.0, w.get(), reo.get(), jdev);
         DPP_LAUNCH_CK();
         seg_dot(w.get(), 0, 1, w.get(), nrm2.get(), 1, reo.get());
         DPP_CK(cudaMemsetAsync(n_iter.get(), 0, sizeof(int), s));
-        k_batch_givens<<<g1(nb), 128, 0, s>>>(nb, j, m, d);
+        k_batch_givens<<<g1(nb), 128, 0, s>>>(nb, 0, m, d, jdev);
         DPP_LAUNCH_CK();
-        if (j + 1 < m) {
-            k_seg_scale<<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), w.get(), hn.get(),
-                                                    V.get() + (size_t)(j + 1) * n);
-            DPP_LAUNCH_CK();
-        }
+        k_seg_scale_next<<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), w.get(), hn.get(),
+                                                     V.get(), n, jdev, m);
+        DPP_LAUNCH_CK();
+        k_iter_advance<<<1, 32, 0, s>>>(jdev, n_iter.get(), m, loop.get() + 1, h_iter);
+        DPP_LAUNCH_CK();
     };
-    auto finish = [&]() {  // least squares, x += Z y, true residual and test
-        k_batch_lsq<<<g1(nb), 128, 0, s>>>(nb, m, d);
+    const int max_cycles = (o.max_iters + m - 1) / m + 1;
+    auto finish = [&](cudaGraphConditionalHandle h_cycle, cudaGraphConditionalHandle h_iter) {
+        k_batch_lsq<<<g1(nb), 128, 0, s>>>(nb, m, d);  // least squares, x += Z y, true residual, test
         DPP_LAUNCH_CK();
         if (mixed)
             k_seg_axpy<float><<<nch, kSegThreads, 0, s>>>(d_ci.get(), d_cb.get(), d_ce.get(), Z32.get(), n, m,
@@ -625,66 +704,70 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
                                                            y.get(), m, 1.0, x, nullptr);
         DPP_LAUNCH_CK();
         tail();
+        k_cycle_advance<<<1, 32, 0, s>>>(jdev, n_active.get(), loop.get() + 2, max_cycles, h_cycle,
+                                         h_iter);
+        DPP_LAUNCH_CK();
     };
-    // A restart cycle runs as chunks of kChunkIters Arnoldi steps, each chunk
-    // captured once as a CUDA graph. After a chunk the host reads how many
-    // instances are still iterating and ends the cycle early when none is;
-    // the end of the cycle is one more graph.
-    constexpr int kChunkIters = 5;
-    const int n_chunks = (m + kChunkIters - 1) / kChunkIters;
-    struct Graph {
+    // The whole solve is one CUDA graph: a WHILE node over restart cycles whose
+    // body is a WHILE node over Arnoldi steps followed by the end of the
+    // cycle. The device ends each loop (cudaGraphSetConditional) when no
+    // instance is still iterating or active; the iteration and cycle caps
+    // bound both. The host launches the graph once and waits once.
+    struct GraphGuard {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t e = nullptr;
-        size_t nodes = 0;
-    };
-    std::vector<Graph> graphs(n_chunks + 1);
-    auto destroy_graphs = [&]() {
-        for (auto& gr : graphs) {
-            if (gr.e) cudaGraphExecDestroy(gr.e);
-            if (gr.g) cudaGraphDestroy(gr.g);
-            gr.e = nullptr;
-            gr.g = nullptr;
+        ~GraphGuard() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
         }
-    };
-    auto capture = [&](Graph& gr, auto&& body) {
-        DPP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    } G;
+    auto capture_into = [&](cudaGraph_t target, const cudaGraphNode_t* deps, size_t ndeps,
+                            auto&& body) {
+        DPP_CK(cudaStreamBeginCaptureToGraph(s, target, deps, nullptr, ndeps,
+                                             cudaStreamCaptureModeThreadLocal));
         try {
             body();
         } catch (...) {
             cudaGraph_t tmp = nullptr;
             cudaStreamEndCapture(s, &tmp);
-            if (tmp) cudaGraphDestroy(tmp);
             throw;
         }
-        DPP_CK(cudaStreamEndCapture(s, &gr.g));
-        DPP_CK(cudaGraphInstantiate(&gr.e, gr.g, 0));
-        DPP_CK(cudaGraphGetNodes(gr.g, nullptr, &gr.nodes));
+        cudaGraph_t out = nullptr;
+        DPP_CK(cudaStreamEndCapture(s, &out));
+    };
+    auto while_node = [&](cudaGraph_t parent, cudaGraphConditionalHandle h, cudaGraphNode_t* node,
+                          cudaGraph_t* body) {
+        cudaGraphNodeParams prm{};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = h;
+        prm.conditional.type = cudaGraphCondTypeWhile;
+        prm.conditional.size = 1;
+        DPP_CK(cudaGraphAddNode(node, parent, nullptr, nullptr, 0, &prm));
+        *body = prm.conditional.phGraph_out[0];
     };
     int active_now = read_scalar(n_active.get(), s, hs);
-    const int max_cycles = (o.max_iters + m - 1) / m + 1;
-    try {
-        if (active_now > 0) {
-            for (int k = 0; k < n_chunks; ++k)
-                capture(graphs[k], [&]() {
-                    for (int j = k * kChunkIters; j < std::min(m, (k + 1) * kChunkIters); ++j) iteration(j);
-                });
-            capture(graphs[n_chunks], finish);
-        }
-        for (int cyc = 0; cyc < max_cycles && active_now > 0; ++cyc) {
-            for (int k = 0; k < n_chunks; ++k) {
-                DPP_CK(cudaGraphLaunch(graphs[k].e, s));
-                graph_launches += (int64_t)graphs[k].nodes;
-                if (k + 1 < n_chunks && read_scalar(n_iter.get(), s, hs) == 0) break;
-            }
-            DPP_CK(cudaGraphLaunch(graphs[n_chunks].e, s));
-            graph_launches += (int64_t)graphs[n_chunks].nodes;
-            active_now = read_scalar(n_active.get(), s, hs);
-        }
-    } catch (...) {
-        destroy_graphs();
-        throw;
+    if (active_now > 0) {
+        DPP_CK(cudaGraphCreate(&G.g, 0));
+        cudaGraphConditionalHandle h_cycle, h_iter;
+        DPP_CK(cudaGraphConditionalHandleCreate(&h_cycle, G.g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNode_t w_cycle, w_iter;
+        cudaGraph_t body_cycle, body_iter;
+        while_node(G.g, h_cycle, &w_cycle, &body_cycle);
+        DPP_CK(cudaGraphConditionalHandleCreate(&h_iter, body_cycle, 1, cudaGraphCondAssignDefault));
+        while_node(body_cycle, h_iter, &w_iter, &body_iter);
+        capture_into(body_iter, nullptr, 0, [&]() { iteration(h_iter); });
+        capture_into(body_cycle, &w_iter, 1, [&]() { finish(h_cycle, h_iter); });
+        DPP_CK(cudaGraphInstantiate(&G.e, G.g, 0));
+        DPP_CK(cudaGraphLaunch(G.e, s));
+        size_t n_iter_nodes = 0, n_cycle_nodes = 0;
+        DPP_CK(cudaGraphGetNodes(body_iter, nullptr, &n_iter_nodes));
+        DPP_CK(cudaGraphGetNodes(body_cycle, nullptr, &n_cycle_nodes));
+        int counts[3];
+        DPP_CK(cudaMemcpyAsync(counts, loop.get(), 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        DPP_CK(cudaStreamSynchronize(s));
+        graph_launches += (int64_t)counts[1] * (int64_t)n_iter_nodes +
+                          (int64_t)counts[2] * (int64_t)(n_cycle_nodes - 1);
     }
-    destroy_graphs();
     status.resize(nb);
     iters.resize(nb);
     relres.resize(nb);
