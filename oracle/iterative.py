@@ -134,7 +134,7 @@ def gmres_right(K, f, apply_pc, tol: float = 1e-13, restart: int = 100, max_iter
 
 
 def solve_field_split_gmres(K, f, n_nodes: int, d: int, tol: float = 1e-13, restart: int = 100):
-    """Solve K x = f (slot-major) by GMRES with the exact-piece field-split preconditioner.
+    """Solve K x = f (slot-major) by flexible GMRES with the field-split preconditioner.
 
     Returns (x, iterations, true relative residual).
     """
