@@ -299,7 +299,7 @@ dpp_status dpp_apply_K_mf(dpp_problem prob, int32_t transpose, const double* x, 
 /* As dpp_apply_K_mf with FP32 geometry, k, x and arithmetic, and FP64 output:
  * the matrix-free counterpart of dpp_apply_K32. The first call makes FP32
  * copies of the coordinates and k (kept with the problem). x: device float
- * [n_nodes][2d+2]; y: device double. */
+ * [n_nodes][2d+2], 16-byte aligned; y: device double. */
 dpp_status dpp_apply_K32_mf(dpp_problem prob, int32_t transpose, const float* x, double* y,
                             dpp_stream_t stream);
 

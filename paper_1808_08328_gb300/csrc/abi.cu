@@ -609,6 +609,7 @@ dpp_status dpp_apply_K32_mf(dpp_problem prob, int32_t transpose, const float* x,
     return guarded("dpp_apply_K32_mf", [&]() -> dpp_status {
         StreamScope scope_((cudaStream_t)stream);
         require(prob && x && y, "null argument");
+        require_aligned(x, "x");
         if (prob->impl.kind != DPP_CELL_SIMPLEX)
             fail(DPP_ERR_BAD_STATE, "the matrix-free apply supports simplices only");
         matrix_free_prepare32(prob->impl, (cudaStream_t)stream);

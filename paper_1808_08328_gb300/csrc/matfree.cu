@@ -37,8 +37,15 @@ namespace {
 
 template <class T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// The FP32 3D path reads through vector loads: coordinates padded to float4,
+// the node's 8 unknowns as two float4, the cell's 4 vertex ids as one int4.
+template <int DIM, class T> struct MfVec {
+    static constexpr bool on = (DIM == 3) && sizeof(T) == 4;
+    static constexpr int xs = on ? 4 : DIM;  // coordinate stride
+};
+
 template <int DIM, class T, class YT, bool TRANS, int G>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4) ? 4 : 2)
 k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restrict__ nc_list,
              const int* __restrict__ cells, const T* __restrict__ X, const T* __restrict__ kk,
              const T* __restrict__ mub, T mu, T beta, const T* __restrict__ x,
@@ -51,6 +58,8 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
     const int lane = (int)(t % G);
     // whole groups leave together, so the group shuffles below see full groups
     if (a >= n_nodes) return;
+    using V = MfVec<DIM, T>;
+    constexpr int XS = V::xs;
     const T sB = TRANS ? T(-1) : T(1);
     T acc[NS];
 #pragma unroll
@@ -59,16 +68,34 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
     for (int q = nc_ptr[a] + lane; q < q1; q += G) {
         const int c = nc_list[q];
         int v[NV];
+        if constexpr (V::on) {
+            const int4 cv = __ldg(reinterpret_cast<const int4*>(cells) + c);
+            v[0] = cv.x;
+            v[1] = cv.y;
+            v[2] = cv.z;
+            v[3] = cv.w;
+        } else {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = ld(cells + (int64_t)c * NV + k);
+            for (int k = 0; k < NV; ++k) v[k] = ld(cells + (int64_t)c * NV + k);
+        }
         // geometry: J = [x_1 - x_0, ..., x_d - x_0]; g_{k+1} = row k of J^-1
-        T x0[DIM], J[DIM][DIM];
+        T xv[NV][DIM], J[DIM][DIM];
 #pragma unroll
-        for (int r = 0; r < DIM; ++r) x0[r] = ld(X + (int64_t)v[0] * DIM + r);
+        for (int k = 0; k < NV; ++k) {
+            if constexpr (V::on) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(X) + v[k]);
+                xv[k][0] = q.x;
+                xv[k][1] = q.y;
+                xv[k][2] = q.z;
+            } else {
+#pragma unroll
+                for (int r = 0; r < DIM; ++r) xv[k][r] = ld(X + (int64_t)v[k] * XS + r);
+            }
+        }
 #pragma unroll
         for (int q2 = 0; q2 < DIM; ++q2)
 #pragma unroll
-            for (int r = 0; r < DIM; ++r) J[r][q2] = ld(X + (int64_t)v[q2 + 1] * DIM + r) - x0[r];
+            for (int r = 0; r < DIM; ++r) J[r][q2] = xv[q2 + 1][r] - xv[0][r];
         T g[NV][DIM], det;
         if constexpr (DIM == 2) {
             det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
@@ -102,7 +129,7 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
             for (int k = 1; k < NV; ++k) s += g[k][r];
             g[0][r] = -s;
         }
-        const T vol = fabs(det) / T(DIM == 2 ? 2 : 6);
+        const T vol = (det < T(0) ? -det : det) / T(DIM == 2 ? 2 : 6);
         // the cell-level sums, and the row node's own values
         T Su1[DIM], Su2[DIM], Gp1[DIM], Gp2[DIM], ua1[DIM], ua2[DIM], ga[DIM];
         T Sp1 = 0, Sp2 = 0, dv1 = 0, dv2 = 0, pa1 = 0, pa2 = 0;
@@ -111,13 +138,27 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
 #pragma unroll
         for (int b = 0; b < NV; ++b) {
             const T* xb = x + (int64_t)v[b] * NS;
-            T u1[DIM], u2[DIM];
+            T u1[DIM], u2[DIM], p1, p2;
+            if constexpr (V::on) {
+                const float4 lo = __ldg(reinterpret_cast<const float4*>(xb));
+                const float4 hi = __ldg(reinterpret_cast<const float4*>(xb) + 1);
+                u1[0] = lo.x;
+                u1[1] = lo.y;
+                u1[2] = lo.z;
+                p1 = lo.w;
+                u2[0] = hi.x;
+                u2[1] = hi.y;
+                u2[2] = hi.z;
+                p2 = hi.w;
+            } else {
 #pragma unroll
-            for (int r = 0; r < DIM; ++r) {
-                u1[r] = ld(xb + r);
-                u2[r] = ld(xb + DIM + 1 + r);
+                for (int r = 0; r < DIM; ++r) {
+                    u1[r] = ld(xb + r);
+                    u2[r] = ld(xb + DIM + 1 + r);
+                }
+                p1 = ld(xb + DIM);
+                p2 = ld(xb + 2 * DIM + 1);
             }
-            const T p1 = ld(xb + DIM), p2 = ld(xb + 2 * DIM + 1);
             const bool self = (v[b] == (int)a);
 #pragma unroll
             for (int r = 0; r < DIM; ++r) {
@@ -140,7 +181,15 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
                 pa2 = p2;
             }
         }
-        const T k1 = ld(kk + 2 * (int64_t)c), k2 = ld(kk + 2 * (int64_t)c + 1);
+        T k1, k2;
+        if constexpr (V::on) {
+            const float2 kv = __ldg(reinterpret_cast<const float2*>(kk) + c);
+            k1 = kv.x;
+            k2 = kv.y;
+        } else {
+            k1 = ld(kk + 2 * (int64_t)c);
+            k2 = ld(kk + 2 * (int64_t)c + 1);
+        }
         const T muc = mub ? ld(mub + 2 * (int64_t)c) : mu;
         const T bc = mub ? ld(mub + 2 * (int64_t)c + 1) : beta;
         const T cm = vol / T((DIM + 1) * (DIM + 2));
@@ -175,6 +224,15 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
         if (s % G == lane) ya[s] = (YT)acc[s];
 }
 
+__global__ void k_pad_coords(int64_t n, const double* __restrict__ X, float* __restrict__ X4) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    X4[4 * i] = (float)X[3 * i];
+    X4[4 * i + 1] = (float)X[3 * i + 1];
+    X4[4 * i + 2] = (float)X[3 * i + 2];
+    X4[4 * i + 3] = 0.0f;
+}
+
 __global__ void k_mf_float_copy(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
@@ -196,7 +254,7 @@ void apply_mf_dim(const ProblemImpl& P, const T* x, YT* y, bool tr, cudaStream_t
     const double n = (double)P.n_nodes, nc = (double)P.n_cells;
     const double alg = (n + 1) * 4.0 + nc * (DIM + 1) * 4.0 * 2.0 +
                        nc * 2.0 * sizeof(T) * (P.cell_mu_beta.get() ? 2.0 : 1.0) +
-                       n * DIM * sizeof(T) + n * P.ns * (double)(sizeof(T) + sizeof(YT));
+                       n * MfVec<DIM, T>::xs * sizeof(T) + n * P.ns * (double)(sizeof(T) + sizeof(YT));
     ProfScope prof(sizeof(T) == 8 ? "apply_K_mf" : "apply_K_mf_fp32", s, alg);
     const int B = 256;
     const int grid = grid_for(P.n_nodes * G, B);
@@ -225,7 +283,14 @@ void to_f32(const DBuf<double>& in, DBuf<float>& out, cudaStream_t s) {
 
 void matrix_free_prepare32(ProblemImpl& P, cudaStream_t s) {
     if (P.coords32.get()) return;
-    to_f32(P.coords, P.coords32, s);
+    if (P.dim == 3) {  // padded to 4 floats per node for one float4 load
+        P.coords32.alloc(P.n_nodes * 4);
+        k_pad_coords<<<grid_for(P.n_nodes, 256), 256, 0, s>>>(P.n_nodes, P.coords.get(),
+                                                               P.coords32.get());
+        DPP_LAUNCH_CK();
+    } else {
+        to_f32(P.coords, P.coords32, s);
+    }
     to_f32(P.kk, P.kk32, s);
     if (P.cell_mu_beta.get()) to_f32(P.cell_mu_beta, P.cell_mu_beta32, s);
 }
