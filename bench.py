@@ -428,12 +428,14 @@ def bench_gb300(args):
         # batched workload: one dpp_solve_batched call per step
         from paper_1808_08328_gb300.system import DPPBatch
         bt = DPPBatch(batch_problems(BATCH["n_inst"], BATCH["seed"]), device=dev)
-        _, binfo, bst = bt.solve(precision=1, rtol=1e-10)  # warm
+        # the schedule autotuner runs in the warm-up call and is cached after it
+        tuned = {"schedule_tuning": 1}
+        _, binfo, bst = bt.solve(precision=1, pc_opts=tuned, rtol=1e-10)  # warm
         torch.cuda.synchronize(dev)
         e2.record(torch.cuda.current_stream(dev))
         bsteps = max(1, args.steps // 2)
         for _ in range(bsteps):
-            _, binfo, bst = bt.solve(precision=1, rtol=1e-10)
+            _, binfo, bst = bt.solve(precision=1, pc_opts=tuned, rtol=1e-10)
         e3.record(torch.cuda.current_stream(dev))
         torch.cuda.synchronize(dev)
         bms = e2.elapsed_time(e3) / bsteps
@@ -460,6 +462,7 @@ def bench_gb300(args):
                               "max_rel_residual": worst}
         modes["batched_vs_one_by_one"] = seq
         modes["batched_config"] = {"instances": BATCH["n_inst"], "dofs": bt.n_dofs,
+                                   "schedule": "autotuned (dpp_pc_opts.schedule_tuning)",
                                    "ms_per_step": bms, "status": bst,
                                    "max_rel_residual": max(i["rel_residual"] for i in binfo),
                                    "max_iterations": max(i["iterations"] for i in binfo),

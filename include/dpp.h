@@ -134,6 +134,14 @@ typedef struct {
                                   1: ILU(0) of each network's mass matrix in natural row order,
                                   the paper's block Jacobi / ILU(0) sub-solver (Sections 4.1,
                                   4.2); level-scheduled, one launch per dependency level. */
+    int32_t schedule_tuning;   /* dpp_solve_batched only. 1: the preconditioner schedule (AMG
+                                  Chebyshev degree, cheb_ratio, mass Chebyshev degree) is chosen
+                                  by timing candidate batched solves on the hierarchy already
+                                  built (coordinate search over {1,2,3}, {10,20,30}, {1,2,3}),
+                                  once per size class (dimension, precision, log2 of the union's
+                                  nodes and of the mean instance's); the choice is cached for
+                                  the process and in the DPP_TUNE_CACHE file if one is named.
+                                  0: the schedule given (default). */
 } dpp_pc_opts;
 
 /* Krylov options. */

@@ -28,6 +28,8 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
                     std::vector<int>& status, std::vector<int>& iters,
                     std::vector<double>& relres, int64_t& graph_launches, cudaStream_t s,
                     HostScratch& hs);
+void tune_batched_schedule(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o,
+                           cudaStream_t s, HostScratch& hs);
 }  // namespace dpp
 
 namespace dpp {
@@ -218,6 +220,7 @@ void dpp_pc_opts_default(dpp_pc_opts* o) {
     o->spmv_format = 0;
     o->composition = 0;
     o->mass_solver = 0;
+    o->schedule_tuning = 0;
 }
 
 void dpp_solve_opts_default(dpp_solve_opts* o) {
@@ -310,6 +313,7 @@ dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t 
                 "composition in {0 (field split), 1 (scale split)}");
         require(o.mass_solver == 0 || o.mass_solver == 1,
                 "mass_solver in {0 (Chebyshev-Jacobi), 1 (ILU(0))}");
+        require(o.schedule_tuning == 0 || o.schedule_tuning == 1, "schedule_tuning in {0,1}");
         cudaStream_t s = (cudaStream_t)stream;
         auto* h = new dpp_pc_s();
         try {
@@ -472,7 +476,9 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
         pc.impl.opts = po;
         pc.impl.precision = po.precision;
         pc.owner = &prob;
+        require(po.schedule_tuning == 0 || po.schedule_tuning == 1, "schedule_tuning in {0,1}");
         pc_setup(pc.impl, prob.impl, s);
+        if (po.schedule_tuning) tune_batched_schedule(prob.impl, pc.impl, o, s, prob.impl.hs);
         const double ms_setup = tb.stop();
         const ProblemImpl& P = prob.impl;
         const int64_t n = P.n_nodes * P.ns;

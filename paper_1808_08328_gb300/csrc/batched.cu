@@ -25,7 +25,12 @@
 // derived from max_iters bound them. An instance stops contributing once its
 // residual estimate meets its target; its later basis vectors are zero.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "amg.cuh"
 
@@ -775,6 +780,151 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
     DPP_CK(cudaMemcpyAsync(iters.data(), it.get(), nb * sizeof(int), cudaMemcpyDeviceToHost, s));
     DPP_CK(cudaMemcpyAsync(relres.data(), rel.get(), nb * sizeof(double), cudaMemcpyDeviceToHost, s));
     DPP_CK(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ schedule autotuner
+// The preconditioner schedule of the batched solve: the AMG Chebyshev degree,
+// the AMG Chebyshev interval ratio and the mass Chebyshev degree. None of
+// them changes the setup (aggregates, Galerkin products, lambda_max), so the
+// candidates are timed as full batched solves on the one hierarchy already
+// built, by a coordinate search from the given schedule: the AMG degree in
+// {1, 2, 3}, then the ratio in {10, 20, 30}, then the mass degree in
+// {1, 2, 3}. A candidate that leaves an instance unconverged is dropped. The
+// choice is cached for the process per size class (dimension, precision,
+// log2 of the union's nodes, log2 of the mean nodes per instance); if
+// DPP_TUNE_CACHE names a file, choices are read from it and new ones appended.
+namespace {
+struct SchedKey {
+    int dim, fp32, log2_nodes, log2_mean;
+    bool operator<(const SchedKey& o) const {
+        return std::tie(dim, fp32, log2_nodes, log2_mean) <
+               std::tie(o.dim, o.fp32, o.log2_nodes, o.log2_mean);
+    }
+};
+struct Sched {
+    int amg, mass;
+    double ratio;
+};
+std::mutex g_sched_mu;
+std::map<SchedKey, Sched> g_sched;
+bool g_sched_loaded = false;
+
+int ilog2(int64_t v) {
+    int r = 0;
+    while (v > 1) { v >>= 1; ++r; }
+    return r;
+}
+
+void sched_load_locked() {
+    if (g_sched_loaded) return;
+    g_sched_loaded = true;
+    const char* path = std::getenv("DPP_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        SchedKey k;
+        Sched v;
+        if (std::sscanf(line,
+                        "{\"schedule\": 1, \"dim\": %d, \"fp32\": %d, \"log2_nodes\": %d, "
+                        "\"log2_mean\": %d, \"amg\": %d, \"mass\": %d, \"ratio\": %lf}",
+                        &k.dim, &k.fp32, &k.log2_nodes, &k.log2_mean, &v.amg, &v.mass,
+                        &v.ratio) == 7 &&
+            v.amg >= 1 && v.amg <= 16 && v.mass >= 1 && v.mass <= 16 && v.ratio > 1)
+            g_sched[k] = v;
+    }
+    std::fclose(f);
+}
+
+void sched_store_locked(const SchedKey& k, const Sched& v) {
+    g_sched[k] = v;
+    const char* path = std::getenv("DPP_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"schedule\": 1, \"dim\": %d, \"fp32\": %d, \"log2_nodes\": %d, "
+                 "\"log2_mean\": %d, \"amg\": %d, \"mass\": %d, \"ratio\": %g}\n",
+                 k.dim, k.fp32, k.log2_nodes, k.log2_mean, v.amg, v.mass, v.ratio);
+    std::fclose(f);
+}
+}  // namespace
+
+void tune_batched_schedule(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o,
+                           cudaStream_t s, HostScratch& hs) {
+    ProfScope pr("setup_schedule_tune", s, 0);
+    SchedKey key{P.dim, pc.precision == DPP_MIXED_FP32_FP64 ? 1 : 0, ilog2(P.n_nodes),
+                 ilog2(P.n_nodes / std::max(P.n_inst, 1))};
+    {
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        sched_load_locked();
+        auto it = g_sched.find(key);
+        if (it != g_sched.end()) {
+            pc.opts.cheb_degree_amg = it->second.amg;
+            pc.opts.cheb_degree_mass = it->second.mass;
+            pc.opts.cheb_ratio = it->second.ratio;
+            return;
+        }
+    }
+    dpp_solve_opts t = o;
+    t.x0_zero = 1;
+    DBuf<double> xt(P.n_nodes * P.ns);
+    cudaEvent_t e0, e1;
+    DPP_CK(cudaEventCreate(&e0));
+    DPP_CK(cudaEventCreate(&e1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } eg{e0, e1};
+    std::map<std::tuple<int, int, double>, float> seen;
+    auto trial = [&](const Sched& c) -> float {
+        auto k = std::make_tuple(c.amg, c.mass, c.ratio);
+        auto f = seen.find(k);
+        if (f != seen.end()) return f->second;
+        pc.opts.cheb_degree_amg = c.amg;
+        pc.opts.cheb_degree_mass = c.mass;
+        pc.opts.cheb_ratio = c.ratio;
+        std::vector<int> st, it;
+        std::vector<double> rr;
+        int64_t launches = 0;
+        DPP_CK(cudaEventRecord(e0, s));
+        fgmres_batched(P, pc, t, xt.get(), st, it, rr, launches, s, hs);
+        DPP_CK(cudaEventRecord(e1, s));
+        DPP_CK(cudaEventSynchronize(e1));
+        for (int64_t q = 0; q < launches; ++q) count_launch();
+        float ms = 0;
+        DPP_CK(cudaEventElapsedTime(&ms, e0, e1));
+        for (int v : st)
+            if (v != DPP_OK) ms = 1e30f;  // a candidate must converge every instance
+        seen[k] = ms;
+        return ms;
+    };
+    Sched best{pc.opts.cheb_degree_amg, pc.opts.cheb_degree_mass, pc.opts.cheb_ratio};
+    float best_ms = trial(best);
+    for (int a : {1, 2, 3}) {
+        Sched c = best;
+        c.amg = a;
+        const float ms = trial(c);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    for (double r : {10.0, 20.0, 30.0}) {
+        Sched c = best;
+        c.ratio = r;
+        const float ms = trial(c);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    for (int m : {1, 2, 3}) {
+        Sched c = best;
+        c.mass = m;
+        const float ms = trial(c);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    pc.opts.cheb_degree_amg = best.amg;
+    pc.opts.cheb_degree_mass = best.mass;
+    pc.opts.cheb_ratio = best.ratio;
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    sched_store_locked(key, best);
 }
 
 }  // namespace dpp

@@ -17,7 +17,7 @@
 // with cm = |K| / ((d+1)(d+2)), s = +1 for K and -1 for K^T (K^T is K with the
 // K_up and K_pu blocks negated).
 //
-// Layout and order: G lanes per node take the node's incident cells in
+// Layout and order: G = 2 lanes per node take the node's incident cells in
 // increasing cell id, G apart. Each lane recomputes the cell's geometry from
 // the vertex coordinates (the inverse of the edge matrix) and gathers the four
 // (three) vertex vectors. The lanes then add their partial rows in a fixed
@@ -25,10 +25,12 @@
 //
 // Bytes per apply: the node->cell lists, the cells' vertex ids and k values,
 // the coordinates, x and y. Each is read once when L2 holds the window of cells
-// that neighbouring nodes share. At 3D 64^3 in FP32 that is about 93 MB, against
-// 220 MB for the assembled FP32 pair values. The arithmetic is about 150
-// operations per (node, cell); in FP64 the FP64 pipe bounds it, so the FP32
-// operator of the mixed-precision inner iteration is where it pays.
+// that neighbouring nodes share. At 3D 64^3 in FP32 that is about 95 MB (DRAM
+// measured 81 MB), against 220 MB for the assembled FP32 pair values. But each
+// cell's vertex data is gathered once per vertex node: about 220 B of L1
+// traffic per (node, cell), 1.45 GB per apply at 64^3. That, not DRAM, bounds
+// the kernel (96 us against 51 us for the assembled FP32 apply). In FP64 the
+// FP64 pipe bounds the recomputed geometry and the element action (3.1 ms).
 #include "kernels.cuh"
 
 namespace dpp {
@@ -52,7 +54,8 @@ k_apply_K_mf(int64_t n_nodes, const int* __restrict__ nc_ptr, const int* __restr
              YT* __restrict__ y) {
     constexpr int NV = DIM + 1;
     constexpr int NS = 2 * DIM + 2;
-    static_assert(G == 4 || G == 8 || G == 16 || G == 32, "group of lanes within a warp");
+    static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32,
+                  "group of lanes within a warp");
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t a = t / G;
     const int lane = (int)(t % G);
@@ -250,7 +253,10 @@ template <> const float* mub_of<float>(const ProblemImpl& P) { return P.cell_mu_
 
 template <int DIM, class T, class YT>
 void apply_mf_dim(const ProblemImpl& P, const T* x, YT* y, bool tr, cudaStream_t s) {
-    constexpr int G = 8;
+    // lanes per node, measured at 3D 64^3 in FP32: 1: 136 us, 2: 96 us, 4: 100 us,
+    // 8: 126 us, 16: 187 us, 32: 289 us (the group's final reduction and idle
+    // lanes cost more than the extra parallelism buys)
+    constexpr int G = 2;
     const double n = (double)P.n_nodes, nc = (double)P.n_cells;
     const double alg = (n + 1) * 4.0 + nc * (DIM + 1) * 4.0 * 2.0 +
                        nc * 2.0 * sizeof(T) * (P.cell_mu_beta.get() ? 2.0 : 1.0) +

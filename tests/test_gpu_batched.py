@@ -87,6 +87,23 @@ def test_batched_recipe_slice_matches_oracle(recipe_slice, precision):
         assert max(err.values()) <= 1e-8, (P.mesh.n, err)
 
 
+def test_batched_schedule_tuning_keeps_the_solution(recipe_slice):
+    # schedule_tuning = 1: the AMG/mass Chebyshev schedule is chosen by timing
+    # candidate solves (first call of the size class), then read from the cache
+    # (second call). The solution must meet the same bar either way.
+    system_cls()
+    from paper_1808_08328_gb300.system import solve_batched
+    probs, refs = recipe_slice
+    for _ in range(2):
+        xs, infos, st = solve_batched(probs, precision=1, rtol=1e-10,
+                                      pc_opts={"schedule_tuning": 1})
+        assert st == 0
+        for P, (K, f, ref), x, inf in zip(probs, refs, xs, infos):
+            assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10
+            err = oracle.field_rel_errors(x.cpu().numpy(), ref)
+            assert max(err.values()) <= 1e-8, (P.mesh.n, err)
+
+
 def test_batched_faults_are_per_instance():
     system_cls()
     from paper_1808_08328_gb300 import binding as B
