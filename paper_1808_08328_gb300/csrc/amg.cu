@@ -486,32 +486,6 @@ __global__ void k_smooth_p(int64_t n, const int* __restrict__ rp, const int* __r
 }
 
 // ------------------------------------------------------------------ coarse block inverse
-// Gauss-Jordan on the diagonal block [b0, b0 + nb) of the row-major n x n
-// matrix M (pivot k of the block; part 1: scale row k, keep column k in f)
-__global__ void k_gj_pivot(int n, int b0, int nb, int k, double* __restrict__ M, double* __restrict__ f) {
-    __shared__ double piv;
-    const int kk = b0 + k;
-    if (threadIdx.x == 0) piv = M[(int64_t)kk * n + kk];
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) f[i] = (i == k) ? 0.0 : M[(int64_t)(b0 + i) * n + kk];
-    __syncthreads();
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        const double v = (j == k) ? 1.0 : M[(int64_t)kk * n + b0 + j];
-        M[(int64_t)kk * n + b0 + j] = v / piv;
-    }
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-        if (i != k) M[(int64_t)(b0 + i) * n + kk] = 0.0;
-}
-
-// part 2: row_i -= f_i * row_k for every i != k of the block
-__global__ void k_gj_elim(int n, int b0, int nb, int k, double* __restrict__ M, const double* __restrict__ f) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)nb * nb) return;
-    const int i = (int)(t / nb), j = (int)(t % nb);
-    if (i == k) return;
-    M[(int64_t)(b0 + i) * n + b0 + j] -= f[i] * M[(int64_t)(b0 + k) * n + b0 + j];
-}
-
 // The coarsest matrix is inverted block by block: its contiguous diagonal
 // blocks (one per instance and network in a batched union, the two S_p blocks
 // of a single problem) are stored compactly, row-major, block c at coff[c].
@@ -570,6 +544,115 @@ __global__ void __launch_bounds__(256) k_gj_blocks(const int* __restrict__ list,
         __syncthreads();
     }
     for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) M[t] = a[t];
+}
+
+// Gauss-Jordan of the blocks above kGjSmall rows, all in one cooperative
+// launch (every CTA resident, which cudaLaunchCooperativeKernel checks). The
+// blocks stay in global memory (L2); each warp takes one block row at a time
+// and its lanes the row's columns. Pivot k of a block is one phase: with its column k (colb)
+// and row k (rowb) as they stood after pivot k - 1,
+//   M[k][j] = rowb[j] / rowb[k]               (rowb[k] is the pivot; M[k][k] = 1 / pivot)
+//   M[i][j] = M[i][j] - colb[i] M[k][j]       (i != k; column k starts from 0)
+// with one reciprocal of the pivot per row and pivot (the FP64 divide is
+// many instructions on this part).
+// and every thread that writes an element of row or column k + 1 also copies
+// it to the other half of rowb / colb, so that one grid barrier per pivot
+// separates the phases. Blocks with fewer than k + 1 rows have finished.
+// The barrier is a generation counter with a bounded wait: a wait that runs
+// out sets err[0] and every CTA returns.
+struct GjBarrier {
+    unsigned* count;
+    unsigned* gen;
+    int* err;
+};
+
+__device__ __forceinline__ bool gj_grid_barrier(const GjBarrier& b, unsigned nblocks) {
+    __shared__ int ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* genv = b.gen;
+        volatile int* errv = b.err;
+        const unsigned g = *genv;
+        __threadfence();
+        if (atomicAdd(b.count, 1u) + 1u == nblocks) {
+            *b.count = 0u;
+            __threadfence();
+            atomicAdd(b.gen, 1u);
+        } else {
+            long spins = 0;
+            while (*genv == g) {
+                if (*errv) { ok = 0; break; }
+                if (++spins > (1L << 24)) {  // far beyond any pivot phase (about a second)
+                    atomicExch(b.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_sh = ok && !*errv;
+    }
+    __syncthreads();
+    return ok_sh != 0;
+}
+
+__global__ void __launch_bounds__(256) k_gj_coop(int n_large, const int* __restrict__ list,
+                                                 const int* __restrict__ blk, double* __restrict__ inv,
+                                                 double* __restrict__ colb, double* __restrict__ rowb,
+                                                 const int* __restrict__ voff, int max_nb, GjBarrier bar) {
+    // one warp per block row at a time; rows are numbered across the blocks
+    // (voff is the prefix sum of the block sizes, searched by bisection)
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int n_rows = voff[n_large];
+    auto locate = [&](int r, int& q, int& i) {
+        int lo = 0, hi = n_large - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (voff[mid] <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        q = lo;
+        i = r - voff[lo];
+    };
+    // column 0 and row 0 of every block, before the first pivot
+    for (int r = warp; r < n_rows; r += n_warps) {
+        int q, i;
+        locate(r, q, i);
+        const int nb = blk[3 * list[q] + 1];
+        const double* M = inv + blk[3 * list[q] + 2] + (int64_t)i * nb;
+        if (lane == 0) colb[2 * voff[q] + i] = M[0];
+        if (i == 0)
+            for (int j = lane; j < nb; j += 32) rowb[2 * voff[q] + j] = M[j];
+    }
+    if (!gj_grid_barrier(bar, gridDim.x)) return;
+    for (int k = 0; k < max_nb; ++k) {
+        const int h = k & 1, hn = h ^ 1;
+        for (int r = warp; r < n_rows; r += n_warps) {
+            int q, i;
+            locate(r, q, i);
+            const int nb = blk[3 * list[q] + 1];
+            if (k >= nb) continue;
+            double* M = inv + blk[3 * list[q] + 2] + (int64_t)i * nb;
+            const double* rb = rowb + 2 * voff[q] + (int64_t)h * nb;
+            double* col_next = colb + 2 * voff[q] + (int64_t)hn * nb;
+            double* row_next = rowb + 2 * voff[q] + (int64_t)hn * nb;
+            const double rpiv = 1.0 / rb[k];
+            const double ci = (i == k) ? 0.0 : colb[2 * voff[q] + (int64_t)h * nb + i];
+            for (int j = lane; j < nb; j += 32) {
+                const double rkj = (j == k) ? rpiv : rb[j] * rpiv;
+                const double mij = (i == k || j == k) ? 0.0 : M[j];
+                const double v = (i == k) ? rkj : fma(-ci, rkj, mij);
+                M[j] = v;
+                if (j == k + 1) col_next[i] = v;
+                if (i == k + 1) row_next[j] = v;
+            }
+        }
+        if (!gj_grid_barrier(bar, gridDim.x)) return;
+    }
 }
 
 // x = Minv b for the block-diagonal inverse: one warp per row; the inverse and
@@ -649,7 +732,8 @@ std::vector<std::pair<int, int>> diag_blocks(const Csr& A, cudaStream_t s) {
 
 // Inverse of the coarsest matrix (SPD: Gauss-Jordan without pivoting), block
 // by block in compact storage. Blocks of at most kGjSmall rows are inverted
-// one CTA each in shared memory, in one launch; larger ones pivot by pivot.
+// one CTA each in shared memory, in one launch; the larger ones together in
+// one cooperative launch, one grid barrier per pivot.
 void block_inverse(Amg& pc, const Csr& A, cudaStream_t s) {
     const int64_t n = A.n_rows;
     const auto blocks = diag_blocks(A, s);
@@ -685,17 +769,40 @@ void block_inverse(Amg& pc, const Csr& A, cudaStream_t s) {
                                                                  pc.coarse_inv.get());
         DPP_LAUNCH_CK();
     }
-    DBuf<double> f(n);
+    // the larger blocks: one cooperative launch for all of them
+    std::vector<int> large, voff(1, 0);
+    int max_nb = 0;
     for (size_t c = 0; c < blocks.size(); ++c) {
         const int nb = blocks[c].second;
         if (nb <= kGjSmall) continue;
-        double* M = pc.coarse_inv.get() + blk[3 * c + 2];
-        for (int k = 0; k < nb; ++k) {
-            k_gj_pivot<<<1, 256, 0, s>>>(nb, 0, nb, k, M, f.get());
-            DPP_LAUNCH_CK();
-            k_gj_elim<<<grid_for((int64_t)nb * nb, 256), 256, 0, s>>>(nb, 0, nb, k, M, f.get());
-            DPP_LAUNCH_CK();
-        }
+        large.push_back((int)c);
+        voff.push_back(voff.back() + nb);
+        max_nb = std::max(max_nb, nb);
+    }
+    if (!large.empty()) {
+        const int nl = (int)large.size();
+        DBuf<int> d_large(nl), d_voff(nl + 1), ctl(3);  // ctl: count, generation, error
+        DBuf<double> colb(2 * (size_t)voff.back()), rowb(2 * (size_t)voff.back());
+        DPP_CK(cudaMemcpyAsync(d_large.get(), large.data(), nl * sizeof(int), cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemcpyAsync(d_voff.get(), voff.data(), (nl + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+        DPP_CK(cudaMemsetAsync(ctl.get(), 0, 3 * sizeof(int), s));
+        const int grid = std::min(kSMs, std::max(1, (voff.back() + 7) / 8));
+        int n_large = nl, mx = max_nb;
+        const int* a_list = d_large.get();
+        const int* a_blk = pc.coarse_blk.get();
+        double* a_inv = pc.coarse_inv.get();
+        double* a_col = colb.get();
+        double* a_row = rowb.get();
+        const int* a_voff = d_voff.get();
+        GjBarrier bar{reinterpret_cast<unsigned*>(ctl.get()), reinterpret_cast<unsigned*>(ctl.get() + 1),
+                      ctl.get() + 2};
+        void* args[] = {&n_large, &a_list, &a_blk, &a_inv, &a_col, &a_row, &a_voff, &mx, &bar};
+        DPP_CK(cudaLaunchCooperativeKernel((const void*)k_gj_coop, dim3(grid), dim3(256), args, 0, s));
+        DPP_LAUNCH_CK();
+        int err = 0;
+        DPP_CK(cudaMemcpyAsync(&err, ctl.get() + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DPP_CK(cudaStreamSynchronize(s));
+        if (err) fail(DPP_ERR_TIMEOUT, "AMG setup: the coarse Gauss-Jordan barrier timed out");
     }
     DPP_CK(cudaStreamSynchronize(s));  // host tables go out of scope
 }

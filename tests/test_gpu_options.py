@@ -8,6 +8,8 @@ relative L2 per field at a true relative residual of 1e-10. Covered:
   * cheb_degree_amg 1 and 3 (both parities of the smoother's start buffer),
     cheb_degree_mass 1 and 3, cheb_ratio 20;
   * strength_theta 0 and 0.08, max_levels 2, coarse_max_rows 64;
+  * max_levels 1: the coarsest level is S_p itself, blocks of 343 and 625
+    rows, inverted by the cooperative Gauss-Jordan (one grid barrier per pivot);
   * inner_rtol 1e-2 and 1e-6 of the mixed mode; restart 5;
   * x0_zero = 0: from a perturbed oracle solution, and from the oracle
     solution itself (converged before the first iteration).
@@ -50,7 +52,7 @@ def _check(ref, x, info):
 PC_OPTS = [dict(use_lumped_diag=1), dict(cheb_degree_amg=1), dict(cheb_degree_amg=3),
            dict(cheb_degree_mass=1), dict(cheb_degree_mass=3), dict(cheb_ratio=20.0),
            dict(strength_theta=0.0), dict(strength_theta=0.08), dict(max_levels=2),
-           dict(coarse_max_rows=64)]
+           dict(max_levels=1), dict(coarse_max_rows=64)]
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
@@ -93,3 +95,23 @@ def test_initial_guess_is_used(refs, name):
     assert info0["status"] == 0 and info0["iterations"] == 0
     assert np.array_equal(xs.cpu().numpy(), x_ref)
     s.close()
+
+
+@pytest.mark.parametrize("name", sorted(PROBS))
+def test_exact_pressure_solve_needs_no_more_iterations(refs, name):
+    # max_levels = 1 replaces the V-cycle on blockdiag(S_p1, S_p2) by its exact
+    # inverse (the coarsest-level Gauss-Jordan on blocks of 343 / 625 rows), so
+    # the factorisation can only get closer to the selfp one: a wrong inverse
+    # would show as more iterations than the multilevel default.
+    ref = refs[name]
+    P = ref[0]
+    s = system_cls().from_problem(P).setup_pc(max_levels=1)
+    x, info = s.solve(rtol=1e-10)
+    _check(ref, x, info)
+    assert info["levels"] == 1
+    s.close()
+    s = system_cls().from_problem(P).setup_pc()
+    _, info_ml = s.solve(rtol=1e-10)
+    s.close()
+    assert info_ml["levels"] >= 2
+    assert info["iterations"] <= info_ml["iterations"], (info, info_ml)
