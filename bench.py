@@ -235,6 +235,81 @@ def bench_reference(args):
     return 0
 
 
+def _timed(dev, fn, reps):
+    """Mean device time of fn() over reps calls, after one warm call."""
+    import torch
+    fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream(dev))
+    for _ in range(reps):
+        out = fn()
+    e1.record(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps, out
+
+
+def small_solve_mode(dev, reps=10):
+    """The small single problem: 2D unit square 32 x 32 (2048 triangles, 6,534 DoF),
+    mu = 1, k1 = 1, k2 = 0.1, beta = 1, manufactured solution; assemble + setup + FP64
+    solve to 1e-10 per call, through DPPSystem (inputs copied from host memory in each call)."""
+    import inputs
+    from paper_1808_08328_gb300.system import DPPSystem
+    P = inputs.mms_problem(2, 32)
+
+    def once():
+        s = DPPSystem.from_problem(P, device=dev).setup_pc()
+        _, info = s.solve(rtol=1e-10)
+        s.close()
+        return info
+    ms, info = _timed(dev, once, reps)
+    return {"dof_per_s": P.n_dofs / (ms * 1e-3), "ms_per_solve": ms, "dofs": P.n_dofs,
+            "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+            "ms_setup": info["ms_setup"], "ms_solve": info["ms_solve"],
+            "description": "2D 32x32 P1 triangles, MMS, k1=1, k2=0.1, mu=beta=1, FP64, "
+                           "assemble+setup_pc+solve per call"}
+
+
+def adjoint_mode(dev, reps=3):
+    """Gradients of J = sum over nodes (p1 - p1_obs)^2 with respect to the per-cell
+    log k1, log k2 and beta on the 3D 32^3 Kuhn mesh (287,496 DoF): one forward solve
+    (assemble + setup + solve) and one adjoint solve (transpose solve + cell
+    sensitivities) per call. p1_obs is the solution for the log-k fields of seed 1."""
+    import torch
+    import inputs
+    from paper_1808_08328_gb300.system import DPPSystem
+    P = inputs.heterogeneous_problem(3, 32, seed=0, beta=1.0)
+    so = DPPSystem.from_problem(inputs.heterogeneous_problem(3, 32, seed=1, beta=1.0),
+                                device=dev).setup_pc()
+    xo, _ = so.solve(rtol=1e-10)
+    p1_obs = xo[:, 3].clone()
+    so.close()
+    t = {}
+
+    def once():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        st = torch.cuda.current_stream(dev)
+        e[0].record(st)
+        s = DPPSystem.from_problem(P, device=dev).setup_pc()
+        x, info = s.solve(rtol=1e-10)
+        e[1].record(st)
+        dJdx = torch.zeros_like(x)
+        dJdx[:, 3] = 2.0 * (x[:, 3] - p1_obs)
+        _, g1, g2, gb, ainfo = s.adjoint(x, dJdx, rtol=1e-10)
+        e[2].record(st)
+        torch.cuda.synchronize(dev)
+        t["fwd"], t["adj"] = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        s.close()
+        return info, ainfo, float(torch.linalg.norm(g1)), float(gb.reshape(-1)[0])
+    ms, (info, ainfo, g1n, gbv) = _timed(dev, once, reps)
+    return {"dof_per_s": P.n_dofs / (ms * 1e-3), "ms_per_gradient": ms, "dofs": P.n_dofs,
+            "ms_forward": t["fwd"], "ms_adjoint": t["adj"],
+            "forward_iterations": info["iterations"], "adjoint_iterations": ainfo["iterations"],
+            "adjoint_rel_residual": ainfo["rel_residual"], "dJ_dbeta": gbv, "norm_dJ_dlogk1": g1n,
+            "description": "3D 32^3 Kuhn tets, log-normal k (seed 0), FP64 forward + adjoint to "
+                           "1e-10; the finite-difference check is tests/test_gpu_adjoint.py"}
+
+
 def bench_gb300(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -468,6 +543,8 @@ def bench_gb300(args):
                                    "max_iterations": max(i["iterations"] for i in binfo),
                                    "description": BATCH["desc"]}
         del bt
+        modes["small_2d32_fp64"] = small_solve_mode(dev)
+        modes["adjoint_3d32"] = adjoint_mode(dev)
 
     if rank != 0:
         if dist:
