@@ -14,6 +14,7 @@
 
 namespace dpp {
 void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s);
+void f2d(const float* in, double* out, int64_t n, cudaStream_t s);
 void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
               cudaStream_t s);
 void pc_apply_mass(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, cudaStream_t s);
@@ -720,14 +721,18 @@ dpp_status dpp_pc_hierarchy_export_level(dpp_pc pc, int32_t hierarchy, int32_t l
         DPP_CK(cudaMemcpyAsync(row_ptr, A.row_ptr.get(), (A.n_rows + 1) * sizeof(int),
                                cudaMemcpyDeviceToDevice, s));
         DPP_CK(cudaMemcpyAsync(col, A.col.get(), A.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
-        DPP_CK(cudaMemcpyAsync(val, A.val.get(), A.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        // the FP32 hierarchy of a mixed-precision preconditioner: values widened
+        auto values = [&](const Csr& M, double* out) {
+            if (fp32_only(M)) f2d(M.val32.get(), out, M.nnz, s);
+            else DPP_CK(cudaMemcpyAsync(out, M.val.get(), M.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        };
+        values(A, val);
         if (p_row_ptr && p_col && p_val && level + 1 < (int)L.size()) {
             const Csr& P = L[level].P;
             DPP_CK(cudaMemcpyAsync(p_row_ptr, P.row_ptr.get(), (P.n_rows + 1) * sizeof(int),
                                    cudaMemcpyDeviceToDevice, s));
             DPP_CK(cudaMemcpyAsync(p_col, P.col.get(), P.nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
-            DPP_CK(cudaMemcpyAsync(p_val, P.val.get(), P.nnz * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, s));
+            values(P, p_val);
         }
         DPP_CK(cudaStreamSynchronize(s));
         return DPP_OK;

@@ -246,7 +246,8 @@ int pick_lanes(const Csr& A) {
     return l;
 }
 
-// SELL-32 copy of a level matrix (FP64 values; amg_make_fp32 adds FP32 ones),
+// SELL-32 copy of a level matrix (the matrix's own values: FP64, to which
+// amg_make_fp32 adds FP32 ones, or FP32 for a matrix of the FP32 hierarchy),
 // built for matrices with at least opts.sell_min_rows rows (default 65536)
 // unless opts.spmv_format asks for CSR only; offsets must fit int32.
 int64_t sell_min_rows(const dpp_pc_opts& o) { return o.sell_min_rows > 0 ? o.sell_min_rows : 65536; }
@@ -259,24 +260,31 @@ void build_sell(Csr& A, cudaStream_t s, HostScratch& hs) {
     const int64_t tot = exclusive_scan(off.get(), off.get(), n_sl + 1, s, hs);
     if (tot <= 0 || tot >= INT32_MAX) return;  // keep CSR only
     A.sell_col.alloc(tot);
-    A.sell_val.alloc(tot);
-    k_sell_fill<double><<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
-                                                        off.get(), A.sell_col.get(), A.sell_val.get());
+    if (fp32_only(A)) {  // a matrix of the FP32 hierarchy
+        A.sell_val32.alloc(tot);
+        k_sell_fill<float><<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val32.get(),
+                                                           off.get(), A.sell_col.get(), A.sell_val32.get());
+    } else {
+        A.sell_val.alloc(tot);
+        k_sell_fill<double><<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
+                                                            off.get(), A.sell_col.get(), A.sell_val.get());
+    }
     DPP_LAUNCH_CK();
     A.sell_off = std::move(off);
 }
 
 // ------------------------------------------------------------------ vectors
+template <class V>
 __global__ void k_diag_inv(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
-                           const double* __restrict__ val, double* __restrict__ dinv,
-                           double* __restrict__ dabs, int* status) {
+                           const V* __restrict__ val, V* __restrict__ dinv,
+                           V* __restrict__ dabs, int* status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double d = 0.0;
+    V d = V(0);
     for (int p = rp[i]; p < rp[i + 1]; ++p)
         if (col[p] == i) d = val[p];
-    if (!(d > 0.0) || !isfinite(d)) atomicOr(status, kDevDegenerate);
-    dinv[i] = 1.0 / d;
+    if (!(d > V(0)) || !isfinite(d)) atomicOr(status, kDevDegenerate);
+    dinv[i] = V(1) / d;
     if (dabs) dabs[i] = fabs(d);
 }
 
@@ -305,15 +313,23 @@ __global__ void k_fill_int(int64_t n, int v, int* __restrict__ x) {
 }
 
 // y = x / sqrt(*nrm2)
-__global__ void k_scale_rsqrt(int64_t n, const double* __restrict__ x, double* __restrict__ y,
+template <class V>
+__global__ void k_scale_rsqrt(int64_t n, const V* __restrict__ x, V* __restrict__ y,
                               const double* __restrict__ nrm2) {
-    const double a = 1.0 / sqrt(*nrm2);
+    const V a = (V)(1.0 / sqrt(*nrm2));
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         y[i] = a * x[i];
 }
 
-__global__ void k_dinv_scale(int64_t n, const double* __restrict__ dinv, double* __restrict__ v) {
+__global__ void k_f2d(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (double)in[i];
+}
+
+template <class V>
+__global__ void k_dinv_scale(int64_t n, const V* __restrict__ dinv, V* __restrict__ v) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         v[i] *= dinv[i];
@@ -328,9 +344,10 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {  // murmur3 finaliser
     return x;
 }
 
-__global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
+template <class V>
+__global__ void k_hash_vector(int64_t n, V* __restrict__ v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = 0.5 + (double)(mix32((uint32_t)i * 2654435761u + 12345u) >> 8) / 16777216.0;
+    if (i < n) v[i] = (V)(0.5 + (double)(mix32((uint32_t)i * 2654435761u + 12345u) >> 8) / 16777216.0);
 }
 
 // ------------------------------------------------------------------ aggregation
@@ -338,20 +355,22 @@ __global__ void k_hash_vector(int64_t n, double* __restrict__ v) {
 // when |a_ij| >= theta sqrt(|a_ii| |a_jj|), tested as a_ij^2 >= theta^2 |a_ii| |a_jj|
 // (no FP64 square root, which is slow on this GPU's FP64 pipe). Ballots keep
 // the row's column order.
-__device__ __forceinline__ bool is_strong(int64_t i, int j, double aij, double di,
-                                          const double* __restrict__ dabs, double theta2) {
+template <class V>
+__device__ __forceinline__ bool is_strong(int64_t i, int j, V aij, V di, const V* __restrict__ dabs,
+                                          V theta2) {
     return j != i && aij * aij >= theta2 * (di * dabs[j]);
 }
 
 // One pass: the strong columns of row i go to tmp[rp[i] ...] (the row's own
 // range in A) and their number to cnt[i]; k_strength_compact then packs them.
+template <class V>
 __global__ void k_strength_stage(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
-                                 const double* __restrict__ val, const double* __restrict__ dabs,
-                                 double theta2, int* __restrict__ cnt, int* __restrict__ tmp) {
+                                 const V* __restrict__ val, const V* __restrict__ dabs,
+                                 V theta2, int* __restrict__ cnt, int* __restrict__ tmp) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
-    const double di = dabs[i];
+    const V di = dabs[i];
     const int p1 = rp[i + 1];
     int q = rp[i];
     for (int p0 = rp[i]; p0 < p1; p0 += 32) {
@@ -464,25 +483,27 @@ __global__ void k_agg_pass2(int64_t n, const int* __restrict__ srp, const int* _
     if (a < 0) atomicOr(status, kDevOverflow);
 }
 
+template <class V>
 __global__ void k_p0(int64_t n, const int* __restrict__ agg, int* __restrict__ rp,
-                     int* __restrict__ col, double* __restrict__ val) {
+                     int* __restrict__ col, V* __restrict__ val) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         rp[i] = (int)i;
         col[i] = agg[i];
-        val[i] = 1.0;
+        val[i] = V(1);
     }
     if (i == n) rp[n] = (int)n;
 }
 
 // P = P0 - omega D^-1 (A P0), in place on the values of A P0.
+template <class V>
 __global__ void k_smooth_p(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
-                           double* __restrict__ val, const int* __restrict__ agg,
-                           const double* __restrict__ dinv, double omega) {
+                           V* __restrict__ val, const int* __restrict__ agg,
+                           const V* __restrict__ dinv, V omega) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double w = omega * dinv[i];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) val[p] = (col[p] == agg[i] ? 1.0 : 0.0) - w * val[p];
+    const V w = omega * dinv[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) val[p] = (col[p] == agg[i] ? V(1) : V(0)) - w * val[p];
 }
 
 // ------------------------------------------------------------------ coarse block inverse
@@ -505,15 +526,16 @@ __global__ void k_row_extents(int64_t n, const int* __restrict__ rp, const int* 
     hi[i] = b;
 }
 
+template <class V>
 __global__ void k_csr_to_blocks(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
-                                const double* __restrict__ val, const int* __restrict__ blk,
+                                const V* __restrict__ val, const int* __restrict__ blk,
                                 const int* __restrict__ rowblk, double* __restrict__ inv) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = rowblk[i];
     const int b0 = blk[3 * c], nb = blk[3 * c + 1], off = blk[3 * c + 2];
     for (int p = rp[i]; p < rp[i + 1]; ++p)
-        inv[(int64_t)off + (int64_t)(i - b0) * nb + (col[p] - b0)] = val[p];
+        inv[(int64_t)off + (int64_t)(i - b0) * nb + (col[p] - b0)] = (double)val[p];
 }
 
 // Gauss-Jordan of many small blocks at once: one CTA per listed block (list
@@ -679,24 +701,37 @@ void check_dev(DBuf<int>& st, cudaStream_t s, HostScratch& hs, const char* what)
     if (v) fail(DPP_ERR_INVALID_ARGUMENT, std::string("AMG setup: ") + what);
 }
 
-// lambda_max(D^-1 A) by 12 power steps; the vector is renormalised on the
-// device (no host round trip per step) and the estimate read once at the end.
-double power_lmax(const Csr& A, const double* dinv, int lanes, cudaStream_t s, HostScratch& hs) {
+// ||x||^2 into out[0], summed in FP64 (an FP32 x is widened first into wide)
+void sq_norm(Reducer& R, const double* x, int64_t n, double* out, DBuf<double>&, cudaStream_t s) {
+    dot(R, x, x, n, out, s);
+}
+void sq_norm(Reducer& R, const float* x, int64_t n, double* out, DBuf<double>& wide, cudaStream_t s) {
+    k_f2d<<<sgrid(n), 256, 0, s>>>(n, x, wide.get());
+    DPP_LAUNCH_CK();
+    dot(R, wide.get(), wide.get(), n, out, s);
+}
+
+// lambda_max(D^-1 A) by 12 power steps in the hierarchy's precision V; the
+// vector is renormalised on the device (no host round trip per step) and the
+// estimate read once at the end.
+template <class V>
+double power_lmax(const Csr& A, const V* dinv, int lanes, cudaStream_t s, HostScratch& hs) {
     const int64_t n = A.n_rows;
-    DBuf<double> v(n), w(n), nrm(1);
+    DBuf<V> v(n), w(n);
+    DBuf<double> nrm(1), wide(sizeof(V) == 4 ? n : 0);
     const int B = 256;
-    k_hash_vector<<<grid_for(n, B), B, 0, s>>>(n, v.get());
+    k_hash_vector<V><<<grid_for(n, B), B, 0, s>>>(n, v.get());
     DPP_LAUNCH_CK();
     Reducer R;
-    dot(R, v.get(), v.get(), n, nrm.get(), s);
-    k_scale_rsqrt<<<sgrid(n), 256, 0, s>>>(n, v.get(), v.get(), nrm.get());
+    sq_norm(R, v.get(), n, nrm.get(), wide, s);
+    k_scale_rsqrt<V><<<sgrid(n), 256, 0, s>>>(n, v.get(), v.get(), nrm.get());
     DPP_LAUNCH_CK();
     for (int it = 0; it < 12; ++it) {
-        spmv_lanes<0, double>(lanes, A, v.get(), nullptr, w.get(), s);
-        k_dinv_scale<<<sgrid(n), 256, 0, s>>>(n, dinv, w.get());
+        spmv_lanes<0, V>(lanes, A, v.get(), nullptr, w.get(), s);
+        k_dinv_scale<V><<<sgrid(n), 256, 0, s>>>(n, dinv, w.get());
         DPP_LAUNCH_CK();
-        dot(R, w.get(), w.get(), n, nrm.get(), s);   // ||D^-1 A v||^2 with ||v|| = 1
-        k_scale_rsqrt<<<sgrid(n), 256, 0, s>>>(n, w.get(), v.get(), nrm.get());
+        sq_norm(R, w.get(), n, nrm.get(), wide, s);   // ||D^-1 A v||^2 with ||v|| = 1
+        k_scale_rsqrt<V><<<sgrid(n), 256, 0, s>>>(n, w.get(), v.get(), nrm.get());
         DPP_LAUNCH_CK();
     }
     const double l2 = read_scalar(nrm.get(), s, hs);
@@ -757,9 +792,14 @@ void block_inverse(Amg& pc, const Csr& A, cudaStream_t s) {
     DPP_CK(cudaMemcpyAsync(pc.coarse_blk.get(), blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     DPP_CK(cudaMemcpyAsync(pc.coarse_rowblk.get(), rowblk.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
     DPP_CK(cudaMemsetAsync(pc.coarse_inv.get(), 0, off * sizeof(double), s));
-    k_csr_to_blocks<<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
-                                                     pc.coarse_blk.get(), pc.coarse_rowblk.get(),
-                                                     pc.coarse_inv.get());
+    if (fp32_only(A))  // the FP32 hierarchy: the coarsest matrix is widened, its inverse is FP64
+        k_csr_to_blocks<float><<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val32.get(),
+                                                                pc.coarse_blk.get(), pc.coarse_rowblk.get(),
+                                                                pc.coarse_inv.get());
+    else
+        k_csr_to_blocks<double><<<grid_for(n, 128), 128, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),
+                                                                 pc.coarse_blk.get(), pc.coarse_rowblk.get(),
+                                                                 pc.coarse_inv.get());
     DPP_LAUNCH_CK();
     if (!small.empty()) {
         DBuf<int> d_small(small.size());
@@ -809,7 +849,17 @@ void block_inverse(Amg& pc, const Csr& A, cudaStream_t s) {
 
 }  // namespace
 
-void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScratch& hs) {
+namespace {
+template <class V> DBuf<V>& dinv_of(Level& L);
+template <> DBuf<double>& dinv_of<double>(Level& L) { return L.dinv; }
+template <> DBuf<float>& dinv_of<float>(Level& L) { return L.dinv32; }
+
+// The setup in the precision V of A0's values: FP64 (the FP64 hierarchy, of
+// which amg_make_fp32 may add FP32 copies), or FP32 (the hierarchy of the
+// mixed mode, built in FP32 from the FP32 S_p; only its coarsest inverse is
+// FP64).
+template <class V>
+void amg_setup_t(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScratch& hs) {
     ProfScope prof_all("setup_amg", s, 0);
     pc.levels.clear();
     pc.levels.emplace_back();
@@ -823,7 +873,7 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
     // S_p is symmetric by construction (D symmetric, C = -B^T in exact
     // arithmetic), so a sample of every 16th row only guards against a
     // structural surprise
-    const bool symmetric = is_symmetric(pc.levels[0].A, 1e-10, 16, s, hs);
+    const bool symmetric = is_symmetric(pc.levels[0].A, sizeof(V) == 8 ? 1e-10 : 1e-5, 16, s, hs);
     pc.symmetric = symmetric;
     for (int l = 0;; ++l) {
         Level& L = pc.levels[l];
@@ -833,18 +883,21 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
             build_sell(L.A, s, hs);
             if (L.A.has_sell()) L.lanes = 0;  // SELL-32 (the autotuner may still pick CSR)
         }
-        L.dinv.alloc(n);
-        DBuf<double> dabs(n);
+        DBuf<V>& dinv = dinv_of<V>(L);
+        dinv.alloc(n);
+        DBuf<V> dabs(n);
         DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
-        k_diag_inv<<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(), L.A.val.get(),
-                                                L.dinv.get(), dabs.get(), st.get());
+        k_diag_inv<V><<<grid_for(n, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                   vbuf<V>(L.A).get(), dinv.get(), dabs.get(), st.get());
         DPP_LAUNCH_CK();
         check_dev(st, s, hs, "a level matrix has a non-positive diagonal entry");
-        L.x.alloc(n);
-        L.xt.alloc(n);
-        L.b.alloc(n);
-        L.r.alloc(n);
-        L.d.alloc(n);
+        if (sizeof(V) == 8) {  // FP64 work vectors (amg_make_fp32 adds the FP32 ones)
+            L.x.alloc(n);
+            L.xt.alloc(n);
+            L.b.alloc(n);
+            L.r.alloc(n);
+            L.d.alloc(n);
+        }
         bool last = (n <= o.coarse_max_rows) || (l + 1 >= o.max_levels);
         if (!last && n <= kBlockCoarseRows) {
             // a level made of small diagonal blocks only (a batched union that
@@ -856,7 +909,7 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
         if (last) break;  // the coarsest level is solved directly: no smoother, no lambda_max
         {
             ProfScope pr("setup_power", s, 0);
-            L.lmax = power_lmax(L.A, L.dinv.get(), L.lanes, s, hs);
+            L.lmax = power_lmax<V>(L.A, dinv.get(), L.lanes, s, hs);
         }
 
         // strength graph
@@ -868,9 +921,9 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
         S.row_ptr.alloc(n + 1);
         DPP_CK(cudaMemsetAsync(S.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
         DBuf<int> stage(std::max<int64_t>(L.A.nnz, 1));
-        k_strength_stage<<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
-                                                      L.A.val.get(), dabs.get(), theta2,
-                                                      S.row_ptr.get(), stage.get());
+        k_strength_stage<V><<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                         vbuf<V>(L.A).get(), dabs.get(), (V)theta2,
+                                                         S.row_ptr.get(), stage.get());
         DPP_LAUNCH_CK();
         S.nnz = exclusive_scan(S.row_ptr.get(), S.row_ptr.get(), n + 1, s, hs);
         S.col.alloc(std::max<int64_t>(S.nnz, 1));
@@ -926,9 +979,9 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
         P0.nnz = n;
         P0.row_ptr.alloc(n + 1);
         P0.col.alloc(n);
-        P0.val.alloc(n);
-        k_p0<<<grid_for(n + 1, B), B, 0, s>>>(n, agg.get(), P0.row_ptr.get(), P0.col.get(),
-                                              P0.val.get());
+        vbuf<V>(P0).alloc(n);
+        k_p0<V><<<grid_for(n + 1, B), B, 0, s>>>(n, agg.get(), P0.row_ptr.get(), P0.col.get(),
+                                                 vbuf<V>(P0).get());
         DPP_LAUNCH_CK();
         Csr Pm;
         {
@@ -936,8 +989,8 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
             spgemm(view(L.A), view(P0), Pm, true, s, hs);
         }
         const double omega = 4.0 / (3.0 * L.lmax);
-        k_smooth_p<<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), Pm.val.get(),
-                                                agg.get(), L.dinv.get(), omega);
+        k_smooth_p<V><<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), vbuf<V>(Pm).get(),
+                                                   agg.get(), dinv.get(), (V)omega);
         DPP_LAUNCH_CK();
         L.P = std::move(Pm);
         if (o.spmv_format != 1 && n >= sell_min_rows(o)) build_sell(L.P, s, hs);  // autotuner may pick it
@@ -968,6 +1021,12 @@ void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScra
     pc.coarse_n = C.A.n_rows;
     ProfScope pr("setup_coarse_inverse", s, 0);
     block_inverse(pc, C.A, s);
+}
+}  // namespace
+
+void amg_setup(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostScratch& hs) {
+    if (fp32_only(A0)) amg_setup_t<float>(pc, o, std::move(A0), s, hs);
+    else amg_setup_t<double>(pc, o, std::move(A0), s, hs);
 }
 
 namespace {
@@ -1186,13 +1245,15 @@ void amg_tune(Amg& pc, const dpp_pc_opts& o, int precision, cudaStream_t s) {
 void amg_make_fp32(Amg& pc, cudaStream_t s) {
     for (size_t l = 0; l < pc.levels.size(); ++l) {
         Level& L = pc.levels[l];
-        to_f32(L.A.val, L.A.val32, s);
-        if (L.A.has_sell()) to_f32(L.A.sell_val, L.A.sell_val32, s);
-        to_f32(L.dinv, L.dinv32, s);
-        if (l + 1 < pc.levels.size()) {
-            to_f32(L.P.val, L.P.val32, s);
-            if (L.P.has_sell()) to_f32(L.P.sell_val, L.P.sell_val32, s);
-            to_f32(L.R.val, L.R.val32, s);
+        if (!fp32_only(L.A)) {  // an FP64 hierarchy: FP32 copies of its values
+            to_f32(L.A.val, L.A.val32, s);
+            if (L.A.has_sell()) to_f32(L.A.sell_val, L.A.sell_val32, s);
+            if (L.dinv.get()) to_f32(L.dinv, L.dinv32, s);
+            if (l + 1 < pc.levels.size()) {
+                to_f32(L.P.val, L.P.val32, s);
+                if (L.P.has_sell()) to_f32(L.P.sell_val, L.P.sell_val32, s);
+                to_f32(L.R.val, L.R.val32, s);
+            }
         }
         const int64_t n = L.A.n_rows;
         L.x32.alloc(n);

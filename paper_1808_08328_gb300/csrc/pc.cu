@@ -88,6 +88,13 @@ void d2f(const double* in, float* out, int64_t n, cudaStream_t s) {
     DPP_LAUNCH_CK();
 }
 
+__global__ void k_f2d_pc(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (double)in[i];
+}
+
+
 // Rows r0 .. r0+m-1 of S as an m x m matrix (columns shifted by -r0). Flags an
 // entry outside the diagonal block: S must be block-diagonal there.
 __global__ void k_block_rows_ptr(int64_t m, const int* __restrict__ rp, int64_t r0,
@@ -95,13 +102,14 @@ __global__ void k_block_rows_ptr(int64_t m, const int* __restrict__ rp, int64_t 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i <= m) orp[i] = rp[r0 + i] - rp[r0];
 }
+template <class V>
 __global__ void k_block_rows_entries(int64_t nnz, int64_t m, const int* __restrict__ col,
-                                     const double* __restrict__ val, int64_t e0, int64_t r0,
-                                     int* __restrict__ ocol, double* __restrict__ oval, int* bad) {
+                                     const V* __restrict__ val, int64_t e0, int64_t r0,
+                                     int* __restrict__ ocol, V* __restrict__ oval, int* bad) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
     const int64_t c = (int64_t)col[e0 + e] - r0;
-    if (c < 0 || c >= m) { atomicOr(bad, 1); ocol[e] = 0; oval[e] = 0.0; return; }
+    if (c < 0 || c >= m) { atomicOr(bad, 1); ocol[e] = 0; oval[e] = V(0); return; }
     ocol[e] = (int)c;
     oval[e] = val[e0 + e];
 }
@@ -114,14 +122,20 @@ void diagonal_block(const Csr& S, int64_t r0, int64_t m, Csr& out, cudaStream_t 
     out.nnz = e1 - e0;
     out.row_ptr.alloc(m + 1);
     out.col.alloc(std::max<int64_t>(out.nnz, 1));
-    out.val.alloc(std::max<int64_t>(out.nnz, 1));
+    const bool f32 = fp32_only(S);  // S_p of the mixed mode (FP32 values only)
+    if (f32) out.val32.alloc(std::max<int64_t>(out.nnz, 1));
+    else out.val.alloc(std::max<int64_t>(out.nnz, 1));
     k_block_rows_ptr<<<grid_for(m + 1, 256), 256, 0, s>>>(m, S.row_ptr.get(), r0, out.row_ptr.get());
     DPP_LAUNCH_CK();
     DBuf<int> bad(1);
     DPP_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
     if (out.nnz) {
-        k_block_rows_entries<<<grid_for(out.nnz, 256), 256, 0, s>>>(
-            out.nnz, m, S.col.get(), S.val.get(), e0, r0, out.col.get(), out.val.get(), bad.get());
+        if (f32)
+            k_block_rows_entries<float><<<grid_for(out.nnz, 256), 256, 0, s>>>(
+                out.nnz, m, S.col.get(), S.val32.get(), e0, r0, out.col.get(), out.val32.get(), bad.get());
+        else
+            k_block_rows_entries<double><<<grid_for(out.nnz, 256), 256, 0, s>>>(
+                out.nnz, m, S.col.get(), S.val.get(), e0, r0, out.col.get(), out.val.get(), bad.get());
         DPP_LAUNCH_CK();
     }
     if (read_scalar(bad.get(), s, hs))
@@ -142,6 +156,13 @@ void schur_vcycle(PcImpl& pc, const T* tp, T* yp, cudaStream_t s) {
 }
 
 }  // namespace
+
+// FP32 -> FP64 copy (the widened values and results of the FP32 hierarchy)
+void f2d(const float* in, double* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_f2d_pc<<<(int)std::min<int64_t>((n + 255) / 256, 8 * kSMs), 256, 0, s>>>(n, in, out);
+    DPP_LAUNCH_CK();
+}
 
 void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
     pc.dim = P.dim;
@@ -166,10 +187,23 @@ void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
         pc.mass_lmin = 0.5;
         pc.mass_lmax = 0.5 * (P.dim + 2);
     }
+    const bool mixed = pc.precision == DPP_MIXED_FP32_FP64;
+    if (mixed) {
+        // The mixed mode's hierarchy is built in FP32, from the FP32 pair values
+        // (converted here if the problem was assembled in FP64 only) and FP32 M^-1.
+        auto& Pm = const_cast<ProblemImpl&>(P);
+        if (!Pm.sell_val32.get()) {
+            Pm.sell_val32.alloc(P.sell_val.n);
+            d2f(P.sell_val.get(), Pm.sell_val32.get(), (int64_t)P.sell_val.n, s);
+        }
+        pc.mdiag32.alloc(2 * n);
+        d2f(pc.mdiag.get(), pc.mdiag32.get(), 2 * n, s);
+    }
     Csr S;
     {
         ProfScope pr("setup_selfp", s, 0);
-        build_selfp(P, pc.mdiag.get(), S, s, pc.hs);
+        if (mixed) build_selfp(P, pc.mdiag32.get(), S, s, pc.hs);
+        else build_selfp(P, pc.mdiag.get(), S, s, pc.hs);
     }
     if (pc.opts.composition == kScaleSplit) {
         // Method 1: S^1_p and S^2_p, each with its own hierarchy
@@ -192,16 +226,9 @@ void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
     pc.tp.alloc(2 * n);
     pc.yp.alloc(2 * n);
     DPP_CK(cudaMemsetAsync(pc.su.get(), 0, nn * sizeof(double), s));
-    if (pc.precision == DPP_MIXED_FP32_FP64) {
-        // FP32 pair values (if the problem was assembled in FP64 only) and FP32 hierarchy
-        auto& Pm = const_cast<ProblemImpl&>(P);
-        if (!Pm.sell_val32.get()) {
-            Pm.sell_val32.alloc(P.sell_val.n);
-            d2f(P.sell_val.get(), Pm.sell_val32.get(), (int64_t)P.sell_val.n, s);
-        }
+    if (mixed) {
+        // the FP32 hierarchy's work vectors
         for (int h = 0; h < pc.n_amg; ++h) amg_make_fp32(pc.amg[h], s);
-        pc.mdiag32.alloc(2 * n);
-        d2f(pc.mdiag.get(), pc.mdiag32.get(), 2 * n, s);
         pc.yu32.alloc(nn);
         pc.su32.alloc(nn);
         pc.tmp32.alloc(nn);
@@ -215,9 +242,21 @@ void pc_setup(PcImpl& pc, const ProblemImpl& P, cudaStream_t s) {
     DPP_CK(cudaStreamSynchronize(s));
 }
 
-// z = P^-1 r in FP64 (values, vectors and arithmetic).
+void pc_apply32(const ProblemImpl& P, PcImpl& pc, const double* r, float* z, bool transpose,
+                cudaStream_t s);
+
+// z = P^-1 r in FP64 (values, vectors and arithmetic). A mixed-precision
+// preconditioner holds its FP32 hierarchy only: there z is its FP32 result,
+// widened.
 void pc_apply(const ProblemImpl& P, PcImpl& pc, const double* r, double* z, bool transpose,
               cudaStream_t s) {
+    if (pc.precision == DPP_MIXED_FP32_FP64) {
+        const int64_t nn = P.n_nodes * P.ns;
+        DBuf<float> z32(nn);
+        pc_apply32(P, pc, r, z32.get(), transpose, s);
+        f2d(z32.get(), z, nn, s);
+        return;
+    }
     // 1. y_u = Ainv r_u
     mass_chebyshev<double>(P, pc, pc.mdiag.get(), r, pc.yu.get(), pc.tmp.get(), pc.dcheb.get(), s);
     // 2. t_p = r_p - C y_u   (split pressures [p1 | p2])

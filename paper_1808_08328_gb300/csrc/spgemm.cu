@@ -104,10 +104,10 @@ __device__ __forceinline__ int b_row_start(const int* __restrict__ brp, const in
 // in (p, q) order; every lane of the warp makes every call (f may use warp
 // collectives), inactive lanes with active == false. Only columns >= col_lo
 // are produced (INT_MIN: all).
-template <bool VALS, class F>
+template <bool VALS, class V, class F>
 __device__ __forceinline__ void for_each_product(int i, const int* __restrict__ arp,
                                                  const int* __restrict__ acol,
-                                                 const double* __restrict__ aval,
+                                                 const V* __restrict__ aval,
                                                  const int* __restrict__ brp,
                                                  const int* __restrict__ bcol, int col_lo, int lane,
                                                  F&& f) {
@@ -115,7 +115,7 @@ __device__ __forceinline__ void for_each_product(int i, const int* __restrict__ 
     for (int pc = a0; pc < a1; pc += 32) {
         const int p = pc + lane;
         int bs = 0, len = 0;
-        double a = 0.0;
+        V a = V(0);
         if (p < a1) {
             const int k = acol[p];
             bs = b_row_start(brp, bcol, k, col_lo);
@@ -139,7 +139,7 @@ __device__ __forceinline__ void for_each_product(int i, const int* __restrict__ 
                 if (e <= t) j += step;
             }
             const int q = __shfl_sync(kFull, bs, j) + (t - __shfl_sync(kFull, excl, j));
-            const double aj = VALS ? __shfl_sync(kFull, a, j) : 0.0;
+            const V aj = VALS ? __shfl_sync(kFull, a, j) : V(0);
             f(t < total, q, aj);
         }
     }
@@ -153,7 +153,7 @@ __device__ bool warp_collect(int i, const int* __restrict__ arp, const int* __re
     for (int t = lane; t < HT; t += 32) keys[t] = -1;
     __syncwarp();
     bool ok = true;
-    for_each_product<false>(i, arp, acol, nullptr, brp, bcol, col_lo, lane, [&](bool act, int q, double) {
+    for_each_product<false, double>(i, arp, acol, nullptr, brp, bcol, col_lo, lane, [&](bool act, int q, double) {
         if (act) ok &= hs_insert<HT>(keys, bcol[q]);
     });
     __syncwarp();
@@ -265,12 +265,12 @@ __global__ void k_spgemm_pattern(int64_t n_rows, const int* __restrict__ arp,
 // Numeric pass for rows with at most CAP distinct columns (shared accumulators).
 // Shared memory per warp: keys[HT], slot[HT], acc[CAP] (the compacted key list
 // lives in acc until the ranks are known).
-template <int HT, int CAP>
+template <int HT, int CAP, class V>
 __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
-                                 const int* __restrict__ acol, const double* __restrict__ aval,
+                                 const int* __restrict__ acol, const V* __restrict__ aval,
                                  const int* __restrict__ brp, const int* __restrict__ bcol,
-                                 const double* __restrict__ bval, const int* __restrict__ crp,
-                                 int* __restrict__ ccol, double* __restrict__ cval,
+                                 const V* __restrict__ bval, const int* __restrict__ crp,
+                                 int* __restrict__ ccol, V* __restrict__ cval,
                                  int* __restrict__ wide, const int* __restrict__ is_long,
                                  int upper) {
     static_assert(HT >= 2 * CAP, "table at most half full");
@@ -288,17 +288,17 @@ __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
     }
     int* keys = smem + warp * 2 * HT;
     int* slot = keys + HT;
-    double* acc = reinterpret_cast<double*>(smem + WPB * 2 * HT) + (size_t)warp * CAP;
+    V* acc = reinterpret_cast<V*>(smem + WPB * 2 * HT) + (size_t)warp * CAP;
     const int col_lo = upper ? i : INT_MIN;
     warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, col_lo);  // cannot overflow (HT >= 2 CAP)
     int* list = reinterpret_cast<int*>(acc);
     const int u = warp_compact<HT>(keys, list, lane);
     warp_rank<HT>(list, u, lane, ccol + c0, keys, slot);
-    for (int e = lane; e < u; e += 32) acc[e] = 0.0;
+    for (int e = lane; e < u; e += 32) acc[e] = V(0);
     __syncwarp();
-    for_each_product<true>(i, arp, acol, aval, brp, bcol, col_lo, lane, [&](bool act, int q, double a) {
+    for_each_product<true, V>(i, arp, acol, aval, brp, bcol, col_lo, lane, [&](bool act, int q, V a) {
         int s = -1 - lane;  // distinct for idle lanes
-        double bv = 0.0;
+        V bv = V(0);
         if (act) {
             const int key = bcol[q];
             bv = bval[q];
@@ -321,14 +321,21 @@ __global__ void k_spgemm_scatter(int64_t n_rows, const int* __restrict__ arp,
 // records its length, so no separate counting pass is needed. Rows that do
 // not fit get uone[i] = -1 and are listed in ovf (ovf[0] = count) for the
 // counting tiers and k_spgemm_wide.
-template <int HT, int CAP>
+// Per warp the accumulators take CAP values, and at least HT ints: the
+// compacted key list lives there until the ranks are known.
+template <int HT, int CAP, class V>
+__host__ __device__ constexpr size_t onepass_acc_bytes() {
+    return CAP * sizeof(V) > HT * sizeof(int) ? CAP * sizeof(V) : HT * sizeof(int);
+}
+
+template <int HT, int CAP, class V>
 __global__ void k_spgemm_onepass(int64_t n_rows, const int* __restrict__ arp,
-                                 const int* __restrict__ acol, const double* __restrict__ aval,
+                                 const int* __restrict__ acol, const V* __restrict__ aval,
                                  const int* __restrict__ brp, const int* __restrict__ bcol,
-                                 const double* __restrict__ bval, int* __restrict__ count,
+                                 const V* __restrict__ bval, int* __restrict__ count,
                                  int* __restrict__ uone, int* __restrict__ tcol,
-                                 double* __restrict__ tval, int* __restrict__ ovf, int upper) {
-    static_assert(HT == 2 * CAP, "the compacted key list lives in the CAP accumulators");
+                                 V* __restrict__ tval, int* __restrict__ ovf, int upper) {
+    static_assert(HT == 2 * CAP, "tables at most half full");
     extern __shared__ int smem[];
     constexpr int WPB = 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -337,7 +344,8 @@ __global__ void k_spgemm_onepass(int64_t n_rows, const int* __restrict__ arp,
     const int i = (int)w;
     int* keys = smem + warp * 2 * HT;
     int* slot = keys + HT;
-    double* acc = reinterpret_cast<double*>(smem + WPB * 2 * HT) + (size_t)warp * CAP;
+    V* acc = reinterpret_cast<V*>(reinterpret_cast<char*>(smem + WPB * 2 * HT) +
+                                  (size_t)warp * onepass_acc_bytes<HT, CAP, V>());
     const int col_lo = upper ? i : INT_MIN;
     const bool ok = warp_collect<HT>(i, arp, acol, brp, bcol, keys, lane, col_lo);
     int* list = reinterpret_cast<int*>(acc);  // HT ints
@@ -352,11 +360,11 @@ __global__ void k_spgemm_onepass(int64_t n_rows, const int* __restrict__ arp,
     }
     int* orow = tcol + (int64_t)i * CAP;
     warp_rank<HT>(list, u, lane, orow, keys, slot);
-    for (int e = lane; e < u; e += 32) acc[e] = 0.0;
+    for (int e = lane; e < u; e += 32) acc[e] = V(0);
     __syncwarp();
-    for_each_product<true>(i, arp, acol, aval, brp, bcol, col_lo, lane, [&](bool act, int q, double a) {
+    for_each_product<true, V>(i, arp, acol, aval, brp, bcol, col_lo, lane, [&](bool act, int q, V a) {
         int sl = -1 - lane;
-        double bv = 0.0;
+        V bv = V(0);
         if (act) {
             bv = bval[q];
             sl = slot[hs_find<HT>(keys, bcol[q])];
@@ -369,7 +377,7 @@ __global__ void k_spgemm_onepass(int64_t n_rows, const int* __restrict__ arp,
             __syncwarp();
         }
     });
-    double* vrow = tval + (int64_t)i * CAP;
+    V* vrow = tval + (int64_t)i * CAP;
     for (int e = lane; e < u; e += 32) vrow[e] = acc[e];
     if (lane == 0) {
         count[i] = u;
@@ -378,11 +386,11 @@ __global__ void k_spgemm_onepass(int64_t n_rows, const int* __restrict__ arp,
 }
 
 // staged rows into C (one warp per row; rows with uone < 0 are done elsewhere)
-template <int CAP>
+template <int CAP, class V>
 __global__ void k_onepass_compact(int64_t n_rows, const int* __restrict__ uone,
                                   const int* __restrict__ crp, const int* __restrict__ tcol,
-                                  const double* __restrict__ tval, int* __restrict__ ccol,
-                                  double* __restrict__ cval) {
+                                  const V* __restrict__ tval, int* __restrict__ ccol,
+                                  V* __restrict__ cval) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n_rows) return;
@@ -395,12 +403,12 @@ __global__ void k_onepass_compact(int64_t n_rows, const int* __restrict__ uone,
 }
 
 // Numeric pass for wide rows: one warp per listed row, accumulating in C.
-template <int HT>
+template <int HT, class V>
 __global__ void k_spgemm_wide(const int* __restrict__ arp, const int* __restrict__ acol,
-                              const double* __restrict__ aval, const int* __restrict__ brp,
-                              const int* __restrict__ bcol, const double* __restrict__ bval,
+                              const V* __restrict__ aval, const int* __restrict__ brp,
+                              const int* __restrict__ bcol, const V* __restrict__ bval,
                               const int* __restrict__ crp, int* __restrict__ ccol,
-                              double* __restrict__ cval, const int* __restrict__ rows,
+                              V* __restrict__ cval, const int* __restrict__ rows,
                               int* __restrict__ status, int upper) {
     extern __shared__ int smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -416,13 +424,13 @@ __global__ void k_spgemm_wide(const int* __restrict__ arp, const int* __restrict
     const int c0 = crp[i];
     const int u = warp_compact<HT>(keys, keys + HT, lane);
     warp_rank<HT>(keys + HT, u, lane, ccol + c0, keys, nullptr);
-    for (int e = lane; e < u; e += 32) cval[c0 + e] = 0.0;
+    for (int e = lane; e < u; e += 32) cval[c0 + e] = V(0);
     __syncwarp();
     for (int p = arp[i]; p < arp[i + 1]; ++p) {
         const int k = acol[p];
-        const double a = aval[p];
+        const V a = aval[p];
         for (int q = b_row_start(brp, bcol, k, col_lo) + lane; q < brp[k + 1]; q += 32) {
-            double& cq = cval[bsearch_row(ccol, c0, c0 + u, bcol[q])];
+            V& cq = cval[bsearch_row(ccol, c0, c0 + u, bcol[q])];
             cq = fma(a, bval[q], cq);
         }
         __syncwarp();
@@ -469,17 +477,18 @@ k_long_count(const int* __restrict__ arp, const int* __restrict__ acol,
     }
 }
 
+template <class V>
 __global__ void __launch_bounds__(kLongWarps * 32)
 k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
-               const double* __restrict__ aval, const int* __restrict__ brp,
-               const int* __restrict__ bcol, const double* __restrict__ bval,
-               const int* __restrict__ crp, int* __restrict__ ccol, double* __restrict__ cval,
+               const V* __restrict__ aval, const int* __restrict__ brp,
+               const int* __restrict__ bcol, const V* __restrict__ bval,
+               const int* __restrict__ crp, int* __restrict__ ccol, V* __restrict__ cval,
                const int* __restrict__ rows, int* __restrict__ wide, int upper) {
     extern __shared__ int smem[];
     int* keys = smem;                                  // kLongHT
     int* list = keys + kLongHT;                        // kLongCap
     int* sorted = list + kLongCap;                     // kLongCap
-    double* acc = reinterpret_cast<double*>(sorted + kLongCap);  // kLongWarps * kLongCap
+    V* acc = reinterpret_cast<V*>(sorted + kLongCap);  // kLongWarps * kLongCap
     __shared__ int nu;
     const int i = rows[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -489,7 +498,7 @@ k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
         return;
     }
     for (int t = threadIdx.x; t < kLongHT; t += blockDim.x) keys[t] = -1;
-    for (int t = threadIdx.x; t < kLongWarps * kLongCap; t += blockDim.x) acc[t] = 0.0;
+    for (int t = threadIdx.x; t < kLongWarps * kLongCap; t += blockDim.x) acc[t] = V(0);
     if (threadIdx.x == 0) nu = 0;
     __syncthreads();
     for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
@@ -508,17 +517,17 @@ k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
     }
     __syncthreads();
     for (int e = threadIdx.x; e < u; e += blockDim.x) ccol[c0 + e] = sorted[e];
-    double* my = acc + warp * kLongCap;
+    V* my = acc + warp * kLongCap;
     for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
         const int k = acol[p];
-        const double a = aval[p];
+        const V a = aval[p];
         for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32)
             my[bsearch_row(sorted, 0, u, bcol[q])] += a * bval[q];
         __syncwarp();
     }
     __syncthreads();
     for (int e = threadIdx.x; e < u; e += blockDim.x) {
-        double v = acc[e];
+        V v = acc[e];
 #pragma unroll
         for (int w = 1; w < kLongWarps; ++w) v += acc[w * kLongCap + e];
         cval[c0 + e] = v;
@@ -559,19 +568,19 @@ __global__ void k_row_len_max(int64_t n, const int* __restrict__ rp, const int* 
 // one round that hit the same column subtract in lane order. Every entry is
 // therefore summed over b in increasing order, as the definition reads. Rows
 // with more than CAP columns are listed in `wide` for k_selfp_values.
-template <int DIM, int CAP>
+template <int DIM, int CAP, class V>
 __global__ void __launch_bounds__(128, 8)
 k_selfp_scatter(int64_t n_nodes, const int* __restrict__ prp, const int* __restrict__ pcol,
-                const int* __restrict__ slice_ptr, const double* __restrict__ pv,
-                const double* __restrict__ mdiag, const int* __restrict__ srp,
-                const int* __restrict__ scol, double* __restrict__ sval, int64_t nnz_half,
+                const int* __restrict__ slice_ptr, const V* __restrict__ pv,
+                const V* __restrict__ mdiag, const int* __restrict__ srp,
+                const int* __restrict__ scol, V* __restrict__ sval, int64_t nnz_half,
                 int* __restrict__ wide) {
     constexpr int NV = pair_values(DIM);
     constexpr int HT = 2 * CAP;
     constexpr int WPB = 4;
     __shared__ int sh_keys[WPB][HT];
     __shared__ int sh_slot[WPB][HT];
-    __shared__ double sh_acc[WPB][2][CAP];
+    __shared__ V sh_acc[WPB][2][CAP];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t a = (int64_t)blockIdx.x * WPB + warp;
     if (a >= n_nodes) return;
@@ -582,14 +591,14 @@ k_selfp_scatter(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
     }
     int* keys = sh_keys[warp];
     int* slot = sh_slot[warp];
-    double* acc1 = sh_acc[warp][0];
-    double* acc2 = sh_acc[warp][1];
-    auto pval = [&](int row, int p, int k) -> double {
+    V* acc1 = sh_acc[warp][0];
+    V* acc2 = sh_acc[warp][1];
+    auto pval = [&](int row, int p, int k) -> V {
         const int64_t grp = (int64_t)slice_ptr[row >> 5] + (p - prp[row]);
         return pv[(grp * NV + k) * kSell + (row & 31)];
     };
     for (int t = lane; t < HT; t += 32) keys[t] = -1;
-    for (int e = lane; e < CAP; e += 32) acc1[e] = acc2[e] = 0.0;
+    for (int e = lane; e < CAP; e += 32) acc1[e] = acc2[e] = V(0);
     __syncwarp();
     for (int e = lane; e < u; e += 32) {  // the row's columns are distinct
         const int c = scol[e0 + e];
@@ -608,9 +617,9 @@ k_selfp_scatter(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
     for (int pc0 = pa0; pc0 < pa1; pc0 += 32) {
         const int pab = pc0 + lane;
         int b = 0, bs = 0, len = 0;
-        double cab[DIM], m1 = 0.0, m2 = 0.0;
+        V cab[DIM], m1 = V(0), m2 = V(0);
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) cab[k] = 0.0;
+        for (int k = 0; k < DIM; ++k) cab[k] = V(0);
         if (pab < pa1) {
             b = pcol[pab];
             bs = prp[b];
@@ -638,13 +647,13 @@ k_selfp_scatter(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
             }
             const int bj = __shfl_sync(kFull, b, j);
             const int pbc = __shfl_sync(kFull, bs, j) + (t - __shfl_sync(kFull, excl, j));
-            double cj[DIM];
+            V cj[DIM];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) cj[k] = __shfl_sync(kFull, cab[k], j);
-            const double mj1 = __shfl_sync(kFull, m1, j), mj2 = __shfl_sync(kFull, m2, j);
+            const V mj1 = __shfl_sync(kFull, m1, j), mj2 = __shfl_sync(kFull, m2, j);
             const bool act = t < total;
             int e = -1 - lane;
-            double dot = 0.0;
+            V dot = V(0);
             if (act) {
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) dot += cj[k] * pval(bj, pbc, 2 + k);
@@ -671,24 +680,24 @@ k_selfp_scatter(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
 
 // Entry-per-lane form with a binary search per (a, b, c): used for the rows
 // listed in rows[0..rows[-1]) that are too wide for k_selfp_scatter.
-template <int DIM>
+template <int DIM, class V>
 __global__ void k_selfp_values(const int* __restrict__ rows, const int* __restrict__ prp,
                                const int* __restrict__ pcol, const int* __restrict__ slice_ptr,
-                               const double* __restrict__ pv, const double* __restrict__ mdiag,
+                               const V* __restrict__ pv, const V* __restrict__ mdiag,
                                const int* __restrict__ srp, const int* __restrict__ scol,
-                               double* __restrict__ sval, int64_t nnz_half) {
+                               V* __restrict__ sval, int64_t nnz_half) {
     constexpr int NV = pair_values(DIM);
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= rows[-1]) return;
     const int64_t a = rows[w];
-    auto pval = [&](int row, int p, int k) -> double {
+    auto pval = [&](int row, int p, int k) -> V {
         int64_t grp = (int64_t)slice_ptr[row >> 5] + (p - prp[row]);
         return pv[(grp * NV + k) * kSell + (row & 31)];
     };
     for (int e = srp[a] + lane; e < srp[a + 1]; e += 32) {
         const int c = scol[e];
-        double s1 = 0.0, s2 = 0.0;
+        V s1 = V(0), s2 = V(0);
         const int pac = bsearch_row(pcol, prp[a], prp[a + 1], c);
         if (pac >= 0) {
             s1 = pval((int)a, pac, 2 + 2 * DIM);
@@ -698,7 +707,7 @@ __global__ void k_selfp_values(const int* __restrict__ rows, const int* __restri
             const int b = pcol[pab];
             const int pbc = bsearch_row(pcol, prp[b], prp[b + 1], c);
             if (pbc < 0) continue;
-            double dot = 0.0;
+            V dot = V(0);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) dot += pval((int)a, pab, 2 + DIM + k) * pval(b, pbc, 2 + k);
             s1 -= dot * mdiag[2 * b];
@@ -715,31 +724,32 @@ __global__ void k_selfp_values(const int* __restrict__ rows, const int* __restri
 // k_selfp_scatter does; the sorted columns and both networks' values go to
 // fixed-capacity staging rows. A row wider than CAP sets *ovf, and the
 // caller then builds S_p the two-pass way.
-template <int DIM, int CAP>
+template <int DIM, int CAP, class V>
 __global__ void __launch_bounds__(128, 8)
 k_selfp_onepass(int64_t n_nodes, const int* __restrict__ prp, const int* __restrict__ pcol,
-                const int* __restrict__ slice_ptr, const double* __restrict__ pv,
-                const double* __restrict__ mdiag, int* __restrict__ count, int* __restrict__ tcol,
-                double* __restrict__ tv1, double* __restrict__ tv2, int* __restrict__ ovf) {
+                const int* __restrict__ slice_ptr, const V* __restrict__ pv,
+                const V* __restrict__ mdiag, int* __restrict__ count, int* __restrict__ tcol,
+                V* __restrict__ tv1, V* __restrict__ tv2, int* __restrict__ ovf) {
     constexpr int NV = pair_values(DIM);
     constexpr int HT = 2 * CAP;
     constexpr int WPB = 4;
     __shared__ int sh_keys[WPB][HT];
     __shared__ int sh_slot[WPB][HT];
-    __shared__ double sh_acc[WPB][2][CAP];
+    __shared__ V sh_acc[WPB][2][CAP];
+    static_assert(2 * CAP * sizeof(V) >= HT * sizeof(int), "the key list lives in the accumulators");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t a = (int64_t)blockIdx.x * WPB + warp;
     if (a >= n_nodes) return;
     int* keys = sh_keys[warp];
     int* slot = sh_slot[warp];
-    double* acc1 = sh_acc[warp][0];
-    double* acc2 = sh_acc[warp][1];
-    auto pval = [&](int row, int p, int k) -> double {
+    V* acc1 = sh_acc[warp][0];
+    V* acc2 = sh_acc[warp][1];
+    auto pval = [&](int row, int p, int k) -> V {
         const int64_t grp = (int64_t)slice_ptr[row >> 5] + (p - prp[row]);
         return pv[(grp * NV + k) * kSell + (row & 31)];
     };
     const bool ok = warp_collect<HT>((int)a, prp, pcol, prp, pcol, keys, lane, INT_MIN);
-    int* list = reinterpret_cast<int*>(sh_acc[warp]);  // 4 CAP ints >= HT
+    int* list = reinterpret_cast<int*>(sh_acc[warp]);  // 2 CAP values >= HT ints
     const int u = ok ? warp_compact<HT>(keys, list, lane) : HT + 1;
     if (u > CAP) {
         if (lane == 0) {
@@ -749,7 +759,7 @@ k_selfp_onepass(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
         return;
     }
     warp_rank<HT>(list, u, lane, tcol + a * CAP, keys, slot);
-    for (int e = lane; e < CAP; e += 32) acc1[e] = acc2[e] = 0.0;
+    for (int e = lane; e < CAP; e += 32) acc1[e] = acc2[e] = V(0);
     __syncwarp();
     const int pa0 = prp[a], pa1 = prp[a + 1];
     for (int pac = pa0 + lane; pac < pa1; pac += 32) {  // D terms: distinct columns
@@ -761,9 +771,9 @@ k_selfp_onepass(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
     for (int pc0 = pa0; pc0 < pa1; pc0 += 32) {
         const int pab = pc0 + lane;
         int b = 0, bs = 0, len = 0;
-        double cab[DIM], m1 = 0.0, m2 = 0.0;
+        V cab[DIM], m1 = V(0), m2 = V(0);
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) cab[k] = 0.0;
+        for (int k = 0; k < DIM; ++k) cab[k] = V(0);
         if (pab < pa1) {
             b = pcol[pab];
             bs = prp[b];
@@ -791,13 +801,13 @@ k_selfp_onepass(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
             }
             const int bj = __shfl_sync(kFull, b, j);
             const int pbc = __shfl_sync(kFull, bs, j) + (t - __shfl_sync(kFull, excl, j));
-            double cj[DIM];
+            V cj[DIM];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) cj[k] = __shfl_sync(kFull, cab[k], j);
-            const double mj1 = __shfl_sync(kFull, m1, j), mj2 = __shfl_sync(kFull, m2, j);
+            const V mj1 = __shfl_sync(kFull, m1, j), mj2 = __shfl_sync(kFull, m2, j);
             const bool act = t < total;
             int e = -1 - lane;
-            double dot = 0.0;
+            V dot = V(0);
             if (act) {
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) dot += cj[k] * pval(bj, pbc, 2 + k);
@@ -824,11 +834,11 @@ k_selfp_onepass(int64_t n_nodes, const int* __restrict__ prp, const int* __restr
 }
 
 // staging rows into blockdiag(S_p1, S_p2): rows a and n + a (columns + n)
-template <int CAP>
+template <int CAP, class V>
 __global__ void k_selfp_compact(int64_t n, int64_t nnz_half, const int* __restrict__ rp,
-                                const int* __restrict__ tcol, const double* __restrict__ tv1,
-                                const double* __restrict__ tv2, int* __restrict__ srp,
-                                int* __restrict__ scol, double* __restrict__ sval) {
+                                const int* __restrict__ tcol, const V* __restrict__ tv1,
+                                const V* __restrict__ tv2, int* __restrict__ srp,
+                                int* __restrict__ scol, V* __restrict__ sval) {
     const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (a > n) return;
@@ -860,10 +870,11 @@ __global__ void k_col_count(const int* __restrict__ col, int64_t nnz, int* __res
     if (i < nnz) atomicAdd(&cnt[col[i]], 1);
 }
 
+template <class V>
 __global__ void k_transpose_scatter(int64_t n_rows, const int* __restrict__ rp,
-                                    const int* __restrict__ col, const double* __restrict__ val,
+                                    const int* __restrict__ col, const V* __restrict__ val,
                                     int* __restrict__ cursor, int* __restrict__ tcol,
-                                    double* __restrict__ tval) {
+                                    V* __restrict__ tval) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_rows) return;
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
@@ -874,9 +885,10 @@ __global__ void k_transpose_scatter(int64_t n_rows, const int* __restrict__ rp,
 }
 
 // warp per row: rank sort of (col, val) by col (distinct cols)
+template <class V>
 __global__ void k_sort_rows(int64_t n_rows, const int* __restrict__ rp, int* __restrict__ col,
-                            double* __restrict__ val, int* __restrict__ tmpc,
-                            double* __restrict__ tmpv) {
+                            V* __restrict__ val, int* __restrict__ tmpc,
+                            V* __restrict__ tmpv) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n_rows) return;
@@ -919,15 +931,15 @@ void pattern_tier(const CsrView& A, const CsrView& B, Csr& C, const int* rows, i
     DPP_LAUNCH_CK();
 }
 
-template <int CAP>
+template <int CAP, class V>
 void scatter_tier(const CsrView& A, const CsrView& B, Csr& C, int* wide, const int* is_long,
                   int upper, cudaStream_t s) {
     constexpr int HT = 2 * CAP < 64 ? 64 : 2 * CAP;
-    const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * CAP * sizeof(double);
-    set_smem(k_spgemm_scatter<HT, CAP>, smem);
-    k_spgemm_scatter<HT, CAP><<<grid_for(A.n_rows, kWarps), kWarps * 32, smem, s>>>(
-        A.n_rows, A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(),
-        C.val.get(), wide, is_long, upper);
+    const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * CAP * sizeof(V);
+    set_smem(k_spgemm_scatter<HT, CAP, V>, smem);
+    k_spgemm_scatter<HT, CAP, V><<<grid_for(A.n_rows, kWarps), kWarps * 32, smem, s>>>(
+        A.n_rows, A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
+        vbuf<V>(C).get(), wide, is_long, upper);
     DPP_LAUNCH_CK();
 }
 
@@ -958,34 +970,36 @@ __global__ void k_count_products(int64_t n, const int* __restrict__ arp, const i
 // memory budget, and the caller takes the counting path.
 constexpr int kOneCap = 128;
 
+template <class V>
 bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStream_t s,
                     HostScratch& hs) {
     const int64_t n = A.n_rows;
     const int64_t stage = n * (int64_t)kOneCap;
-    if (stage * (int64_t)(sizeof(int) + sizeof(double)) > (int64_t(4) << 30)) return false;
+    if (stage * (int64_t)(sizeof(int) + sizeof(V)) > (int64_t(4) << 30)) return false;
     C.n_rows = n;
     C.n_cols = B.n_cols;
     C.row_ptr.alloc(n + 1);
     DPP_CK(cudaMemsetAsync(C.row_ptr.get(), 0, (n + 1) * sizeof(int), s));
     DBuf<int> tcol(stage), uone(n), ovf(n + 2), ovf2(n + 2), last(2);
-    DBuf<double> tval(stage);
+    DBuf<V> tval(stage);
     DPP_CK(cudaMemsetAsync(ovf.get(), 0, sizeof(int), s));
     DPP_CK(cudaMemsetAsync(ovf2.get(), 0, sizeof(int), s));
     DPP_CK(cudaMemsetAsync(last.get(), 0, sizeof(int), s));
     // The one-pass product is also timed as a kernel family of its own. Its
     // algorithmic bytes: A and B (values, columns, row pointers) read once, and
     // the rows of C written once (known after the launch).
-    ProfScope po("spgemm_onepass", s, 0);
-    // the same launches with their algorithmic FP64 work (2 flops per product)
-    ProfScope pw("spgemm_onepass_flop", s, 0);
+    ProfScope po(sizeof(V) == 8 ? "spgemm_onepass" : "spgemm_onepass_fp32", s, 0);
+    // the same launches with their algorithmic work (2 flops per product)
+    ProfScope pw(sizeof(V) == 8 ? "spgemm_onepass_flop" : "spgemm_onepass_flop_fp32", s, 0);
     {
         ProfScope pf("spgemm_fill", s, 0);
         constexpr int HT = 2 * kOneCap;
-        const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) + (size_t)kWarps * kOneCap * sizeof(double);
-        set_smem(k_spgemm_onepass<HT, kOneCap>, smem);
-        k_spgemm_onepass<HT, kOneCap><<<grid_for(n, kWarps), kWarps * 32, smem, s>>>(
-            n, A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), uone.get(), tcol.get(),
-            tval.get(), ovf.get(), up);
+        const size_t smem = (size_t)kWarps * 2 * HT * sizeof(int) +
+                            (size_t)kWarps * onepass_acc_bytes<HT, kOneCap, V>();
+        set_smem(k_spgemm_onepass<HT, kOneCap, V>, smem);
+        k_spgemm_onepass<HT, kOneCap, V><<<grid_for(n, kWarps), kWarps * 32, smem, s>>>(
+            n, A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), uone.get(),
+            tcol.get(), tval.get(), ovf.get(), up);
         DPP_LAUNCH_CK();
     }
     po.end_range();
@@ -1011,36 +1025,36 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
         }
     }
     C.nnz = exclusive_scan(C.row_ptr.get(), C.row_ptr.get(), n + 1, s, hs);
-    po.bytes = 12.0 * (double)(A.nnz + B.nnz + C.nnz) + 4.0 * (double)(A.n_rows + B.n_rows + 2) +
+    po.bytes = (4.0 + sizeof(V)) * (double)(A.nnz + B.nnz + C.nnz) + 4.0 * (double)(A.n_rows + B.n_rows + 2) +
                4.0 * (double)n;
     po.stop();
     {
         ProfScope pa("spgemm_alloc", s, 0);
         C.col.alloc(std::max<int64_t>(C.nnz, 1));
-        C.val.alloc(std::max<int64_t>(C.nnz, 1));
+        vbuf<V>(C).alloc(std::max<int64_t>(C.nnz, 1));
     }
     ProfScope pf("spgemm_fill", s, 0);
-    k_onepass_compact<kOneCap><<<grid_for(n * 32, 256), 256, 0, s>>>(n, uone.get(), C.row_ptr.get(), tcol.get(),
-                                                                    tval.get(), C.col.get(), C.val.get());
+    k_onepass_compact<kOneCap, V><<<grid_for(n * 32, 256), 256, 0, s>>>(
+        n, uone.get(), C.row_ptr.get(), tcol.get(), tval.get(), C.col.get(), vbuf<V>(C).get());
     DPP_LAUNCH_CK();
     if (n_ovf > 0) {  // one block per overflow row; rows wider than kLongCap: one warp each
         DBuf<int> wide(n_ovf + 2), st(1);
         DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
         DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
         const size_t smem_l = (size_t)(kLongHT + 2 * kLongCap) * sizeof(int) +
-                              (size_t)kLongWarps * kLongCap * sizeof(double);
-        set_smem(k_long_numeric, smem_l);
-        k_long_numeric<<<(unsigned)n_ovf, kLongWarps * 32, smem_l, s>>>(
-            A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(), C.val.get(),
-            ovf.get() + 1, wide.get(), up);
+                              (size_t)kLongWarps * kLongCap * sizeof(V);
+        set_smem(k_long_numeric<V>, smem_l);
+        k_long_numeric<V><<<(unsigned)n_ovf, kLongWarps * 32, smem_l, s>>>(
+            A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
+            vbuf<V>(C).get(), ovf.get() + 1, wide.get(), up);
         DPP_LAUNCH_CK();
         const int n_wide = read_scalar(wide.get(), s, hs);
         if (n_wide > 0) {
             const size_t smem = (size_t)2 * 8192 * sizeof(int);
-            set_smem(k_spgemm_wide<8192>, smem);
-            k_spgemm_wide<8192><<<(unsigned)n_wide, 32, smem, s>>>(A.rp, A.col, A.val, B.rp, B.col, B.val,
-                                                                   C.row_ptr.get(), C.col.get(), C.val.get(),
-                                                                   wide.get() + 1, st.get(), up);
+            set_smem(k_spgemm_wide<8192, V>, smem);
+            k_spgemm_wide<8192, V><<<(unsigned)n_wide, 32, smem, s>>>(
+                A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
+                vbuf<V>(C).get(), wide.get() + 1, st.get(), up);
             DPP_LAUNCH_CK();
             if (read_scalar(st.get(), s, hs))
                 fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
@@ -1051,14 +1065,18 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
 }
 }  // namespace
 
-void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
-            HostScratch& hs, bool upper_only) {
+namespace {
+template <class V>
+void spgemm_t(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
+              HostScratch& hs, bool upper_only) {
     const int up = upper_only ? 1 : 0;
     ProfScope prof(values ? "spgemm_numeric" : "spgemm_pattern", s, 0);
     if (A.n_cols != B.n_rows) fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: shape mismatch");
+    if (values && (!vals_of<V>(A) || !vals_of<V>(B)))
+        fail(DPP_ERR_BAD_STATE, "spgemm: operands without values of the product's type");
     const int64_t n = A.n_rows;
     // many rows: one numeric pass, counting only the rows that overflow it
-    if (values && n >= 16384 && spgemm_onepass(A, B, C, up, s, hs)) return;
+    if (values && n >= 16384 && spgemm_onepass<V>(A, B, C, up, s, hs)) return;
     C.n_rows = n;
     C.n_cols = B.n_cols;
     C.row_ptr.alloc(n + 1);
@@ -1116,7 +1134,7 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     {
         ProfScope pa("spgemm_alloc", s, 0);
         C.col.alloc(std::max<int64_t>(C.nnz, 1));
-        if (values) C.val.alloc(std::max<int64_t>(C.nnz, 1));
+        if (values) vbuf<V>(C).alloc(std::max<int64_t>(C.nnz, 1));
     }
     ProfScope pf(values ? "spgemm_fill" : "spgemm_fill_pattern", s, 0);
     if (!values) {
@@ -1136,36 +1154,45 @@ void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_
     DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
     if (n_long > 0) {
         const size_t smem = (size_t)(kLongHT + 2 * kLongCap) * sizeof(int) +
-                            (size_t)kLongWarps * kLongCap * sizeof(double);
-        set_smem(k_long_numeric, smem);
-        k_long_numeric<<<(unsigned)n_long, kLongWarps * 32, smem, s>>>(
-            A.rp, A.col, A.val, B.rp, B.col, B.val, C.row_ptr.get(), C.col.get(), C.val.get(),
-            long_rows.get() + 1, wide.get(), up);
+                            (size_t)kLongWarps * kLongCap * sizeof(V);
+        set_smem(k_long_numeric<V>, smem);
+        k_long_numeric<V><<<(unsigned)n_long, kLongWarps * 32, smem, s>>>(
+            A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
+            vbuf<V>(C).get(), long_rows.get() + 1, wide.get(), up);
         DPP_LAUNCH_CK();
     }
     if (n_long < n) {
-        if (max_u <= 32) scatter_tier<32>(A, B, C, wide.get(), long_flag, up, s);
-        else if (max_u <= 64) scatter_tier<64>(A, B, C, wide.get(), long_flag, up, s);
-        else if (max_u <= 128) scatter_tier<128>(A, B, C, wide.get(), long_flag, up, s);
-        else if (max_u <= 256) scatter_tier<256>(A, B, C, wide.get(), long_flag, up, s);
-        else if (max_u <= 512) scatter_tier<512>(A, B, C, wide.get(), long_flag, up, s);
-        else scatter_tier<1024>(A, B, C, wide.get(), long_flag, up, s);
+        if (max_u <= 32) scatter_tier<32, V>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 64) scatter_tier<64, V>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 128) scatter_tier<128, V>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 256) scatter_tier<256, V>(A, B, C, wide.get(), long_flag, up, s);
+        else if (max_u <= 512) scatter_tier<512, V>(A, B, C, wide.get(), long_flag, up, s);
+        else scatter_tier<1024, V>(A, B, C, wide.get(), long_flag, up, s);
     }
     const int n_wide = read_scalar(wide.get(), s, hs);
     if (n_wide > 0) {
         const size_t smem = (size_t)2 * 8192 * sizeof(int);
-        set_smem(k_spgemm_wide<8192>, smem);
-        k_spgemm_wide<8192><<<n_wide, 32, smem, s>>>(A.rp, A.col, A.val, B.rp, B.col, B.val,
-                                                     C.row_ptr.get(), C.col.get(), C.val.get(),
-                                                     wide.get() + 1, st.get(), up);
+        set_smem(k_spgemm_wide<8192, V>, smem);
+        k_spgemm_wide<8192, V><<<n_wide, 32, smem, s>>>(A.rp, A.col, vals_of<V>(A), B.rp, B.col,
+                                                        vals_of<V>(B), C.row_ptr.get(), C.col.get(),
+                                                        vbuf<V>(C).get(), wide.get() + 1, st.get(), up);
         DPP_LAUNCH_CK();
         if (read_scalar(st.get(), s, hs))
             fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
     }
     DPP_CK(cudaStreamSynchronize(s));
 }
+}  // namespace
 
-void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs) {
+void spgemm(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStream_t s,
+            HostScratch& hs, bool upper_only) {
+    if (values && !A.val && A.val32) spgemm_t<float>(A, B, C, values, s, hs, upper_only);
+    else spgemm_t<double>(A, B, C, values, s, hs, upper_only);
+}
+
+namespace {
+template <class V>
+void transpose_t(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs) {
     T.n_rows = A.n_cols;
     T.n_cols = A.n_rows;
     T.nnz = A.nnz;
@@ -1178,20 +1205,27 @@ void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs) {
     }
     exclusive_scan(T.row_ptr.get(), T.row_ptr.get(), T.n_rows + 1, s, hs);
     T.col.alloc(std::max<int64_t>(A.nnz, 1));
-    T.val.alloc(std::max<int64_t>(A.nnz, 1));
+    vbuf<V>(T).alloc(std::max<int64_t>(A.nnz, 1));
     DBuf<int> cursor(T.n_rows + 1);
     DPP_CK(cudaMemcpyAsync(cursor.get(), T.row_ptr.get(), (T.n_rows + 1) * sizeof(int),
                            cudaMemcpyDeviceToDevice, s));
-    k_transpose_scatter<<<grid_for(A.n_rows, B), B, 0, s>>>(A.n_rows, A.row_ptr.get(), A.col.get(),
-                                                            A.val.get(), cursor.get(), T.col.get(),
-                                                            T.val.get());
+    k_transpose_scatter<V><<<grid_for(A.n_rows, B), B, 0, s>>>(A.n_rows, A.row_ptr.get(), A.col.get(),
+                                                               vbuf<V>(A).get(), cursor.get(), T.col.get(),
+                                                               vbuf<V>(T).get());
     DPP_LAUNCH_CK();
     DBuf<int> tc(std::max<int64_t>(A.nnz, 1));
-    DBuf<double> tv(std::max<int64_t>(A.nnz, 1));
-    k_sort_rows<<<grid_for(T.n_rows * 32, B), B, 0, s>>>(T.n_rows, T.row_ptr.get(), T.col.get(),
-                                                         T.val.get(), tc.get(), tv.get());
+    DBuf<V> tv(std::max<int64_t>(A.nnz, 1));
+    k_sort_rows<V><<<grid_for(T.n_rows * 32, B), B, 0, s>>>(T.n_rows, T.row_ptr.get(), T.col.get(),
+                                                            vbuf<V>(T).get(), tc.get(), tv.get());
     DPP_LAUNCH_CK();
     DPP_CK(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+// The FP64 values are transposed when A has them, else the FP32 ones.
+void transpose(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs) {
+    if (fp32_only(A)) transpose_t<float>(A, T, s, hs);
+    else transpose_t<double>(A, T, s, hs);
 }
 
 namespace {
@@ -1207,11 +1241,12 @@ __global__ void k_sym_count(int64_t n, const int* __restrict__ urp, const int* _
 }
 
 // one warp per row: the strictly lower part from T, then U's row (both sorted)
+template <class V>
 __global__ void k_sym_fill(int64_t n, const int* __restrict__ urp, const int* __restrict__ ucol,
-                           const double* __restrict__ uval, const int* __restrict__ trp,
-                           const int* __restrict__ tcol, const double* __restrict__ tval,
+                           const V* __restrict__ uval, const int* __restrict__ trp,
+                           const int* __restrict__ tcol, const V* __restrict__ tval,
                            const int* __restrict__ crp, int* __restrict__ ccol,
-                           double* __restrict__ cval) {
+                           V* __restrict__ cval) {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -1229,8 +1264,9 @@ __global__ void k_sym_fill(int64_t n, const int* __restrict__ urp, const int* __
 
 // one warp per checked row (every stride-th row): flag entries whose mirror
 // is missing or differs
+template <class V>
 __global__ void k_sym_check(int64_t n, int stride, const int* __restrict__ rp, const int* __restrict__ col,
-                            const double* __restrict__ val, double tol, int* __restrict__ bad) {
+                            const V* __restrict__ val, double tol, int* __restrict__ bad) {
     const int64_t i = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * stride;
     const int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -1246,7 +1282,9 @@ __global__ void k_sym_check(int64_t n, int stride, const int* __restrict__ rp, c
 }
 }  // namespace
 
-void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs) {
+namespace {
+template <class V>
+void symmetrize_upper_t(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs) {
     Csr T;
     transpose(U, T, s, hs);
     const int64_t n = U.n_rows;
@@ -1258,12 +1296,18 @@ void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs) {
     DPP_LAUNCH_CK();
     C.nnz = exclusive_scan(C.row_ptr.get(), C.row_ptr.get(), n + 1, s, hs);
     C.col.alloc(std::max<int64_t>(C.nnz, 1));
-    C.val.alloc(std::max<int64_t>(C.nnz, 1));
-    k_sym_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(n, U.row_ptr.get(), U.col.get(), U.val.get(),
-                                                     T.row_ptr.get(), T.col.get(), T.val.get(),
-                                                     C.row_ptr.get(), C.col.get(), C.val.get());
+    vbuf<V>(C).alloc(std::max<int64_t>(C.nnz, 1));
+    k_sym_fill<V><<<grid_for(n * 32, 256), 256, 0, s>>>(n, U.row_ptr.get(), U.col.get(), vbuf<V>(U).get(),
+                                                        T.row_ptr.get(), T.col.get(), vbuf<V>(T).get(),
+                                                        C.row_ptr.get(), C.col.get(), vbuf<V>(C).get());
     DPP_LAUNCH_CK();
     DPP_CK(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+void symmetrize_upper(const Csr& U, Csr& C, cudaStream_t s, HostScratch& hs) {
+    if (fp32_only(U)) symmetrize_upper_t<float>(U, C, s, hs);
+    else symmetrize_upper_t<double>(U, C, s, hs);
 }
 
 bool is_symmetric(const Csr& A, double tol, int stride, cudaStream_t s, HostScratch& hs) {
@@ -1271,24 +1315,33 @@ bool is_symmetric(const Csr& A, double tol, int stride, cudaStream_t s, HostScra
     DBuf<int> bad(1);
     DPP_CK(cudaMemsetAsync(bad.get(), 0, sizeof(int), s));
     const int64_t rows = (A.n_rows + stride - 1) / stride;
-    k_sym_check<<<grid_for(rows * 32, 256), 256, 0, s>>>(A.n_rows, stride, A.row_ptr.get(), A.col.get(),
-                                                         A.val.get(), tol, bad.get());
+    const int g = grid_for(rows * 32, 256);
+    if (fp32_only(A))
+        k_sym_check<float><<<g, 256, 0, s>>>(A.n_rows, stride, A.row_ptr.get(), A.col.get(),
+                                             A.val32.get(), tol, bad.get());
+    else
+        k_sym_check<double><<<g, 256, 0, s>>>(A.n_rows, stride, A.row_ptr.get(), A.col.get(),
+                                              A.val.get(), tol, bad.get());
     DPP_LAUNCH_CK();
     return read_scalar(bad.get(), s, hs) == 0;
 }
 
 namespace {
 // one-pass S_p when every row fits kSelfpOneCap columns; false = not built
-template <int DIM, int CAP>
-bool selfp_onepass(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
+template <class V> const V* pair_vals(const ProblemImpl& P);
+template <> const double* pair_vals<double>(const ProblemImpl& P) { return P.sell_val.get(); }
+template <> const float* pair_vals<float>(const ProblemImpl& P) { return P.sell_val32.get(); }
+
+template <int DIM, int CAP, class V>
+bool selfp_onepass(const ProblemImpl& P, const V* mdiag, Csr& S, cudaStream_t s,
                    HostScratch& hs) {
     const int64_t n = P.n_nodes;
     DBuf<int> cnt(n + 1), tcol(n * CAP), ovf(1);
-    DBuf<double> tv1(n * CAP), tv2(n * CAP);
+    DBuf<V> tv1(n * CAP), tv2(n * CAP);
     DPP_CK(cudaMemsetAsync(cnt.get(), 0, (n + 1) * sizeof(int), s));
     DPP_CK(cudaMemsetAsync(ovf.get(), 0, sizeof(int), s));
-    k_selfp_onepass<DIM, CAP><<<grid_for(n, 4), 128, 0, s>>>(
-        n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(), mdiag, cnt.get(),
+    k_selfp_onepass<DIM, CAP, V><<<grid_for(n, 4), 128, 0, s>>>(
+        n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), pair_vals<V>(P), mdiag, cnt.get(),
         tcol.get(), tv1.get(), tv2.get(), ovf.get());
     DPP_LAUNCH_CK();
     if (read_scalar(ovf.get(), s, hs)) return false;
@@ -1297,18 +1350,18 @@ bool selfp_onepass(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream
     S.nnz = 2 * nnz;
     S.row_ptr.alloc(2 * n + 1);
     S.col.alloc(std::max<int64_t>(2 * nnz, 1));
-    S.val.alloc(std::max<int64_t>(2 * nnz, 1));
-    k_selfp_compact<CAP><<<grid_for((n + 1) * 32, 256), 256, 0, s>>>(
-        n, nnz, cnt.get(), tcol.get(), tv1.get(), tv2.get(), S.row_ptr.get(), S.col.get(), S.val.get());
+    vbuf<V>(S).alloc(std::max<int64_t>(2 * nnz, 1));
+    k_selfp_compact<CAP, V><<<grid_for((n + 1) * 32, 256), 256, 0, s>>>(
+        n, nnz, cnt.get(), tcol.get(), tv1.get(), tv2.get(), S.row_ptr.get(), S.col.get(),
+        vbuf<V>(S).get());
     DPP_LAUNCH_CK();
     DPP_CK(cudaStreamSynchronize(s));
     return true;
 }
-}  // namespace
-
-void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
-                 HostScratch& hs) {
-    if (P.dim == 3 ? selfp_onepass<3, 128>(P, mdiag, S, s, hs) : selfp_onepass<2, 64>(P, mdiag, S, s, hs))
+template <class V>
+void build_selfp_t(const ProblemImpl& P, const V* mdiag, Csr& S, cudaStream_t s, HostScratch& hs) {
+    if (!pair_vals<V>(P)) fail(DPP_ERR_BAD_STATE, "selfp: pair values of this precision were not assembled");
+    if (P.dim == 3 ? selfp_onepass<3, 128, V>(P, mdiag, S, s, hs) : selfp_onepass<2, 64, V>(P, mdiag, S, s, hs))
         return;
     // two passes: pattern of G*G with G the pair graph (self pairs included), then values
     CsrView G;
@@ -1323,7 +1376,7 @@ void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t
     S.nnz = 2 * nnz;
     S.row_ptr.alloc(2 * n + 1);
     S.col.alloc(2 * nnz);
-    S.val.alloc(2 * nnz);
+    vbuf<V>(S).alloc(2 * nnz);
     DPP_CK(cudaMemcpyAsync(S.row_ptr.get(), Sh.row_ptr.get(), (n + 1) * sizeof(int),
                            cudaMemcpyDeviceToDevice, s));
     DPP_CK(cudaMemcpyAsync(S.col.get(), Sh.col.get(), nnz * sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -1335,27 +1388,38 @@ void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t
     DBuf<int> wide(n + 1);
     DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
     if (P.dim == 2)
-        k_selfp_scatter<2, kSelfpCap><<<grid_for(n, 4), 128, 0, s>>>(
-            n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(), mdiag,
-            Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz, wide.get());
+        k_selfp_scatter<2, kSelfpCap, V><<<grid_for(n, 4), 128, 0, s>>>(
+            n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), pair_vals<V>(P), mdiag,
+            Sh.row_ptr.get(), Sh.col.get(), vbuf<V>(S).get(), nnz, wide.get());
     else
-        k_selfp_scatter<3, kSelfpCap><<<grid_for(n, 4), 128, 0, s>>>(
-            n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(), mdiag,
-            Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz, wide.get());
+        k_selfp_scatter<3, kSelfpCap, V><<<grid_for(n, 4), 128, 0, s>>>(
+            n, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), pair_vals<V>(P), mdiag,
+            Sh.row_ptr.get(), Sh.col.get(), vbuf<V>(S).get(), nnz, wide.get());
     DPP_LAUNCH_CK();
     const int n_wide = read_scalar(wide.get(), s, hs);
     if (n_wide > 0) {
         if (P.dim == 2)
-            k_selfp_values<2><<<grid_for((int64_t)n_wide * 32, B), B, 0, s>>>(
-                wide.get() + 1, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(),
-                mdiag, Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz);
+            k_selfp_values<2, V><<<grid_for((int64_t)n_wide * 32, B), B, 0, s>>>(
+                wide.get() + 1, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), pair_vals<V>(P),
+                mdiag, Sh.row_ptr.get(), Sh.col.get(), vbuf<V>(S).get(), nnz);
         else
-            k_selfp_values<3><<<grid_for((int64_t)n_wide * 32, B), B, 0, s>>>(
-                wide.get() + 1, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), P.sell_val.get(),
-                mdiag, Sh.row_ptr.get(), Sh.col.get(), S.val.get(), nnz);
+            k_selfp_values<3, V><<<grid_for((int64_t)n_wide * 32, B), B, 0, s>>>(
+                wide.get() + 1, P.row_ptr.get(), P.col.get(), P.slice_ptr.get(), pair_vals<V>(P),
+                mdiag, Sh.row_ptr.get(), Sh.col.get(), vbuf<V>(S).get(), nnz);
         DPP_LAUNCH_CK();
     }
     DPP_CK(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+void build_selfp(const ProblemImpl& P, const double* mdiag, Csr& S, cudaStream_t s,
+                 HostScratch& hs) {
+    build_selfp_t<double>(P, mdiag, S, s, hs);
+}
+
+void build_selfp(const ProblemImpl& P, const float* mdiag, Csr& S, cudaStream_t s,
+                 HostScratch& hs) {
+    build_selfp_t<float>(P, mdiag, S, s, hs);
 }
 
 }  // namespace dpp
