@@ -197,7 +197,9 @@ dpp_status dpp_assemble(const dpp_problem_desc* desc, int32_t precision, dpp_str
  * the default) or Method 1 (splitting by scales), as opts->composition says.
  * It forms S_pi = Ki_pp - Ki_pu diag(Ki_uu)^-1 Ki_up (Eqs. "S4_sp1",
  * "S4_sp2") on the device, then smoothed-aggregation AMG: one hierarchy on
- * blockdiag(S_p1, S_p2) (Method 2) or one per S_pi (Method 1).
+ * blockdiag(S_p1, S_p2) (Method 2) or one per S_pi (Method 1). With
+ * opts->precision = DPP_MIXED_FP32_FP64 the S_pi and the whole hierarchy are
+ * built in FP32 from the FP32 pair values (only the coarsest inverse is FP64).
  * Synchronises `stream`. Errors: INVALID_ARGUMENT, OUT_OF_MEMORY, CUDA.
  * Size limit: row pointers are int32, so the nonzeros of blockdiag(S_p1,
  * S_p2), of every level matrix and of every prolongator must each stay below
@@ -323,7 +325,8 @@ dpp_status dpp_export_pairs(dpp_problem prob, int32_t* row_ptr, int32_t* col, do
                             dpp_stream_t stream);
 
 /* z = P^-1 r for the preconditioner (device [n_nodes][2d+2]); transpose != 0
- * applies the preconditioner of K^T. */
+ * applies the preconditioner of K^T. A DPP_MIXED_FP32_FP64 preconditioner holds
+ * its FP32 hierarchy only: z is then its FP32 result, widened to FP64. */
 dpp_status dpp_pc_apply(dpp_problem prob, dpp_pc pc, int32_t transpose, const double* r,
                         double* z, dpp_stream_t stream);
 
@@ -349,7 +352,8 @@ dpp_status dpp_pc_level_sizes(dpp_pc pc, int32_t level, int64_t out[5]);
  * = blockdiag(S_p1, S_p2) for the field split; S_p1 or S_p2 for the scale
  * split) and, for level < levels-1, its prolongator P (device arrays sized
  * from the level sizes). Null P pointers skip P. dpp_pc_export_level is
- * hierarchy 0. */
+ * hierarchy 0. The hierarchy of a DPP_MIXED_FP32_FP64 preconditioner is built
+ * in FP32; its values are exported widened to FP64. */
 dpp_status dpp_pc_hierarchy_export_level(dpp_pc pc, int32_t hierarchy, int32_t level,
                                          int32_t* row_ptr, int32_t* col, double* val,
                                          int32_t* p_row_ptr, int32_t* p_col, double* p_val,

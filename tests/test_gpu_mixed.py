@@ -77,3 +77,50 @@ def test_mixed_adjoint_matches_fp64_adjoint(DPPSystem):
     assert abs(hb.item() - gb.item()) <= 1e-8 * abs(gb.item())
     ref.close()
     mix.close()
+
+
+@pytest.mark.parametrize("dim,n,opts", [(2, 40, {"coarse_max_rows": 64}), (3, 20, {})],
+                         ids=["2d40_multilevel", "3d20_onepass"])
+def test_fp32_hierarchy_matches_its_definitions(DPPSystem, dim, n, opts):
+    # The mixed mode builds S_p and every level in FP32 (FP32 pair values,
+    # FP32 accumulators in the FP64 path's summation order). Level 0 must be the
+    # selfp Schur matrices of the oracle's K, and every coarser level the
+    # Galerkin product P^T A P of the exported FP32 level, both to FP32
+    # rounding: 1e-5 of the largest entry (sums of up to ~700 products). Two
+    # setups are bit-identical.
+    import scipy.sparse as sp
+    from gpu_helpers import csr_from_export
+    P = inputs.heterogeneous_problem(dim, n, seed=8, beta=1.0)
+    K, _ = assemble_problem(P)
+    S1, S2 = oracle.selfp_schur(K, P.mesh.n_nodes, dim)
+    ref0 = sp.block_diag([S1, S2]).tocsr()
+    s1 = DPPSystem.from_problem(P, precision=MIXED).setup_pc(precision=MIXED, **opts)
+    s2 = DPPSystem.from_problem(P, precision=MIXED).setup_pc(precision=MIXED, **opts)
+    sz, (rp, col, val), _ = s1.level(0, with_p=False)
+    S = csr_from_export(rp, col, val, ref0.shape)
+    assert abs(S - ref0).max() <= 1e-5 * abs(ref0).max()
+    assert np.array_equal(val.cpu().numpy(), val.cpu().numpy().astype(np.float32))  # FP32 values
+    nlev = sz["levels"]
+    assert nlev >= 2
+    for l in range(nlev - 1):
+        szl, (rp, col, val), (prp, pcol, pval) = s1.level(l)
+        A = csr_from_export(rp, col, val, (szl["rows"], szl["rows"]))
+        Pm = csr_from_export(prp, pcol, pval, (szl["rows"], szl["p_cols"]))
+        sz2, (rp2, col2, val2), _ = s1.level(l + 1, with_p=False)
+        Ac = csr_from_export(rp2, col2, val2, (sz2["rows"], sz2["rows"]))
+        ref = (Pm.T @ A @ Pm).tocsr()
+        assert abs(Ac - ref).max() <= 1e-5 * abs(ref).max(), l
+        assert abs(Ac - Ac.T).max() <= 1e-5 * abs(Ac).max(), l
+    for l in range(nlev):
+        a = s1.level(l, with_p=False)[1]
+        b = s2.level(l, with_p=False)[1]
+        for u, v in zip(a, b):
+            assert torch.equal(u, v), f"level {l} differs between two setups"
+    # the FP64 entry point of a mixed preconditioner returns its FP32 result, widened
+    r = torch.tensor(inputs.rng(3).standard_normal((P.mesh.n_nodes, 2 * dim + 2)), device="cuda")
+    z = s1.pc_apply(r)
+    assert torch.isfinite(z).all()
+    assert np.array_equal(z.cpu().numpy(), z.cpu().numpy().astype(np.float32).astype(np.float64))
+    assert torch.equal(z, s2.pc_apply(r))
+    s1.close()
+    s2.close()
