@@ -471,7 +471,13 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
         dpp_pc_s pc;
         EventTimer ta(s);
         prob.impl.precision = po.precision;
-        assemble_union(prob.impl, n_inst, descs, codes, s);
+        try {
+            assemble_union(prob.impl, n_inst, descs, codes, s);
+        } catch (const Error& e) {  // e.g. no valid instance: every info says why
+            for (int i = 0; i < n_inst; ++i)
+                infos[i].status = (i < (int)codes.size() && codes[i]) ? codes[i] : e.status;
+            throw;
+        }
         const double ms_asm = ta.stop();
         EventTimer tb(s);
         pc.impl.opts = po;

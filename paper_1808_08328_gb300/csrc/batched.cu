@@ -49,9 +49,14 @@ constexpr int kChunk = 4096;   // vector entries per reduction chunk
 constexpr int kSegThreads = 256;
 
 // ------------------------------------------------------------------ union construction
+// Cell checks per instance: vertex ids in range, finite log k, and (ids in
+// range) a simplex of nonzero measure. Ids are still the instance's own, so
+// its vertices are read at the instance's node offset in the union.
 __global__ void k_check_instance_cells(const int* __restrict__ cells, int64_t n_cells, int nv,
                                        const int* __restrict__ cell_inst,
                                        const int64_t* __restrict__ inst_nodes,
+                                       const int64_t* __restrict__ inst_noff,
+                                       const double* __restrict__ X, int dim,
                                        const double* __restrict__ lk1,
                                        const double* __restrict__ lk2, int* __restrict__ flag) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,6 +68,19 @@ __global__ void k_check_instance_cells(const int* __restrict__ cells, int64_t n_
         if (a < 0 || a >= inst_nodes[b]) bad |= kDevBadIndex;
     }
     if (!isfinite(lk1[c]) || !isfinite(lk2[c])) bad |= kDevNonFinite;
+    if (!(bad & kDevBadIndex)) {  // det of the edge vectors from vertex 0
+        double e[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        const double* x0 = X + (inst_noff[b] + cells[c * nv]) * dim;
+        for (int v = 1; v < nv && v <= 3; ++v) {
+            const double* xv = X + (inst_noff[b] + cells[c * nv + v]) * dim;
+            for (int k = 0; k < dim; ++k) e[v - 1][k] = xv[k] - x0[k];
+        }
+        const double det = (dim == 2) ? e[0][0] * e[1][1] - e[0][1] * e[1][0]
+                                      : e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                                            e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                                            e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        if (isfinite(det) && !(fabs(det) > 0.0)) bad |= kDevDegenerate;  // NaN: the node check
+    }
     if (bad) atomicOr(&flag[b], bad);
 }
 
@@ -531,7 +549,8 @@ void assemble_union(ProblemImpl& P, int n, const dpp_problem_desc* descs, std::v
         DBuf<int> flags(nl);
         DPP_CK(cudaMemsetAsync(flags.get(), 0, nl * sizeof(int), s));
         k_check_instance_cells<<<grid_for(P.n_cells, 256), 256, 0, s>>>(
-            P.cells.get(), P.n_cells, nv, cell_inst.get(), d_nnodes.get(), P.logk1.get(), P.logk2.get(), flags.get());
+            P.cells.get(), P.n_cells, nv, cell_inst.get(), d_nnodes.get(), d_noff.get(), P.coords.get(), dim,
+            P.logk1.get(), P.logk2.get(), flags.get());
         DPP_LAUNCH_CK();
         k_check_instance_nodes<<<grid_for(P.n_nodes, 256), 256, 0, s>>>(
             P.coords.get(), P.n_nodes, dim, node_inst.get(), P.p01.get(), P.p02.get(), flags.get());
@@ -547,7 +566,8 @@ void assemble_union(ProblemImpl& P, int n, const dpp_problem_desc* descs, std::v
         bool any_bad = false;
         for (int i = 0; i < nl; ++i)
             if (hf[i]) {
-                codes[live[i]] = (hf[i] & kDevBadIndex) ? DPP_ERR_INVALID_ARGUMENT : DPP_ERR_NONFINITE;
+                codes[live[i]] = (hf[i] & (kDevBadIndex | kDevDegenerate)) ? DPP_ERR_INVALID_ARGUMENT
+                                                                           : DPP_ERR_NONFINITE;
                 any_bad = true;
             }
         if (any_bad) {

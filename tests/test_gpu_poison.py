@@ -24,7 +24,7 @@ def test_suites_pass_with_poisoned_allocations():
     targets = [os.path.join(HERE, f) for f in
                ("test_gpu_parity.py", "test_gpu_mixed.py", "test_gpu_batched.py",
                 "test_gpu_adjoint.py", "test_gpu_sell.py", "test_gpu_scale_split.py",
-                "test_gpu_matfree.py", "test_gpu_inner.py", "test_gpu_q1.py")]
+                "test_gpu_matfree.py", "test_gpu_inner.py", "test_gpu_q1.py", "test_gpu_edge.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-m", "gpu", "-p", "no:cacheprovider",
                         *targets], env=env, cwd=os.path.dirname(HERE), capture_output=True,
                        text=True, timeout=1200)
