@@ -27,7 +27,9 @@
 // 1.1 lambda_max] (Adams, Brezina, Hu & Tuminaro, J. Comput. Phys. 188,
 // 2003).
 #include "amg.cuh"
+#include "level_spmv.cuh"
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -39,123 +41,40 @@ namespace dpp {
 
 namespace {
 
-// ------------------------------------------------------------------ CSR SpMV
-// Chebyshev step fused into the residual SpMV (MODE 3): with r = b - A x,
-// d = c1 d + c2 Dinv r and xo = x + d, written to xo (not x, which other rows
-// still read). c1 = 0 does not read d.
-template <class T>
-struct ChebOut {
-    const T* dinv = nullptr;
-    T* d = nullptr;
-    T* xo = nullptr;
-    T c1 = T(0), c2 = T(0);
-};
-
-template <int MODE, class T>
-__device__ __forceinline__ void spmv_out(int64_t row, T acc, const T* __restrict__ x, const T* __restrict__ b,
-                                         T* __restrict__ y, const ChebOut<T>& ch) {
-    if (MODE == 0) y[row] = acc;
-    else if (MODE == 1) y[row] = b[row] - acc;
-    else if (MODE == 2) y[row] += acc;
-    else {
-        const T r = b[row] - acc;
-        const T dn = (ch.c1 != T(0) ? ch.c1 * ch.d[row] : T(0)) + ch.c2 * ch.dinv[row] * r;
-        ch.d[row] = dn;
-        ch.xo[row] = x[row] + dn;
+// smallest column of each slice (base[s]) and a flag if any slice's columns
+// span 65536 or more; one warp per slice. A lane reads only its own row's
+// slots (k * 32 + lane): the slots of rows past n_rows in the last slice are
+// never written.
+__global__ void k_sell_span(int64_t n_rows, int64_t n_sl, const int* __restrict__ off,
+                            const int* __restrict__ scol, int* __restrict__ base, int* __restrict__ wide) {
+    const int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= n_sl) return;
+    int lo = INT_MAX, hi = INT_MIN;
+    if (sl * 32 + lane < n_rows)
+        for (int q = off[sl] + lane; q < off[sl + 1]; q += 32) {
+            lo = min(lo, scol[q]);
+            hi = max(hi, scol[q]);
+        }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        base[sl] = (lo == INT_MAX) ? 0 : lo;
+        if (lo != INT_MAX && (int64_t)hi - (int64_t)lo > 65535) atomicOr(wide, 1);
     }
 }
 
-// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x; 3: Chebyshev step (above).
-// T: values, vectors and arithmetic.
-// L lanes share a row; each lane walks its entries four at a time with four
-// independent partial sums, so that several gathers are in flight.
-template <int L, int MODE, class T>
-__global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __restrict__ rp,
-                                                  const int* __restrict__ col,
-                                                  const T* __restrict__ val,
-                                                  const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y,
-                                                  ChebOut<T> ch) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = t / L;
-    const int lane = (int)(t % L);
-    const bool active = row < n_rows;  // inactive lanes still join the shuffles
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    if (active) {
-        int p = rp[row] + lane;
-        const int e = rp[row + 1];
-        for (; p + 3 * L < e; p += 4 * L) {
-            const int c0 = col[p], c1 = col[p + L], c2 = col[p + 2 * L], c3 = col[p + 3 * L];
-            const T v0 = val[p], v1 = val[p + L], v2 = val[p + 2 * L], v3 = val[p + 3 * L];
-            a0 += v0 * __ldg(x + c0);
-            a1 += v1 * __ldg(x + c1);
-            a2 += v2 * __ldg(x + c2);
-            a3 += v3 * __ldg(x + c3);
-        }
-        for (; p < e; p += L) a0 += val[p] * __ldg(x + col[p]);
-    }
-    T acc = (a0 + a1) + (a2 + a3);
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
-    if (active && lane == 0) spmv_out<MODE, T>(row, acc, x, b, y, ch);
-}
-
-// ------------------------------------------------------------------ SELL-32 SpMV
-// One thread per row; a warp owns a slice, so every column and value load of
-// the warp is one contiguous 128 B (int, float) or 256 B (double) transaction.
-// U partial sums keep U gathers in flight: 4 in FP64 (the FP64 pipe is the
-// other limit there), 8 in FP32. Same MODEs as k_csr_spmv.
-//
-// H warps may share a slice (H = 2 in FP32): warp h takes the slots
-// h, h + H, ... of every row, and the partial sums meet in shared memory.
-template <int MODE, class T, int H>
-__global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __restrict__ off,
-                                                   const int* __restrict__ col,
-                                                   const T* __restrict__ val,
-                                                   const T* __restrict__ x,
-                                                   const T* __restrict__ b, T* __restrict__ y,
-                                                   ChebOut<T> ch) {
-    constexpr int U = sizeof(T) == 4 ? 8 : 4;
-    constexpr int SPB = 8 / H;  // slices per 256-thread block
-    static_assert(H == 1 || H == 2, "one or two warps per slice");
-    __shared__ T part[H > 1 ? SPB : 1][32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, h = warp % H;
-    const int64_t sl = (int64_t)blockIdx.x * SPB + warp / H;
-    const int64_t row = sl * 32 + lane;
-    const bool live = row < n_rows;
-    T a[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) a[u] = T(0);
-    if (live) {
-        const int e = off[sl + 1];
-        int p = off[sl] + 32 * h + lane;
-        constexpr int S = 32 * H;  // stride between this warp's slots
-        for (; p + S * (U - 1) < e; p += S * U) {
-            int c[U];
-            T v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                c[u] = col[p + S * u];
-                v[u] = val[p + S * u];
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) a[u] += v[u] * __ldg(x + c[u]);
-        }
-        for (; p < e; p += S) a[0] += val[p] * __ldg(x + col[p]);
-    }
-#pragma unroll
-    for (int w = U / 2; w > 0; w >>= 1)
-#pragma unroll
-        for (int u = 0; u < w; ++u) a[u] += a[u + w];
-    T acc = a[0];
-    if (H > 1) {
-        if (h == 1) part[warp / H][lane] = acc;
-        __syncthreads();
-        if (h == 1) return;
-        acc += part[warp / H][lane];
-    }
-    if (!live) return;
-    spmv_out<MODE, T>(row, acc, x, b, y, ch);
+// 16-bit columns relative to the slice base; the never-read slots of rows
+// past n_rows are set to 0
+__global__ void k_sell_col16(int64_t n_rows, int64_t n_sl, const int* __restrict__ off,
+                             const int* __restrict__ scol, const int* __restrict__ base,
+                             uint16_t* __restrict__ c16) {
+    const int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (sl >= n_sl) return;
+    const bool live = sl * 32 + lane < n_rows;
+    const int b = base[sl];
+    for (int q = off[sl] + lane; q < off[sl + 1]; q += 32) c16[q] = live ? (uint16_t)(scol[q] - b) : 0;
 }
 
 // slice widths: w[s] = 32 * (longest row of slice s); one warp per slice
@@ -202,7 +121,9 @@ void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStrea
     // algorithmic bytes: values and column indices of the nonzeros, the row
     // pointers (CSR only), x once, y (and b) once; SELL padding is not counted
     // (MODE 3 moves b, Dinv, d, and writes d and the new x: 5 values per row)
-    const double alg = (double)A.nnz * (sizeof(T) + 4.0) + (sell ? 0.0 : (double)(A.n_rows + 1) * 4.0) +
+    const bool c16 = sell && sizeof(T) == 4 && A.sell_col16.get();
+    const double alg = (double)A.nnz * (sizeof(T) + (c16 ? 2.0 : 4.0)) +
+                       (sell ? (c16 ? (double)((A.n_rows + 31) / 32) * 4.0 : 0.0) : (double)(A.n_rows + 1) * 4.0) +
                        (double)A.n_cols * sizeof(T) +
                        (double)A.n_rows * sizeof(T) * (MODE == 0 ? 1 : MODE == 3 ? 5 : 2);
     ProfScope prof(family ? family : (sizeof(T) == 8 ? "amg_spmv_setup" : "amg_spmv_setup_fp32"), s, alg);
@@ -214,8 +135,17 @@ void spmv_lanes(int lanes, const Csr& A, const T* x, const T* b, T* y, cudaStrea
         // one in FP64 (the FP64 pipe is the limit there)
         constexpr int H = sizeof(T) == 4 ? 2 : 1;
         const int64_t n_sl = (A.n_rows + 31) / 32;
-        k_sell_spmv<MODE, T, H><<<grid_for(n_sl, 8 / H), B, 0, s>>>(A.n_rows, A.sell_off.get(),
-                                                                   A.sell_col.get(), sv, x, b, y, ch);
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (A.sell_col16.get()) {
+                k_sell_spmv<MODE, T, H, true><<<grid_for(n_sl, 8 / H), B, 0, s>>>(
+                    A.n_rows, A.sell_off.get(), nullptr, sv, x, b, y, ch, A.sell_base.get(), A.sell_col16.get());
+                done = true;
+            }
+        }
+        if (!done)
+            k_sell_spmv<MODE, T, H><<<grid_for(n_sl, 8 / H), B, 0, s>>>(A.n_rows, A.sell_off.get(),
+                                                                       A.sell_col.get(), sv, x, b, y, ch);
         DPP_LAUNCH_CK();
         return;
     }
@@ -260,10 +190,23 @@ void build_sell(Csr& A, cudaStream_t s, HostScratch& hs) {
     const int64_t tot = exclusive_scan(off.get(), off.get(), n_sl + 1, s, hs);
     if (tot <= 0 || tot >= INT32_MAX) return;  // keep CSR only
     A.sell_col.alloc(tot);
-    if (fp32_only(A)) {  // a matrix of the FP32 hierarchy
+    if (fp32_only(A)) {  // a matrix of the FP32 hierarchy: FP32 values, 16-bit columns if they fit
         A.sell_val32.alloc(tot);
         k_sell_fill<float><<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val32.get(),
                                                            off.get(), A.sell_col.get(), A.sell_val32.get());
+        DPP_LAUNCH_CK();
+        DBuf<int> base(n_sl), wide(1);
+        DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
+        k_sell_span<<<grid_for(n_sl * 32, 256), 256, 0, s>>>(n, n_sl, off.get(), A.sell_col.get(), base.get(),
+                                                            wide.get());
+        DPP_LAUNCH_CK();
+        if (read_scalar(wide.get(), s, hs) == 0) {
+            A.sell_col16.alloc(tot);
+            k_sell_col16<<<grid_for(n_sl * 32, 256), 256, 0, s>>>(n, n_sl, off.get(), A.sell_col.get(),
+                                                                 base.get(), A.sell_col16.get());
+            DPP_LAUNCH_CK();
+            A.sell_base = std::move(base);
+        }
     } else {
         A.sell_val.alloc(tot);
         k_sell_fill<double><<<grid_for(n, 256), 256, 0, s>>>(n, A.row_ptr.get(), A.col.get(), A.val.get(),

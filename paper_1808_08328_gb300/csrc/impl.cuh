@@ -31,6 +31,11 @@ struct Csr {
     DBuf<int> sell_col;
     DBuf<double> sell_val;
     DBuf<float> sell_val32;
+    // Optional 16-bit columns of the SELL-32 copy (FP32 hierarchy): column =
+    // sell_base[slice] + sell_col16[slot], built when every slice's columns
+    // span less than 65536.
+    DBuf<int> sell_base;
+    DBuf<uint16_t> sell_col16;
     bool has_sell() const { return sell_off.get() != nullptr; }
 };
 
