@@ -142,6 +142,11 @@ typedef struct {
                                   nodes and of the mean instance's); the choice is cached for
                                   the process and in the DPP_TUNE_CACHE file if one is named.
                                   0: the schedule given (default). */
+    int32_t smooth_filter;     /* prolongator smoothing: 0 = P = (I - w D^-1 A) P0 with the level
+                                  matrix A; 1 = with the filtered matrix A^F of Vanek, Mandel and
+                                  Brezina (strong entries of A by strength_theta, the weak ones
+                                  added into the diagonal), w = 4 / (3 lambda_max(D_F^-1 A^F)):
+                                  sparser P and Galerkin products. */
 } dpp_pc_opts;
 
 /* Krylov options. */

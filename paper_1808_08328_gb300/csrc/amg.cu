@@ -426,6 +426,58 @@ __global__ void k_agg_pass2(int64_t n, const int* __restrict__ srp, const int* _
     if (a < 0) atomicOr(status, kDevOverflow);
 }
 
+// Filtered matrix A^F of the prolongator smoother (Vanek, Mandel & Brezina,
+// Computing 56, 1996): row i keeps its diagonal and its strong entries (the
+// same test as the strength graph), and the weak off-diagonal entries are
+// added into the diagonal, a^F_ii = a_ii - sum_weak a_ij (kept as a_ii if that
+// is not positive). frp[i] = strong entries before row i + i (one diagonal per
+// row). One warp per row; entries keep A's column order, and the weak sum is
+// a fixed shuffle tree, so A^F is deterministic.
+template <class V>
+__global__ void k_filter_rows(int64_t n, const int* __restrict__ rp, const int* __restrict__ col,
+                              const V* __restrict__ val, const V* __restrict__ dabs, V theta2,
+                              const int* __restrict__ frp, int* __restrict__ fcol, V* __restrict__ fval) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const V di = dabs[i];
+    const int p1 = rp[i + 1];
+    int q = frp[i];
+    int dpos = -1;
+    V weak = V(0), aii = V(0);
+    for (int p0 = rp[i]; p0 < p1; p0 += 32) {
+        const int p = p0 + lane;
+        const int j = p < p1 ? col[p] : -1;
+        const V v = p < p1 ? val[p] : V(0);
+        const bool diag = p < p1 && j == i;
+        const bool st = p < p1 && is_strong(i, j, v, di, dabs, theta2);
+        const bool keep = diag || st;
+        if (p < p1 && !keep) weak += v;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        const int at = q + __popc(m & ((1u << lane) - 1u));
+        if (keep) {
+            fcol[at] = j;
+            fval[at] = v;
+        }
+        if (diag) {
+            dpos = at;
+            aii = v;
+        }
+        q += __popc(m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) weak += __shfl_xor_sync(0xffffffffu, weak, o);
+    if (dpos >= 0) {
+        const V lumped = aii - weak;
+        fval[dpos] = lumped > V(0) ? lumped : aii;
+    }
+}
+
+__global__ void k_filter_ptr(int64_t n, const int* __restrict__ srp, int* __restrict__ frp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) frp[i] = srp[i] + (int)i;
+}
+
 template <class V>
 __global__ void k_p0(int64_t n, const int* __restrict__ agg, int* __restrict__ rp,
                      int* __restrict__ col, V* __restrict__ val) {
@@ -927,14 +979,48 @@ void amg_setup_t(Amg& pc, const dpp_pc_opts& o, Csr&& A0, cudaStream_t s, HostSc
                                                  vbuf<V>(P0).get());
         DPP_LAUNCH_CK();
         Csr Pm;
-        {
-            ProfScope q(l == 0 ? "spgemm_AP0_L0" : "spgemm_AP0_Lc", s, 0);
-            spgemm(view(L.A), view(P0), Pm, true, s, hs);
+        if (o.smooth_filter) {
+            // P = (I - omega D_F^-1 A^F) P0 with the filtered A^F, omega = 4 / (3 lambda_max(D_F^-1 A^F))
+            Csr AF;
+            AF.n_rows = AF.n_cols = n;
+            AF.nnz = S.nnz + n;
+            AF.row_ptr.alloc(n + 1);
+            AF.col.alloc(std::max<int64_t>(AF.nnz, 1));
+            vbuf<V>(AF).alloc(std::max<int64_t>(AF.nnz, 1));
+            k_filter_ptr<<<grid_for(n + 1, B), B, 0, s>>>(n, S.row_ptr.get(), AF.row_ptr.get());
+            DPP_LAUNCH_CK();
+            k_filter_rows<V><<<grid_for(n * 32, B), B, 0, s>>>(n, L.A.row_ptr.get(), L.A.col.get(),
+                                                              vbuf<V>(L.A).get(), dabs.get(), (V)theta2,
+                                                              AF.row_ptr.get(), AF.col.get(), vbuf<V>(AF).get());
+            DPP_LAUNCH_CK();
+            DBuf<V> dinv_f(n);
+            DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
+            k_diag_inv<V><<<grid_for(n, B), B, 0, s>>>(n, AF.row_ptr.get(), AF.col.get(), vbuf<V>(AF).get(),
+                                                       dinv_f.get(), nullptr, st.get());
+            DPP_LAUNCH_CK();
+            check_dev(st, s, hs, "a filtered level matrix has a non-positive diagonal entry");
+            double lmax_f;
+            {
+                ProfScope pr("setup_power", s, 0);
+                lmax_f = power_lmax<V>(AF, dinv_f.get(), pick_lanes(AF), s, hs);
+            }
+            {
+                ProfScope q(l == 0 ? "spgemm_AP0_L0" : "spgemm_AP0_Lc", s, 0);
+                spgemm(view(AF), view(P0), Pm, true, s, hs);
+            }
+            k_smooth_p<V><<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), vbuf<V>(Pm).get(),
+                                                       agg.get(), dinv_f.get(), (V)(4.0 / (3.0 * lmax_f)));
+            DPP_LAUNCH_CK();
+        } else {
+            {
+                ProfScope q(l == 0 ? "spgemm_AP0_L0" : "spgemm_AP0_Lc", s, 0);
+                spgemm(view(L.A), view(P0), Pm, true, s, hs);
+            }
+            const double omega = 4.0 / (3.0 * L.lmax);
+            k_smooth_p<V><<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), vbuf<V>(Pm).get(),
+                                                       agg.get(), dinv.get(), (V)omega);
+            DPP_LAUNCH_CK();
         }
-        const double omega = 4.0 / (3.0 * L.lmax);
-        k_smooth_p<V><<<grid_for(n, B), B, 0, s>>>(n, Pm.row_ptr.get(), Pm.col.get(), vbuf<V>(Pm).get(),
-                                                   agg.get(), dinv.get(), (V)omega);
-        DPP_LAUNCH_CK();
         L.P = std::move(Pm);
         if (o.spmv_format != 1 && n >= sell_min_rows(o)) build_sell(L.P, s, hs);  // autotuner may pick it
         transpose(L.P, L.R, s, hs);

@@ -116,9 +116,10 @@ def test_selfp_schur_wide_rows_match_definition(DPPSystem):
     s.close()
 
 
-def test_amg_levels_are_galerkin_products(DPPSystem):
+@pytest.mark.parametrize("smooth_filter", [0, 1], ids=["A", "filtered"])
+def test_amg_levels_are_galerkin_products(DPPSystem, smooth_filter):
     P = inputs.heterogeneous_problem(2, 40, seed=6)
-    s = DPPSystem.from_problem(P).setup_pc(coarse_max_rows=64)
+    s = DPPSystem.from_problem(P).setup_pc(coarse_max_rows=64, smooth_filter=smooth_filter)
     nlev = s.level(0)[0]["levels"]
     assert nlev >= 2
     for l in range(nlev - 1):
@@ -279,3 +280,21 @@ def test_error_paths(DPPSystem):
     x, info = s.solve(check=False, max_iters=1, restart=1)
     assert info["status"] == B.DPP_ERR_NOT_CONVERGED and info["iterations"] == 1
     s.close()
+
+
+def test_filtered_smoothing_keeps_only_strong_couplings(DPPSystem):
+    # smooth_filter = 1 smooths P0 with A^F (the strong entries of A and the
+    # diagonal): every nonzero of P is then within one strong edge of its
+    # aggregate, so level 0's P is sparser than with the full A, and each row
+    # of P still holds its own aggregate's column.
+    P = inputs.heterogeneous_problem(3, 10, seed=4, beta=1.0)
+    nnz = {}
+    for f in (0, 1):
+        s = DPPSystem.from_problem(P).setup_pc(smooth_filter=f)
+        sz, (rp, col, val), (prp, pcol, pval) = s.level(0)
+        nnz[f] = sz["p_nnz"]
+        Pm = csr_from_export(prp, pcol, pval, (sz["rows"], sz["p_cols"]))
+        # the largest entry of every row of P is its aggregate's (1 - w ...), and positive
+        assert (Pm.max(axis=1).toarray() > 0).all()
+        s.close()
+    assert nnz[1] < 0.6 * nnz[0], nnz
