@@ -135,9 +135,10 @@ typedef struct {
                                   the paper's block Jacobi / ILU(0) sub-solver (Sections 4.1,
                                   4.2); level-scheduled, one launch per dependency level. */
     int32_t schedule_tuning;   /* dpp_solve_batched only. 1: the preconditioner schedule (AMG
-                                  Chebyshev degree, cheb_ratio, mass Chebyshev degree) is chosen
+                                  Chebyshev degrees, cheb_ratio, mass Chebyshev degree) is chosen
                                   by timing candidate batched solves on the hierarchy already
-                                  built (coordinate search over {1,2,3}, {10,20,30}, {1,2,3}),
+                                  built (coordinate search: AMG degree {1,2,3}, coarse-level
+                                  degree {1,2,3}, ratio {10,20,30}, mass degree {1,2,3}),
                                   once per size class (dimension, precision, log2 of the union's
                                   nodes and of the mean instance's); the choice is cached for
                                   the process and in the DPP_TUNE_CACHE file if one is named.
@@ -147,6 +148,8 @@ typedef struct {
                                   Brezina (strong entries of A by strength_theta, the weak ones
                                   added into the diagonal), w = 4 / (3 lambda_max(D_F^-1 A^F)):
                                   sparser P and Galerkin products. */
+    int32_t cheb_degree_coarse; /* Chebyshev degree of the AMG smoother on the levels below the
+                                  finest; 0 (default) = cheb_degree_amg on every level */
 } dpp_pc_opts;
 
 /* Krylov options. */

@@ -50,7 +50,7 @@ class dpp_pc_opts(C.Structure):
         ("use_lumped_diag", C.c_int32), ("precision", C.c_int32),
         ("sell_min_rows", C.c_int32), ("spmv_format", C.c_int32),
         ("composition", C.c_int32), ("mass_solver", C.c_int32), ("schedule_tuning", C.c_int32),
-        ("smooth_filter", C.c_int32),
+        ("smooth_filter", C.c_int32), ("cheb_degree_coarse", C.c_int32),
     ]
 
 

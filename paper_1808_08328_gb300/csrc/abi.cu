@@ -223,6 +223,7 @@ void dpp_pc_opts_default(dpp_pc_opts* o) {
     o->mass_solver = 0;
     o->schedule_tuning = 0;
     o->smooth_filter = 0;
+    o->cheb_degree_coarse = 0;
 }
 
 void dpp_solve_opts_default(dpp_solve_opts* o) {
@@ -316,6 +317,7 @@ dpp_status dpp_setup_pc(dpp_problem prob, const dpp_pc_opts* opts, dpp_stream_t 
         require(o.mass_solver == 0 || o.mass_solver == 1,
                 "mass_solver in {0 (Chebyshev-Jacobi), 1 (ILU(0))}");
         require(o.smooth_filter == 0 || o.smooth_filter == 1, "smooth_filter in {0,1}");
+        require(o.cheb_degree_coarse >= 0 && o.cheb_degree_coarse <= 16, "cheb_degree_coarse in [0,16]");
         require(o.schedule_tuning == 0 || o.schedule_tuning == 1, "schedule_tuning in {0,1}");
         cudaStream_t s = (cudaStream_t)stream;
         auto* h = new dpp_pc_s();
@@ -487,6 +489,7 @@ dpp_status dpp_solve_batched(int32_t n_inst, const dpp_problem_desc* descs,
         pc.owner = &prob;
         require(po.schedule_tuning == 0 || po.schedule_tuning == 1, "schedule_tuning in {0,1}");
         require(po.smooth_filter == 0 || po.smooth_filter == 1, "smooth_filter in {0,1}");
+        require(po.cheb_degree_coarse >= 0 && po.cheb_degree_coarse <= 16, "cheb_degree_coarse in [0,16]");
         pc_setup(pc.impl, prob.impl, s);
         if (po.schedule_tuning) tune_batched_schedule(prob.impl, pc.impl, o, s, prob.impl.hs);
         const double ms_setup = tb.stop();

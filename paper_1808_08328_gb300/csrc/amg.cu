@@ -1064,10 +1064,16 @@ template <class T> T* lv(DBuf<double>& d, DBuf<float>& f);
 template <> double* lv<double>(DBuf<double>& d, DBuf<float>&) { return d.get(); }
 template <> float* lv<float>(DBuf<double>&, DBuf<float>& f) { return f.get(); }
 
+// Chebyshev degree of level l: cheb_degree_amg, or on the coarser levels
+// cheb_degree_coarse when that is set
+inline int cheb_degree(const dpp_pc_opts& o, size_t l) {
+    return std::max(1, (l > 0 && o.cheb_degree_coarse > 0) ? o.cheb_degree_coarse : o.cheb_degree_amg);
+}
+
 template <class T>
-void cheb_smooth(const dpp_pc_opts& o, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s,
+void cheb_smooth(const dpp_pc_opts& o, size_t l, Level& L, const T* b, T* x, bool zero_init, cudaStream_t s,
                  const char* fam = nullptr) {
-    const int deg = std::max(1, o.cheb_degree_amg);
+    const int deg = cheb_degree(o, l);
     const double hi = 1.1 * L.lmax, lo = L.lmax / o.cheb_ratio;
     const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
     const int64_t n = L.A.n_rows;
@@ -1126,12 +1132,12 @@ void vcycle_level(Amg& pc, const dpp_pc_opts& o, size_t l, const T* b, T* x, cud
     const char* fam = (l == 0) ? (f64 ? "amg_spmv_L0" : "amg_spmv_L0_fp32")
                                : (f64 ? "amg_spmv_Lc" : "amg_spmv_Lc_fp32");
     const char* fam_pr = f64 ? "amg_spmv_PR" : "amg_spmv_PR_fp32";
-    cheb_smooth<T>(o, L, b, x, true, s, fam);
+    cheb_smooth<T>(o, l, L, b, x, true, s, fam);
     spmv_lanes<1, T>(L.lanes, L.A, x, b, r, s, fam);
     spmv_lanes<0, T>(L.lanes_R, L.R, r, nullptr, cb, s, fam_pr);
     vcycle_level<T>(pc, o, l + 1, cb, cx, s);
     spmv_lanes<2, T>(L.lanes_P, L.P, cx, nullptr, x, s, fam_pr);
-    cheb_smooth<T>(o, L, b, x, false, s, fam);
+    cheb_smooth<T>(o, l, L, b, x, false, s, fam);
 }
 
 void to_f32(const DBuf<double>& in, DBuf<float>& out, cudaStream_t s) {

@@ -803,13 +803,13 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
 }
 
 // ------------------------------------------------------------------ schedule autotuner
-// The preconditioner schedule of the batched solve: the AMG Chebyshev degree,
-// the AMG Chebyshev interval ratio and the mass Chebyshev degree. None of
-// them changes the setup (aggregates, Galerkin products, lambda_max), so the
-// candidates are timed as full batched solves on the one hierarchy already
-// built, by a coordinate search from the given schedule: the AMG degree in
-// {1, 2, 3}, then the ratio in {10, 20, 30}, then the mass degree in
-// {1, 2, 3}. A candidate that leaves an instance unconverged is dropped. The
+// The preconditioner schedule of the batched solve: the AMG Chebyshev degree
+// (finest level, then the coarser levels), the AMG Chebyshev interval ratio
+// and the mass Chebyshev degree. None of them changes the setup (aggregates,
+// Galerkin products, lambda_max), so the candidates are timed as full batched
+// solves on the one hierarchy already built, by a coordinate search from the
+// given schedule: the AMG degree in {1, 2, 3}, the coarse-level degree in
+// {1, 2, 3}, the ratio in {10, 20, 30}, then the mass degree in {1, 2, 3}. A candidate that leaves an instance unconverged is dropped. The
 // choice is cached for the process per size class (dimension, precision,
 // log2 of the union's nodes, log2 of the mean nodes per instance); if
 // DPP_TUNE_CACHE names a file, choices are read from it and new ones appended.
@@ -824,6 +824,7 @@ struct SchedKey {
 struct Sched {
     int amg, mass;
     double ratio;
+    int coarse;  // 0: the AMG degree on every level
 };
 std::mutex g_sched_mu;
 std::map<SchedKey, Sched> g_sched;
@@ -847,11 +848,12 @@ void sched_load_locked() {
         SchedKey k;
         Sched v;
         if (std::sscanf(line,
-                        "{\"schedule\": 1, \"dim\": %d, \"fp32\": %d, \"log2_nodes\": %d, "
-                        "\"log2_mean\": %d, \"amg\": %d, \"mass\": %d, \"ratio\": %lf}",
-                        &k.dim, &k.fp32, &k.log2_nodes, &k.log2_mean, &v.amg, &v.mass,
-                        &v.ratio) == 7 &&
-            v.amg >= 1 && v.amg <= 16 && v.mass >= 1 && v.mass <= 16 && v.ratio > 1)
+                        "{\"schedule\": 2, \"dim\": %d, \"fp32\": %d, \"log2_nodes\": %d, "
+                        "\"log2_mean\": %d, \"amg\": %d, \"coarse\": %d, \"mass\": %d, \"ratio\": %lf}",
+                        &k.dim, &k.fp32, &k.log2_nodes, &k.log2_mean, &v.amg, &v.coarse, &v.mass,
+                        &v.ratio) == 8 &&
+            v.amg >= 1 && v.amg <= 16 && v.coarse >= 0 && v.coarse <= 16 && v.mass >= 1 &&
+            v.mass <= 16 && v.ratio > 1)
             g_sched[k] = v;
     }
     std::fclose(f);
@@ -864,9 +866,9 @@ void sched_store_locked(const SchedKey& k, const Sched& v) {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
-                 "{\"schedule\": 1, \"dim\": %d, \"fp32\": %d, \"log2_nodes\": %d, "
-                 "\"log2_mean\": %d, \"amg\": %d, \"mass\": %d, \"ratio\": %g}\n",
-                 k.dim, k.fp32, k.log2_nodes, k.log2_mean, v.amg, v.mass, v.ratio);
+                 "{\"schedule\": 2, \"dim\": %d, \"fp32\": %d, \"log2_nodes\": %d, "
+                 "\"log2_mean\": %d, \"amg\": %d, \"coarse\": %d, \"mass\": %d, \"ratio\": %g}\n",
+                 k.dim, k.fp32, k.log2_nodes, k.log2_mean, v.amg, v.coarse, v.mass, v.ratio);
     std::fclose(f);
 }
 }  // namespace
@@ -882,6 +884,7 @@ void tune_batched_schedule(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opt
         auto it = g_sched.find(key);
         if (it != g_sched.end()) {
             pc.opts.cheb_degree_amg = it->second.amg;
+            pc.opts.cheb_degree_coarse = it->second.coarse;
             pc.opts.cheb_degree_mass = it->second.mass;
             pc.opts.cheb_ratio = it->second.ratio;
             return;
@@ -897,12 +900,13 @@ void tune_batched_schedule(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opt
         cudaEvent_t a, b;
         ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } eg{e0, e1};
-    std::map<std::tuple<int, int, double>, float> seen;
+    std::map<std::tuple<int, int, int, double>, float> seen;
     auto trial = [&](const Sched& c) -> float {
-        auto k = std::make_tuple(c.amg, c.mass, c.ratio);
+        auto k = std::make_tuple(c.amg, c.coarse ? c.coarse : c.amg, c.mass, c.ratio);
         auto f = seen.find(k);
         if (f != seen.end()) return f->second;
         pc.opts.cheb_degree_amg = c.amg;
+        pc.opts.cheb_degree_coarse = c.coarse;
         pc.opts.cheb_degree_mass = c.mass;
         pc.opts.cheb_ratio = c.ratio;
         std::vector<int> st, it;
@@ -920,11 +924,18 @@ void tune_batched_schedule(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opt
         seen[k] = ms;
         return ms;
     };
-    Sched best{pc.opts.cheb_degree_amg, pc.opts.cheb_degree_mass, pc.opts.cheb_ratio};
+    Sched best{pc.opts.cheb_degree_amg, pc.opts.cheb_degree_mass, pc.opts.cheb_ratio,
+               pc.opts.cheb_degree_coarse};
     float best_ms = trial(best);
     for (int a : {1, 2, 3}) {
         Sched c = best;
         c.amg = a;
+        const float ms = trial(c);
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    for (int a : {1, 2, 3}) {
+        Sched c = best;
+        c.coarse = a;
         const float ms = trial(c);
         if (ms < best_ms) { best_ms = ms; best = c; }
     }
@@ -941,6 +952,7 @@ void tune_batched_schedule(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opt
         if (ms < best_ms) { best_ms = ms; best = c; }
     }
     pc.opts.cheb_degree_amg = best.amg;
+    pc.opts.cheb_degree_coarse = best.coarse;
     pc.opts.cheb_degree_mass = best.mass;
     pc.opts.cheb_ratio = best.ratio;
     std::lock_guard<std::mutex> lk(g_sched_mu);

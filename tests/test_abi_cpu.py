@@ -55,7 +55,7 @@ def test_defaults_and_status_strings(lib):
 def test_struct_layouts_match_header(lib):
     # sizes fixed by the C declarations (x86-64 and aarch64 share this ABI)
     assert C.sizeof(lib.dpp_problem_desc) == 4 + 4 + 3 * 8 + 5 * 8 + 2 * 8 + 3 * 8 + 2 * 8 + 8
-    assert C.sizeof(lib.dpp_pc_opts) == 4 * 4 + 2 * 8 + 8 * 4
+    assert C.sizeof(lib.dpp_pc_opts) == 4 * 4 + 2 * 8 + 9 * 4 + 4   # padded to 8 bytes
     assert C.sizeof(lib.dpp_solve_opts) == 8 + 5 * 4 + 4 + 8 + 8 + 8 + 4 + 4   # padded to 8
     assert C.sizeof(lib.dpp_solve_info) == 4 * 4 + 4 * 8
 

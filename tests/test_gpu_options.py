@@ -11,6 +11,7 @@ relative L2 per field at a true relative residual of 1e-10. Covered:
   * max_levels 1: the coarsest level is S_p itself, blocks of 343 and 625
     rows, inverted by the cooperative Gauss-Jordan (one grid barrier per pivot);
   * smooth_filter = 1 (prolongator smoothed with the filtered matrix A^F);
+  * cheb_degree_coarse 1 and 3 (a separate smoother degree below the finest level);
   * inner_rtol 1e-2 and 1e-6 of the mixed mode; restart 5;
   * x0_zero = 0: from a perturbed oracle solution, and from the oracle
     solution itself (converged before the first iteration).
@@ -53,7 +54,8 @@ def _check(ref, x, info):
 PC_OPTS = [dict(use_lumped_diag=1), dict(cheb_degree_amg=1), dict(cheb_degree_amg=3),
            dict(cheb_degree_mass=1), dict(cheb_degree_mass=3), dict(cheb_ratio=20.0),
            dict(strength_theta=0.0), dict(strength_theta=0.08), dict(max_levels=2),
-           dict(max_levels=1), dict(coarse_max_rows=64), dict(smooth_filter=1)]
+           dict(max_levels=1), dict(coarse_max_rows=64), dict(smooth_filter=1),
+           dict(cheb_degree_coarse=1), dict(cheb_degree_coarse=3)]
 
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
