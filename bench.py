@@ -270,6 +270,42 @@ def small_solve_mode(dev, reps=10):
                            "assemble+setup_pc+solve per call"}
 
 
+# The paper's strong-scaling tables of CG-VMS P1 (tables "Strong_CGVMS_hsize" and
+# "Strong_CGVMS_DoF"): 3D MMS (k1 = 1, k2 = 0.1, mu = beta = 1) on the unit cube, assembly and
+# solver wall time on one Xeon E5-2698v3 core, solver tolerance not stated. Context only.
+PAPER_MMS = {16: {"dofs": 39305, "field": {"total_s": 3.39, "solver_s": 1.02, "ksp": 12},
+                  "scale": {"total_s": 3.25, "solver_s": 0.862, "ksp": 12}},
+             28: {"dofs": 195112, "field": {"total_s": 17.3, "solver_s": 5.01, "ksp": 13},
+                  "scale": {"total_s": 16.6, "solver_s": 4.14, "ksp": 13}}}
+
+
+def paper_mms_mode(dev, reps=3):
+    """The paper's own workloads: 3D MMS at h = 1/16 and 1/28, both compositions, FP64,
+    assemble + setup + solve to 1e-10 per call through DPPSystem (inputs copied from
+    host memory in each call)."""
+    import inputs
+    from paper_1808_08328_gb300.system import DPPSystem
+    out = {}
+    for n, ref in PAPER_MMS.items():
+        P = inputs.mms_problem(3, n)
+        for comp, name in ((0, "field"), (1, "scale")):
+            def once():
+                s = DPPSystem.from_problem(P, device=dev).setup_pc(composition=comp)
+                _, info = s.solve(rtol=1e-10)
+                s.close()
+                return info
+            ms, info = _timed(dev, once, reps)
+            out[f"h1_{n}_{name}"] = {
+                "dofs": P.n_dofs, "ms_total": ms, "dof_per_s": P.n_dofs / (ms * 1e-3),
+                "iterations": info["iterations"], "rel_residual": info["rel_residual"],
+                "ms_assemble": info["ms_assemble"], "ms_setup": info["ms_setup"],
+                "ms_solve": info["ms_solve"],
+                "paper_1_xeon_core": {"dofs": ref["dofs"], "total_s": ref[name]["total_s"],
+                                      "solver_s": ref[name]["solver_s"], "ksp": ref[name]["ksp"],
+                                      "tolerance": "not stated"}}
+    return out
+
+
 def adjoint_mode(dev, reps=3):
     """Gradients of J = sum over nodes (p1 - p1_obs)^2 with respect to the per-cell
     log k1, log k2 and beta on the 3D 32^3 Kuhn mesh (287,496 DoF): one forward solve
@@ -545,6 +581,7 @@ def bench_gb300(args):
         del bt
         modes["small_2d32_fp64"] = small_solve_mode(dev)
         modes["adjoint_3d32"] = adjoint_mode(dev)
+        modes["paper_mms_3d"] = paper_mms_mode(dev)
 
     if rank != 0:
         if dist:
