@@ -772,6 +772,8 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
     };
     int active_now = read_scalar(n_active.get(), s, hs);
     if (active_now > 0) {
+        // host time of building the graph (the device is idle meanwhile)
+        ProfScope pg("batched_graph_build", s, 0);
         DPP_CK(cudaGraphCreate(&G.g, 0));
         cudaGraphConditionalHandle h_cycle, h_iter;
         DPP_CK(cudaGraphConditionalHandleCreate(&h_cycle, G.g, 1, cudaGraphCondAssignDefault));
@@ -783,6 +785,7 @@ void fgmres_batched(const ProblemImpl& P, PcImpl& pc, const dpp_solve_opts& o, d
         capture_into(body_iter, nullptr, 0, [&]() { iteration(h_iter); });
         capture_into(body_cycle, &w_iter, 1, [&]() { finish(h_cycle, h_iter); });
         DPP_CK(cudaGraphInstantiate(&G.e, G.g, 0));
+        pg.stop();
         DPP_CK(cudaGraphLaunch(G.e, s));
         size_t n_iter_nodes = 0, n_cycle_nodes = 0;
         DPP_CK(cudaGraphGetNodes(body_iter, nullptr, &n_iter_nodes));
