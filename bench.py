@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DoF/s to rel. residual 1e-10"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # derived FP64 peak of a GB300 (see roofline)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # derived FP32 (non-tensor) peak
 WORKLOADS = {
     # name: (dim, n, seed, beta, description, precision)
     "3d64_lognormal_fp64": (3, 64, 0, 1.0, "3D unit cube 64^3 x 6 Kuhn tets, log k1~N(0,1), "
@@ -412,7 +413,7 @@ def bench_gb300(args):
     families = ("apply_K", "amg_spmv_L0", "amg_spmv_Lc", "amg_spmv_PR", "mass_cheb",
                 "apply_K_fp32", "amg_spmv_L0_fp32", "amg_spmv_Lc_fp32", "amg_spmv_PR_fp32",
                 "mass_cheb_fp32", "amg_spmv_setup", "amg_spmv_setup_fp32", "spgemm_onepass",
-                "apply_K_mf", "apply_K_mf_fp32", "mass_ilu", "mass_ilu_fp32")
+                "spgemm_onepass_fp32", "apply_K_mf", "apply_K_mf_fp32", "mass_ilu", "mass_ilu_fp32")
     phase_names = ("assemble", "setup_selfp", "setup_amg", "setup_power", "setup_aggregate",
                    "setup_strength", "setup_mis", "setup_prolong_rap", "setup_coarse_inverse",
                    "setup_tune", "spgemm_numeric", "spgemm_pattern", "spgemm_count",
@@ -426,9 +427,11 @@ def bench_gb300(args):
     torch.cuda.synchronize(dev)
     fam = {f: B.dpp_profile_read(f) for f in families}
     fam = {k: v for k, v in fam.items() if v["launches"]}
-    # FP64 work of the setup's sparse product per step (products counted on the
-    # device in this untimed step only; the step is deterministic)
-    spg_flop = B.dpp_profile_read("spgemm_onepass_flop")
+    # work of the setup's sparse product per step (products counted on the device
+    # in this untimed step only; the step is deterministic): FP64, or FP32 for the
+    # hierarchy of the mixed mode
+    spg_flop = {"spgemm_onepass": B.dpp_profile_read("spgemm_onepass_flop"),
+                "spgemm_onepass_fp32": B.dpp_profile_read("spgemm_onepass_flop_fp32")}
     phases = {f: B.dpp_profile_read(f)["ms"] for f in phase_names}
     B.dpp_profile_enable(False)
     dom = max(fam, key=lambda f: fam[f]["ms"])
@@ -599,29 +602,35 @@ def bench_gb300(args):
                 "avg_launch_us": 1000.0 * d["ms"] / max(d["launches"], 1),
                 "candidates_ms_per_step": {f: round(v["ms"], 3) for f, v in
                                            sorted(fam.items(), key=lambda kv: -kv[1]["ms"])[:4]}}
-    # The setup's sparse product is bound by arithmetic, not DRAM. Its own
-    # roofline: its FP64 multiply-adds (2 flops per product formed, counted on
-    # the device) against the FP64 peak derived from the unit counts and the
-    # clock: 152 SMs x 2 FP64 FMA per cycle x 2 flops x 2.07 GHz = 1.26 TFLOP/s.
+    # The setup's sparse product is bound on chip, not by DRAM. Its own
+    # roofline: its multiply-adds (2 flops per product formed, counted on the
+    # device) against the arithmetic peak derived from the unit counts and the
+    # clock: FP64 152 SMs x 2 FMA per cycle x 2 flops x 2.07 GHz = 1.26 TFLOP/s;
+    # FP32 (mixed mode) 152 SMs x 128 FMA per cycle x 2 flops x 2.07 GHz.
     spg = None
-    if spg_flop["launches"] and "spgemm_onepass" in fam:
+    prod = next((f for f in ("spgemm_onepass", "spgemm_onepass_fp32") if f in fam), None)
+    if prod and spg_flop[prod]["launches"]:
         # live time of the family: the timed region if it was the one timed there,
         # else the untimed profiled step
-        if dom == "spgemm_onepass":
+        if dom == prod:
             live_ms, live_l = d["ms"] / args.steps, d["launches"] / args.steps
         else:
-            live_ms, live_l = fam["spgemm_onepass"]["ms"], fam["spgemm_onepass"]["launches"]
-        fl = {"alg_bytes": spg_flop["alg_bytes"], "ms": live_ms, "launches": live_l}
+            live_ms, live_l = fam[prod]["ms"], fam[prod]["launches"]
+        fl = {"alg_bytes": spg_flop[prod]["alg_bytes"], "ms": live_ms, "launches": live_l}
         tf = fl["alg_bytes"] / (fl["ms"] * 1e-3) / 1e12
-        spg = {"bound": "alu", "kernel": "spgemm_onepass", "achieved": tf, "peak": FP64_PEAK_TFLOPS,
-               "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-               "peak_kind": "derived: 152 SMs x 2 FP64 FMA/cycle x 2 flop x 2.07 GHz",
+        f32 = prod.endswith("_fp32")
+        peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+        spg = {"bound": "alu", "kernel": prod, "achieved": tf, "peak": peak,
+               "unit": "TFLOP/s", "frac": tf / peak,
+               "peak_kind": ("derived: 152 SMs x 128 FP32 FMA/cycle x 2 flop x 2.07 GHz" if f32 else
+                             "derived: 152 SMs x 2 FP64 FMA/cycle x 2 flop x 2.07 GHz"),
                "flop_per_launch": fl["alg_bytes"] / fl["launches"],
                "avg_launch_us": 1000.0 * fl["ms"] / fl["launches"]}
     if dom.startswith("spgemm") and spg:
         spg.update(traffic=None, hbm_view={"achieved_gbs": achieved, "frac": achieved / peaks["hbm_gbs"]},
                    candidates_ms_per_step=roofline["candidates_ms_per_step"],
-                   note="bound on chip (FP64 pipe, shared memory); DRAM is not its limit")
+                   note="bound on chip (shared-memory hash probes, and the FP64 pipe in FP64); "
+                        "DRAM is not its limit")
         roofline = spg
     elif spg:
         roofline["setup_kernel"] = spg
