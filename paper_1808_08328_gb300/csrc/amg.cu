@@ -28,6 +28,7 @@
 // 2003).
 #include "amg.cuh"
 #include "level_spmv.cuh"
+#include "csr_spmv.cuh"
 
 #include <climits>
 #include <cmath>

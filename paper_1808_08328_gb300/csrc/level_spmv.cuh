@@ -1,7 +1,7 @@
-// Level SpMV kernels of the AMG hierarchy: CSR with L lanes per row and
-// SELL-32 (one thread per row, one or two warps per slice), each with the
-// Chebyshev step of the smoother fused into its residual (MODE 3). Included
-// by amg.cu only.
+// SELL-32 SpMV of the AMG hierarchy's large levels (one thread per row, one or
+// two warps per slice), with the Chebyshev step of the smoother fused into its
+// residual (MODE 3), and the output modes it shares with the CSR kernel
+// (csr_spmv.cuh). Included by amg.cu only.
 #pragma once
 
 #include <cstdint>
@@ -9,7 +9,7 @@
 namespace dpp {
 namespace {
 
-// ------------------------------------------------------------------ CSR SpMV
+// ------------------------------------------------------------------ output modes
 // Chebyshev step fused into the residual SpMV (MODE 3): with r = b - A x,
 // d = c1 d + c2 Dinv r and xo = x + d, written to xo (not x, which other rows
 // still read). c1 = 0 does not read d.
@@ -33,41 +33,6 @@ __device__ __forceinline__ void spmv_out(int64_t row, T acc, const T* __restrict
         ch.d[row] = dn;
         ch.xo[row] = x[row] + dn;
     }
-}
-
-// MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x; 3: Chebyshev step (above).
-// T: values, vectors and arithmetic.
-// L lanes share a row; each lane walks its entries four at a time with four
-// independent partial sums, so that several gathers are in flight.
-template <int L, int MODE, class T>
-__global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __restrict__ rp,
-                                                  const int* __restrict__ col,
-                                                  const T* __restrict__ val,
-                                                  const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y,
-                                                  ChebOut<T> ch) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = t / L;
-    const int lane = (int)(t % L);
-    const bool active = row < n_rows;  // inactive lanes still join the shuffles
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    if (active) {
-        int p = rp[row] + lane;
-        const int e = rp[row + 1];
-        for (; p + 3 * L < e; p += 4 * L) {
-            const int c0 = col[p], c1 = col[p + L], c2 = col[p + 2 * L], c3 = col[p + 3 * L];
-            const T v0 = val[p], v1 = val[p + L], v2 = val[p + 2 * L], v3 = val[p + 3 * L];
-            a0 += v0 * __ldg(x + c0);
-            a1 += v1 * __ldg(x + c1);
-            a2 += v2 * __ldg(x + c2);
-            a3 += v3 * __ldg(x + c3);
-        }
-        for (; p < e; p += L) a0 += val[p] * __ldg(x + col[p]);
-    }
-    T acc = (a0 + a1) + (a2 + a3);
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);
-    if (active && lane == 0) spmv_out<MODE, T>(row, acc, x, b, y, ch);
 }
 
 // ------------------------------------------------------------------ SELL-32 SpMV
