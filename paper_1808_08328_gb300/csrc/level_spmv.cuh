@@ -80,15 +80,27 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __
                 c[u] = column(p + S * u);
                 v[u] = val[p + S * u];
             }
+            T xv[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) a[u] += v[u] * __ldg(x + c[u]);
+            for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+            if constexpr (sizeof(T) == 8) {
+                // FP64: one accumulator, so no partial sums to add up per row (the
+                // FP64 pipe is a limit here); the U gathers are still in flight together
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[0] = fma(v[u], xv[u], a[0]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[u] += v[u] * xv[u];
+            }
         }
         for (; p < e; p += S) a[0] += val[p] * __ldg(x + column(p));
     }
+    if constexpr (sizeof(T) != 8) {
 #pragma unroll
-    for (int w = U / 2; w > 0; w >>= 1)
+        for (int w = U / 2; w > 0; w >>= 1)
 #pragma unroll
-        for (int u = 0; u < w; ++u) a[u] += a[u + w];
+            for (int u = 0; u < w; ++u) a[u] += a[u + w];
+    }
     T acc = a[0];
     if (H > 1) {
         if (h == 1) part[warp / H][lane] = acc;
