@@ -10,9 +10,9 @@ namespace {
 
 // MODE 0: y = A x; 1: y = b - A x; 2: y = y + A x; 3: Chebyshev step (above).
 // T: values, vectors and arithmetic.
-// L lanes share a row; each lane walks its entries U at a time with U
-// independent partial sums (4 in FP64, 8 in FP32), so that several gathers are
-// in flight.
+// L lanes share a row; each lane walks its entries U at a time (4 in FP64, 8
+// in FP32), so that several gathers are in flight; FP32 keeps U partial sums,
+// FP64 one accumulator (the FP64 pipe is a limit, and partial sums cost adds).
 template <int L, int MODE, class T>
 __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __restrict__ rp,
                                                   const int* __restrict__ col,
@@ -39,15 +39,25 @@ __global__ void __launch_bounds__(256) k_csr_spmv(int64_t n_rows, const int* __r
                 c[u] = col[p + u * L];
                 v[u] = val[p + u * L];
             }
+            T xv[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) a[u] += v[u] * __ldg(x + c[u]);
+            for (int u = 0; u < U; ++u) xv[u] = __ldg(x + c[u]);
+            if constexpr (sizeof(T) == 8) {  // FP64: one accumulator (no partial sums to add)
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[0] = fma(v[u], xv[u], a[0]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[u] += v[u] * xv[u];
+            }
         }
         for (; p < e; p += L) a[0] += val[p] * __ldg(x + col[p]);
     }
+    if constexpr (sizeof(T) != 8) {
 #pragma unroll
-    for (int w = U / 2; w > 0; w >>= 1)
+        for (int w = U / 2; w > 0; w >>= 1)
 #pragma unroll
-        for (int u = 0; u < w; ++u) a[u] += a[u + w];
+            for (int u = 0; u < w; ++u) a[u] += a[u + w];
+    }
     T acc = a[0];
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, L);

@@ -38,8 +38,9 @@ __device__ __forceinline__ void spmv_out(int64_t row, T acc, const T* __restrict
 // ------------------------------------------------------------------ SELL-32 SpMV
 // One thread per row; a warp owns a slice, so every column and value load of
 // the warp is one contiguous 128 B (int, float) or 256 B (double) transaction.
-// U partial sums keep U gathers in flight: 4 in FP64 (the FP64 pipe is the
-// other limit there), 8 in FP32. Same MODEs as k_csr_spmv.
+// U gathers are kept in flight: 4 in FP64 (the FP64 pipe is the other limit
+// there), 8 in FP32 with U partial sums; FP64 sums into one accumulator,
+// which saves the adds of the partial sums. Same MODEs as k_csr_spmv.
 //
 // H warps may share a slice (H = 2 in FP32): warp h takes the slots
 // h, h + H, ... of every row, and the partial sums meet in shared memory.
