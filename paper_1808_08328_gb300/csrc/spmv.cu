@@ -144,16 +144,21 @@ __global__ void __launch_bounds__(128) k_apply_K(int64_t n_rows, int64_t n_slice
         AT xb[NS];
         load_node_as<NS, XT>(x, cb, xb);
         const AT p1 = xb[DIM], p2 = xb[2 * DIM + 1];
-        AT cp1 = d1 * p1 + e * p2, cp2 = d2 * p2 + e * p1;
+        // every term is a multiply-add straight into its accumulator (22 per pair
+        // in 3D): in FP64 the pipe, not memory, bounds this kernel
+        acc[DIM] = fma(d1, p1, acc[DIM]);
+        acc[DIM] = fma(e, p2, acc[DIM]);
+        acc[2 * DIM + 1] = fma(d2, p2, acc[2 * DIM + 1]);
+        acc[2 * DIM + 1] = fma(e, p1, acc[2 * DIM + 1]);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            acc[k] += m1 * xb[k] + bu[k] * p1;
-            acc[DIM + 1 + k] += m2 * xb[DIM + 1 + k] + bu[k] * p2;
-            cp1 += cu[k] * xb[k];
-            cp2 += cu[k] * xb[DIM + 1 + k];
+            acc[k] = fma(m1, xb[k], acc[k]);
+            acc[k] = fma(bu[k], p1, acc[k]);
+            acc[DIM + 1 + k] = fma(m2, xb[DIM + 1 + k], acc[DIM + 1 + k]);
+            acc[DIM + 1 + k] = fma(bu[k], p2, acc[DIM + 1 + k]);
+            acc[DIM] = fma(cu[k], xb[k], acc[DIM]);
+            acc[2 * DIM + 1] = fma(cu[k], xb[DIM + 1 + k], acc[2 * DIM + 1]);
         }
-        acc[DIM] += cp1;
-        acc[2 * DIM + 1] += cp2;
     }
     if (H > 1) {
         if (h == 1)
