@@ -423,9 +423,11 @@ void mass_cheb_step(const ProblemImpl& P, const T* mdiag, const T* r, const T* x
     const double alg = first ? 3 * vecb : (double)P.n_pairs * (2.0 * sizeof(T) + 4.0) + 5 * vecb;
     ProfScope prof(sizeof(T) == 8 ? "mass_cheb" : "mass_cheb_fp32", s, alg);
     const int B = 128;
-    // two warps per slice in FP64 (see k_apply_K); in FP32 the per-row epilogue
-    // outweighs the short pair loop, and one warp per slice measured faster
-    constexpr int H = (sizeof(T) == 8) ? 2 : 1;
+    // one warp per slice: in FP32 the per-row epilogue outweighs the short pair
+    // loop, and in FP64 the FP64 pipe bounds the kernel, so the adds that join
+    // two warps' partial sums cost more than the extra loads in flight gain
+    // (3.56 against 3.65 ms per step at 64^3)
+    constexpr int H = 1;
     const int grid = grid_for(P.n_slices, 4 / H);
     const T* val = vals_of<T>(P);
     if (P.dim == 2)
