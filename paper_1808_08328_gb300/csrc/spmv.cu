@@ -203,9 +203,13 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
     const int64_t s = (int64_t)blockIdx.x * SPB + warp / H;
     const bool live = s < n_slices;
     const int64_t a = s * 32 + lane;
+    // acc starts at the row's right-hand side (warp 0 of the slice) and the
+    // products are subtracted, so that acc ends as the residual r - A x with
+    // one multiply-add per product and no separate subtraction
     T acc[NS];
 #pragma unroll
     for (int k = 0; k < NS; ++k) acc[k] = T(0);
+    if (!first && live && h == 0 && a < n_rows) load_node<NS>(r, a, acc);
     if (!first && live) {
         const int g0 = slice_ptr[s] + h, g1 = slice_ptr[s + 1];
         for (int g = g0; g < g1; g += H) {
@@ -217,8 +221,8 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
             load_node<NS>(xin, cb, xb);
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
-                acc[k] += m1 * xb[k];
-                acc[DIM + 1 + k] += m2 * xb[DIM + 1 + k];
+                acc[k] = fma(-m1, xb[k], acc[k]);
+                acc[DIM + 1 + k] = fma(-m2, xb[DIM + 1 + k], acc[DIM + 1 + k]);
             }
         }
     }
@@ -249,10 +253,11 @@ __global__ void __launch_bounds__(128) k_mass_cheb(int64_t n_rows, int64_t n_sli
     }
     load_node<NS>(d, a, dd);
     load_node<NS>(xin, a, xx);
+    const T s1 = c2 * i1, s2 = c2 * i2;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        dd[k] = c1 * dd[k] + c2 * i1 * (rr[k] - acc[k]);
-        dd[DIM + 1 + k] = c1 * dd[DIM + 1 + k] + c2 * i2 * (rr[DIM + 1 + k] - acc[DIM + 1 + k]);
+    for (int k = 0; k < DIM; ++k) {  // acc = r - A x (see above)
+        dd[k] = fma(s1, acc[k], c1 * dd[k]);
+        dd[DIM + 1 + k] = fma(s2, acc[DIM + 1 + k], c1 * dd[DIM + 1 + k]);
         xx[k] += dd[k];
         xx[DIM + 1 + k] += dd[DIM + 1 + k];
     }
