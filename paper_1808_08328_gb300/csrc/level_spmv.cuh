@@ -21,14 +21,16 @@ struct ChebOut {
     T c1 = T(0), c2 = T(0);
 };
 
-template <int MODE, class T>
+// RES: for MODE 1 and 3, acc already holds the residual b - A x (the FP64 SELL
+// kernel starts its accumulator at b and subtracts the products).
+template <int MODE, class T, bool RES = false>
 __device__ __forceinline__ void spmv_out(int64_t row, T acc, const T* __restrict__ x, const T* __restrict__ b,
                                          T* __restrict__ y, const ChebOut<T>& ch) {
     if (MODE == 0) y[row] = acc;
-    else if (MODE == 1) y[row] = b[row] - acc;
+    else if (MODE == 1) y[row] = RES ? acc : b[row] - acc;
     else if (MODE == 2) y[row] += acc;
     else {
-        const T r = b[row] - acc;
+        const T r = RES ? acc : b[row] - acc;
         const T dn = (ch.c1 != T(0) ? ch.c1 * ch.d[row] : T(0)) + ch.c2 * ch.dinv[row] * r;
         ch.d[row] = dn;
         ch.xo[row] = x[row] + dn;
@@ -64,9 +66,15 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __
     const int64_t sl = (int64_t)blockIdx.x * SPB + warp / H;
     const int64_t row = sl * 32 + lane;
     const bool live = row < n_rows;
+    // FP64 residual modes: the first warp of the slice starts at b, and the
+    // products are subtracted (one multiply-add each, no separate b - A x: the
+    // FP64 pipe is a limit here; in FP32 the early load of b measured slower)
+    constexpr bool RES = sizeof(T) == 8 && (MODE == 1 || MODE == 3);
+    constexpr T sgn = RES ? T(-1) : T(1);
     T a[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) a[u] = T(0);
+    if (RES && live && h == 0) a[0] = b[row];
     if (live) {
         const int e = off[sl + 1];
         int p = off[sl] + 32 * h + lane;
@@ -88,13 +96,13 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __
                 // FP64: one accumulator, so no partial sums to add up per row (the
                 // FP64 pipe is a limit here); the U gathers are still in flight together
 #pragma unroll
-                for (int u = 0; u < U; ++u) a[0] = fma(v[u], xv[u], a[0]);
+                for (int u = 0; u < U; ++u) a[0] = fma(sgn * v[u], xv[u], a[0]);
             } else {
 #pragma unroll
-                for (int u = 0; u < U; ++u) a[u] += v[u] * xv[u];
+                for (int u = 0; u < U; ++u) a[u] = fma(sgn * v[u], xv[u], a[u]);
             }
         }
-        for (; p < e; p += S) a[0] += val[p] * __ldg(x + column(p));
+        for (; p < e; p += S) a[0] = fma(sgn * val[p], __ldg(x + column(p)), a[0]);
     }
     if constexpr (sizeof(T) != 8) {
 #pragma unroll
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int64_t n_rows, const int* __
         acc += part[warp / H][lane];
     }
     if (!live) return;
-    spmv_out<MODE, T>(row, acc, x, b, y, ch);
+    spmv_out<MODE, T, RES>(row, acc, x, b, y, ch);
 }
 
 }  // namespace
