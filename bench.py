@@ -75,6 +75,9 @@ import inputs, oracle
 from oracle.assembly import assemble_problem
 dim, n, seed, beta = {spec!r}
 P = inputs.heterogeneous_problem(dim, n, seed=seed, beta=beta) if dim == 3 else inputs.mms_problem(2, n)
+for _ in range({warmup}):  # untimed warm-up steps
+    K, f = assemble_problem(P)
+    oracle.solve_direct(K, f, coords=P.mesh.coords)
 reps, t_tot, steps = {reps}, 0.0, 0
 res = None
 while steps < reps:
@@ -90,12 +93,15 @@ print(json.dumps({{"dofs": P.n_dofs, "steps": steps, "seconds": t_tot, "residual
 """
 
 
-def run_oracle(spec, reps, budget):
-    """Time the oracle (assembly + direct solve) in a single-threaded child process."""
+def run_oracle(spec, reps, budget, warmup=0):
+    """Time the oracle (assembly + direct solve) in a single-threaded child process:
+    `warmup` untimed steps, then up to `reps` timed ones (fewer if `budget` seconds
+    run out; the line reports the steps timed)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[k] = "1"
-    code = _ORACLE_SNIPPET.format(root=ROOT, spec=tuple(spec[:4]), reps=reps, budget=budget)
+    code = _ORACLE_SNIPPET.format(root=ROOT, spec=tuple(spec[:4]), reps=reps, budget=budget,
+                                  warmup=warmup)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                        timeout=900)
     if r.returncode:
@@ -220,11 +226,11 @@ def bench_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    out = run_oracle(CPU_SAMPLE, reps=args.steps + args.warmup, budget=240.0)
+    out = run_oracle(CPU_SAMPLE, reps=args.steps, budget=240.0, warmup=args.warmup)
     steps = out["steps"]
     line = {
         "impl": "reference", "metric": METRIC, "value": out["dof_per_s"], "unit": "DoF/s",
-        "n_gpus": args.gpus, "steps": steps, "warmup": 0,
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * out["seconds"] / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "sample_dofs": out["dofs"]},
