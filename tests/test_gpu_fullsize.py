@@ -71,6 +71,14 @@ def test_fullsize_galerkin_rows(workload):
     sz1, (rp1, col1, val1), _ = s.level(1, with_p=False)
     Ac = csr_from_export(rp1, col1, val1, (sz1["rows"], sz1["rows"]))
     s.close()
+    # every exported row holds strictly increasing column indices (the transposes and the
+    # Galerkin product sort rows; the SELL export keeps that order)
+    for M in (A, Pm, Ac):
+        d = np.diff(M.indices.astype(np.int64))
+        starts = M.indptr[1:-1]
+        inside = np.ones(d.size, dtype=bool)
+        inside[starts[(starts > 0) & (starts <= d.size)] - 1] = False
+        assert (d[inside] > 0).all()
     assert (Ac != Ac.T).nnz == 0
     Icoarse = np.sort(inputs.rng(23).choice(sz1["rows"], size=50, replace=False))
     ref = ((Pm[:, Icoarse].T.tocsr() @ A) @ Pm).toarray()
