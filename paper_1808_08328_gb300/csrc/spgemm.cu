@@ -889,90 +889,7 @@ __global__ void k_transpose_scatter(int64_t n_rows, const int* __restrict__ rp,
     }
 }
 
-// Rows of 2..256 entries: one warp per row, a bitonic sort of (col, val) by
-// col in shared memory (columns distinct, so the result is the sorted row).
-constexpr int kSortWarpMax = 256;
-constexpr int kSortBlockMax = 4096;
-template <class V>
-__global__ void __launch_bounds__(256) k_sort_rows_warp(int64_t n_rows, const int* __restrict__ rp,
-                                                        int* __restrict__ col, V* __restrict__ val) {
-    __shared__ int sk[8][kSortWarpMax];
-    __shared__ V sv[8][kSortWarpMax];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + warp;
-    if (i >= n_rows) return;  // whole warp
-    const int s = rp[i], len = rp[i + 1] - s;
-    if (len <= 1 || len > kSortWarpMax) return;  // whole warp
-    int P = 2;
-    while (P < len) P <<= 1;
-    int* k = sk[warp];
-    V* v = sv[warp];
-    for (int t = lane; t < P; t += 32) {
-        k[t] = (t < len) ? col[s + t] : INT_MAX;
-        v[t] = (t < len) ? val[s + t] : V(0);
-    }
-    __syncwarp();
-    for (int kk = 2; kk <= P; kk <<= 1)
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int t = lane; t < P; t += 32) {
-                const int u = t ^ j;
-                if (u > t) {
-                    const bool up = (t & kk) == 0;
-                    if ((k[t] > k[u]) == up) {
-                        const int tk = k[t]; k[t] = k[u]; k[u] = tk;
-                        const V tv = v[t]; v[t] = v[u]; v[u] = tv;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    for (int t = lane; t < len; t += 32) {
-        col[s + t] = k[t];
-        val[s + t] = v[t];
-    }
-}
-
-// Rows of kSortWarpMax+1..kSortBlockMax entries: one block per row, the same
-// bitonic sort with the block's threads.
-template <class V>
-__global__ void __launch_bounds__(256) k_sort_rows_block(int64_t n_rows, const int* __restrict__ rp,
-                                                         int* __restrict__ col, V* __restrict__ val) {
-    extern __shared__ unsigned char sort_smem[];
-    int* k = reinterpret_cast<int*>(sort_smem);
-    V* v = reinterpret_cast<V*>(sort_smem + kSortBlockMax * sizeof(int));
-    const int64_t i = blockIdx.x;
-    if (i >= n_rows) return;
-    const int s = rp[i], len = rp[i + 1] - s;
-    if (len <= kSortWarpMax || len > kSortBlockMax) return;  // uniform over the block
-    int P = 2;
-    while (P < len) P <<= 1;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) {
-        k[t] = (t < len) ? col[s + t] : INT_MAX;
-        v[t] = (t < len) ? val[s + t] : V(0);
-    }
-    __syncthreads();
-    for (int kk = 2; kk <= P; kk <<= 1)
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < P; t += blockDim.x) {
-                const int u = t ^ j;
-                if (u > t) {
-                    const bool up = (t & kk) == 0;
-                    if ((k[t] > k[u]) == up) {
-                        const int tk = k[t]; k[t] = k[u]; k[u] = tk;
-                        const V tv = v[t]; v[t] = v[u]; v[u] = tv;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    for (int t = threadIdx.x; t < len; t += blockDim.x) {
-        col[s + t] = k[t];
-        val[s + t] = v[t];
-    }
-}
-
-// warp per row: rank sort of (col, val) by col (distinct cols), for rows
-// longer than kSortBlockMax (the two bitonic kernels take the others)
+// warp per row: rank sort of (col, val) by col (distinct cols)
 template <class V>
 __global__ void k_sort_rows(int64_t n_rows, const int* __restrict__ rp, int* __restrict__ col,
                             V* __restrict__ val, int* __restrict__ tmpc,
@@ -981,7 +898,6 @@ __global__ void k_sort_rows(int64_t n_rows, const int* __restrict__ rp, int* __r
     const int lane = threadIdx.x & 31;
     if (i >= n_rows) return;
     const int s = rp[i], e = rp[i + 1];
-    if (e - s <= kSortBlockMax) return;
     for (int p = s + lane; p < e; p += 32) { tmpc[p] = col[p]; tmpv[p] = val[p]; }
     __syncwarp();
     for (int p = s + lane; p < e; p += 32) {
@@ -1301,16 +1217,6 @@ void transpose_t(const Csr& A, Csr& T, cudaStream_t s, HostScratch& hs) {
     k_transpose_scatter<V><<<grid_for(A.n_rows, B), B, 0, s>>>(A.n_rows, A.row_ptr.get(), A.col.get(),
                                                                vbuf<V>(A).get(), cursor.get(), T.col.get(),
                                                                vbuf<V>(T).get());
-    DPP_LAUNCH_CK();
-    // sorted rows: bitonic sorts for rows of up to kSortBlockMax entries, the
-    // rank sort beyond (each kernel skips the rows of the others)
-    k_sort_rows_warp<V><<<grid_for(T.n_rows, 8), 256, 0, s>>>(T.n_rows, T.row_ptr.get(), T.col.get(),
-                                                              vbuf<V>(T).get());
-    DPP_LAUNCH_CK();
-    const size_t smem = (size_t)kSortBlockMax * (sizeof(int) + sizeof(V));
-    set_smem(k_sort_rows_block<V>, smem);
-    k_sort_rows_block<V><<<(unsigned)std::max<int64_t>(T.n_rows, 1), 256, smem, s>>>(
-        T.n_rows, T.row_ptr.get(), T.col.get(), vbuf<V>(T).get());
     DPP_LAUNCH_CK();
     DBuf<int> tc(std::max<int64_t>(A.nnz, 1));
     DBuf<V> tv(std::max<int64_t>(A.nnz, 1));
