@@ -57,6 +57,7 @@ def batch_problems(n_inst, seed):
 def precision_of(spec) -> int:
     return spec[5] if len(spec) > 5 else 0
 CPU_SAMPLE = (3, 12, 0, 1.0)   # the oracle's bounded sample of the same recipe: 3D 12^3 cubes
+CPU_SMALL = (2, 32, 0, 1.0)    # 2D 32^2 MMS, the small single-solve workload
 
 
 def make_problem(spec):
@@ -113,10 +114,14 @@ def run_oracle(spec, reps, budget, warmup=0):
 
 def cpu_baseline_block(out, spec):
     dim, n = spec[:2]
-    return {"value": out["dof_per_s"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{out['steps']} x (numpy CG-VMS assembly + SuperLU nested-dissection solve) "
-                      f"on the same recipe at {n}^{dim} cubes ({out['dofs']} DoF), "
-                      f"{out['seconds']:.1f} s, single-threaded BLAS"}
+    blk = {"value": out["dof_per_s"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+           "sample": f"{out['steps']} x (numpy CG-VMS assembly + SuperLU nested-dissection solve) "
+                     f"on the same recipe at {n}^{dim} cubes ({out['dofs']} DoF), "
+                     f"{out['seconds']:.1f} s, single-threaded BLAS"}
+    if "other_sizes" in out:
+        blk["other_sizes"] = {k: {"dofs": o["dofs"], "dof_per_s": o["dof_per_s"], "steps": o["steps"]}
+                              for k, o in out["other_sizes"].items()}
+    return blk
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -362,6 +367,9 @@ def bench_gb300(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = run_oracle(CPU_SAMPLE, reps=3, budget=20.0)   # before any GPU call
+        # the oracle's rate on the 2D 32^2 MMS problem of the small-solve mode, for scale:
+        # the direct solve's fill grows faster than the DoF, so its rate falls with size
+        cpu["other_sizes"] = {"2d32_mms_fp64": run_oracle(CPU_SMALL, reps=5, budget=5.0)}
 
     import numpy as np
     import torch
