@@ -534,6 +534,149 @@ k_long_numeric(const int* __restrict__ arp, const int* __restrict__ acol,
     }
 }
 
+// Long rows of a product whose B has at most kLongBitCols columns: the row's
+// column set is a bitmap in shared memory. A column's place in the sorted row
+// is the number of set bits before it (a prefix sum of the words' popcounts and
+// one popcount inside the word), so no hash table, sort or search is needed.
+// The values are accumulated as in k_long_numeric (one accumulator per warp,
+// entries of A in p order, added in warp order), so both give the same sums.
+constexpr int kLongBitCols = 65536;
+constexpr int kLongBitWords = kLongBitCols / 32;
+
+// false (and nothing written) for a column outside the bitmap's n_words words
+__device__ __forceinline__ bool bm_set(unsigned* bm, int c, int n_words) {
+    if ((unsigned)c >= 32u * (unsigned)n_words) return false;
+    const unsigned bit = 1u << (c & 31);
+    if (!(bm[c >> 5] & bit)) atomicOr(&bm[c >> 5], bit);  // plain read first: most bits repeat
+    return true;
+}
+
+// pre[w] = set bits in words 0..w-1 (block-wide exclusive scan); bm is final.
+__device__ __forceinline__ void bm_prefix(const unsigned* bm, int* pre, int n_words, int* warp_tot) {
+    const int per = (n_words + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int w0 = min((int)threadIdx.x * per, n_words), w1 = min(w0 + per, n_words);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int mine = 0;
+    for (int w = w0; w < w1; ++w) mine += __popc(bm[w]);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int run = incl - mine;
+    for (int w = 0; w < warp; ++w) run += warp_tot[w];
+    for (int w = w0; w < w1; ++w) {
+        pre[w] = run;
+        run += __popc(bm[w]);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kLongWarps * 32)
+k_long_count_bm(const int* __restrict__ arp, const int* __restrict__ acol,
+                const int* __restrict__ brp, const int* __restrict__ bcol, int n_words,
+                int* __restrict__ count, const int* __restrict__ rows, int* __restrict__ status,
+                int upper) {
+    __shared__ unsigned bm[kLongBitWords];
+    __shared__ int part[kLongWarps];
+    const int i = rows[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < n_words; t += blockDim.x) bm[t] = 0u;
+    __syncthreads();
+    bool ok = true;
+    for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
+        const int k = acol[p];
+        for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32)
+            ok &= bm_set(bm, bcol[q], n_words);
+    }
+    if (!ok) atomicOr(status, 1);
+    __syncthreads();
+    int c = 0;
+    for (int t = threadIdx.x; t < n_words; t += blockDim.x) c += __popc(bm[t]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) part[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kLongWarps; ++w) t += part[w];
+        count[i] = t;
+    }
+}
+
+template <class V>
+constexpr size_t long_bm_smem() {
+    return (size_t)kLongWarps * kLongCap * sizeof(V) + (size_t)kLongBitWords * (sizeof(unsigned) + sizeof(int)) +
+           (size_t)kLongWarps * sizeof(int);
+}
+
+template <class V>
+__global__ void __launch_bounds__(kLongWarps * 32)
+k_long_numeric_bm(const int* __restrict__ arp, const int* __restrict__ acol,
+                  const V* __restrict__ aval, const int* __restrict__ brp,
+                  const int* __restrict__ bcol, const V* __restrict__ bval, int n_words,
+                  const int* __restrict__ crp, int* __restrict__ ccol, V* __restrict__ cval,
+                  const int* __restrict__ rows, int* __restrict__ wide, int* __restrict__ status,
+                  int upper) {
+    extern __shared__ __align__(16) unsigned char long_bm_mem[];
+    V* acc = reinterpret_cast<V*>(long_bm_mem);                                // kLongWarps * kLongCap
+    unsigned* bm = reinterpret_cast<unsigned*>(acc + kLongWarps * kLongCap);  // kLongBitWords
+    int* pre = reinterpret_cast<int*>(bm + kLongBitWords);                     // kLongBitWords
+    int* warp_tot = pre + kLongBitWords;                                       // kLongWarps
+    // (all of it dynamic: the launch sets the opt-in size whenever it passes 48 KB)
+    const int i = rows[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = crp[i], u = crp[i + 1] - c0;
+    if (u > kLongCap) {
+        if (threadIdx.x == 0) wide[atomicAdd(&wide[0], 1) + 1] = i;
+        return;
+    }
+    V* my = acc + warp * kLongCap;
+    for (int e = lane; e < u; e += 32) my[e] = V(0);
+    for (int t = threadIdx.x; t < n_words; t += blockDim.x) bm[t] = 0u;
+    __syncthreads();
+    bool ok = true;
+    for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
+        const int k = acol[p];
+        for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32)
+            ok &= bm_set(bm, bcol[q], n_words);
+    }
+    if (!ok) atomicOr(status, 1);
+    __syncthreads();
+    bm_prefix(bm, pre, n_words, warp_tot);
+    // the row's column count must be the one counted (it sizes C's row)
+    if (threadIdx.x == 0 && (n_words > 0 ? pre[n_words - 1] + __popc(bm[n_words - 1]) : 0) != u)
+        atomicOr(status, 1);
+    for (int w = threadIdx.x; w < n_words; w += blockDim.x) {
+        unsigned m = bm[w];
+        int r = pre[w];
+        while (m && r < u) {
+            ccol[c0 + r++] = w * 32 + (__ffs(m) - 1);
+            m &= m - 1u;
+        }
+    }
+    for (int p = arp[i] + warp; p < arp[i + 1]; p += kLongWarps) {
+        const int k = acol[p];
+        const V a = aval[p];
+        for (int q = b_row_start(brp, bcol, k, upper ? i : INT_MIN) + lane; q < brp[k + 1]; q += 32) {
+            const int c = bcol[q];
+            if ((unsigned)c >= 32u * (unsigned)n_words) continue;  // flagged above
+            const int pos = pre[c >> 5] + __popc(bm[c >> 5] & ((1u << (c & 31)) - 1u));
+            if (pos < u) my[pos] += a * bval[q];                    // else flagged above
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < u; e += blockDim.x) {
+        V v = acc[e];
+#pragma unroll
+        for (int w = 1; w < kLongWarps; ++w) v += acc[w * kLongCap + e];
+        cval[c0 + e] = v;
+    }
+}
+
 // products per row: sum of B's row lengths over A's row; long rows are listed
 __global__ void k_split_long(int64_t n, const int* __restrict__ arp, const int* __restrict__ acol,
                              const int* __restrict__ brp, int threshold, int* __restrict__ is_long,
@@ -1046,12 +1189,20 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
         DBuf<int> wide(n_ovf + 2), st(1);
         DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
         DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
-        const size_t smem_l = (size_t)(kLongHT + 2 * kLongCap) * sizeof(int) +
-                              (size_t)kLongWarps * kLongCap * sizeof(V);
-        set_smem(k_long_numeric<V>, smem_l);
-        k_long_numeric<V><<<(unsigned)n_ovf, kLongWarps * 32, smem_l, s>>>(
-            A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
-            vbuf<V>(C).get(), ovf.get() + 1, wide.get(), up);
+        if (B.n_cols <= kLongBitCols) {
+            const size_t smem_b = long_bm_smem<V>();
+            set_smem(k_long_numeric_bm<V>, smem_b);
+            k_long_numeric_bm<V><<<(unsigned)n_ovf, kLongWarps * 32, smem_b, s>>>(
+                A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), (int)((B.n_cols + 31) / 32),
+                C.row_ptr.get(), C.col.get(), vbuf<V>(C).get(), ovf.get() + 1, wide.get(), st.get(), up);
+        } else {
+            const size_t smem_l = (size_t)(kLongHT + 2 * kLongCap) * sizeof(int) +
+                                  (size_t)kLongWarps * kLongCap * sizeof(V);
+            set_smem(k_long_numeric<V>, smem_l);
+            k_long_numeric<V><<<(unsigned)n_ovf, kLongWarps * 32, smem_l, s>>>(
+                A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
+                vbuf<V>(C).get(), ovf.get() + 1, wide.get(), up);
+        }
         DPP_LAUNCH_CK();
         const int n_wide = read_scalar(wide.get(), s, hs);
         if (n_wide > 0) {
@@ -1061,9 +1212,11 @@ bool spgemm_onepass(const CsrView& A, const CsrView& B, Csr& C, int up, cudaStre
                 A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), C.row_ptr.get(), C.col.get(),
                 vbuf<V>(C).get(), wide.get() + 1, st.get(), up);
             DPP_LAUNCH_CK();
-            if (read_scalar(st.get(), s, hs))
-                fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
         }
+        if (read_scalar(st.get(), s, hs))
+            fail(DPP_ERR_INVALID_ARGUMENT,
+                 "spgemm: a product row has more than 8191 distinct columns, or a column index "
+                 "outside the operand's columns");
     }
     DPP_CK(cudaStreamSynchronize(s));
     return true;
@@ -1123,7 +1276,16 @@ void spgemm_t(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStrea
             if (read_scalar(last_ovf.get(), s, hs) > 0)
                 fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
         }
-        if (n_long > 0) {
+        if (n_long > 0 && B.n_cols <= kLongBitCols) {
+            DBuf<int> st(1);
+            DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
+            k_long_count_bm<<<(unsigned)n_long, kLongWarps * 32, 0, s>>>(
+                A.rp, A.col, B.rp, B.col, (int)((B.n_cols + 31) / 32), C.row_ptr.get(),
+                long_rows.get() + 1, st.get(), up);
+            DPP_LAUNCH_CK();
+            if (read_scalar(st.get(), s, hs))
+                fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a column index outside the operand's columns");
+        } else if (n_long > 0) {
             DBuf<int> st(1);
             DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
             const size_t smem = (size_t)kLongHT * sizeof(int);
@@ -1157,7 +1319,14 @@ void spgemm_t(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStrea
     DBuf<int> wide(n + 2), st(1);
     DPP_CK(cudaMemsetAsync(wide.get(), 0, sizeof(int), s));
     DPP_CK(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
-    if (n_long > 0) {
+    if (n_long > 0 && B.n_cols <= kLongBitCols) {
+        const size_t smem = long_bm_smem<V>();
+        set_smem(k_long_numeric_bm<V>, smem);
+        k_long_numeric_bm<V><<<(unsigned)n_long, kLongWarps * 32, smem, s>>>(
+            A.rp, A.col, vals_of<V>(A), B.rp, B.col, vals_of<V>(B), (int)((B.n_cols + 31) / 32),
+            C.row_ptr.get(), C.col.get(), vbuf<V>(C).get(), long_rows.get() + 1, wide.get(), st.get(), up);
+        DPP_LAUNCH_CK();
+    } else if (n_long > 0) {
         const size_t smem = (size_t)(kLongHT + 2 * kLongCap) * sizeof(int) +
                             (size_t)kLongWarps * kLongCap * sizeof(V);
         set_smem(k_long_numeric<V>, smem);
@@ -1182,8 +1351,12 @@ void spgemm_t(const CsrView& A, const CsrView& B, Csr& C, bool values, cudaStrea
                                                         vals_of<V>(B), C.row_ptr.get(), C.col.get(),
                                                         vbuf<V>(C).get(), wide.get() + 1, st.get(), up);
         DPP_LAUNCH_CK();
+    }
+    if (n_long > 0 || n_wide > 0) {
         if (read_scalar(st.get(), s, hs))
-            fail(DPP_ERR_INVALID_ARGUMENT, "spgemm: a product row has more than 8191 distinct columns");
+            fail(DPP_ERR_INVALID_ARGUMENT,
+                 "spgemm: a product row has more than 8191 distinct columns, or a column index "
+                 "outside the operand's columns");
     }
     DPP_CK(cudaStreamSynchronize(s));
 }
